@@ -1,0 +1,149 @@
+/*
+ * qtp.h - C ABI of libqtp, the GB300 (sm_103a) fast T-product of third-order
+ * quaternion tensors.
+ *
+ * Method: Zheng & Ni, "Block diagonalization of block circulant quaternion
+ * matrices and the fast calculation for T-product of quaternion tensors"
+ * (arXiv 2212.14318), Algorithm 5.1 with Theorem 5.1.  For A in Q^{m x n x p}
+ * and B in Q^{n x s x p} the library returns C = A * B in Q^{m x s x p}, the
+ * T-product of Definition 2.3, C = fold(bcirc(A) . unfold(B)).
+ *
+ * ------------------------------------------------------------------------
+ * Data layout ("tube-contiguous complex-pair planes")
+ * ------------------------------------------------------------------------
+ * A quaternion q = a + b i + c j + d k is stored by its Cayley-Dickson halves
+ * q = q1 + q2 j with q1 = a + b i, q2 = c + d i (Sec. 2.2).  A tensor
+ * X in Q^{R x K x p} is ONE buffer of 2*R*K*p complex FP32 numbers, each
+ * complex number two consecutive floats (real, imag):
+ *
+ *     X[plane][r][k][t]  at float offset  2 * (((plane*R + r)*K + k)*p + t)
+ *
+ * plane 0 holds X1 = (a, b), plane 1 holds X2 = (c, d); t is the index along
+ * the third mode (frontal slice), so every tube X(r, k, :) is contiguous.
+ * Every tensor pointer must be 16-byte aligned.
+ *
+ * ------------------------------------------------------------------------
+ * Ownership, streams, errors
+ * ------------------------------------------------------------------------
+ * - The caller owns every tensor and the workspace; all of them are device
+ *   memory unless the entry point's name ends in _host.  The plan owns only
+ *   its twiddle tables, its device error word and tuned parameters.
+ * - Everything after plan creation is asynchronous on the caller's stream
+ *   (a cudaStream_t passed as void*; NULL = legacy default stream).  Only
+ *   qtp_plan_create / qtp_plan_destroy allocate, free or synchronise.
+ * - Every call returns a qtp_status and never throws.  Invalid shapes, null
+ *   or misaligned pointers, an unsupported precision and an undersized
+ *   workspace are rejected on the host before any launch.  A failed launch
+ *   maps to QTP_ERR_CUDA.  Kernels that wait on a barrier give up after a
+ *   bounded number of polls, record it in the plan's error word and return;
+ *   qtp_plan_sync reports that as QTP_ERR_TIMEOUT.
+ * - qtp_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef QTP_H_
+#define QTP_H_
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define QTP_API __attribute__((visibility("default")))
+#else
+#define QTP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QTP_OK = 0,
+  QTP_ERR_INVALID_ARG = 1,  /* bad shape, null or misaligned pointer       */
+  QTP_ERR_UNSUPPORTED = 2,  /* precision or size this build does not do   */
+  QTP_ERR_WORKSPACE = 3,    /* workspace missing or smaller than required */
+  QTP_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed          */
+  QTP_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up         */
+  QTP_ERR_INTERNAL = 6
+} qtp_status;
+
+/* Arithmetic of the per-frequency products (Alg. 5.1 Step 2).  The tube FFTs
+ * (Steps 1 and 3) always run in FP32.
+ *   QTP_PREC_FP32   : FP32 FMA on CUDA cores ("plain FP32 path").
+ *   QTP_PREC_BF16X3 : each FP32 operand x is split x = hi + lo with
+ *                     hi = bf16(x), lo = bf16(x - hi); the products
+ *                     hi*hi + hi*lo + lo*hi run on the tcgen05 tensor cores
+ *                     with FP32 accumulation (relative error ~1e-6).
+ *   QTP_PREC_BF16   : hi*hi only (relative error ~1e-3; comparison only). */
+typedef enum { QTP_PREC_FP32 = 0, QTP_PREC_BF16X3 = 1, QTP_PREC_BF16 = 2 } qtp_precision;
+
+typedef struct qtp_plan qtp_plan;
+
+/* Create a plan for C = A * B with A in Q^{m x n x p}, B in Q^{n x s x p}.
+ * Requires 1 <= m, n, s <= 2^20, 1 <= p <= 4096 and m*n*p, n*s*p, m*s*p
+ * each below 2^31 complex entries per plane.  Allocates the twiddle table
+ * w^e = exp(-2 pi i e / p), e in [0, p) (eq. DFT, generated in FP64 and
+ * rounded to FP32) and synchronises the current device.  flags must be 0. */
+QTP_API qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p,
+                           int precision, unsigned flags);
+QTP_API qtp_status qtp_plan_destroy(qtp_plan* plan);
+
+/* Bytes of device workspace qtp_forward needs: the spectra of A and B in the
+ * GEMM operand format of the plan's precision plus the FP32 spectrum of C. */
+QTP_API qtp_status qtp_workspace_size(const qtp_plan* plan, size_t* bytes);
+
+/* Bytes of device workspace qtp_backward needs (spectra of A, B and dC and
+ * the FP32 spectra of dA and dB). */
+QTP_API qtp_status qtp_backward_workspace_size(const qtp_plan* plan, size_t* bytes);
+
+/* C = A * B (Definition 2.3) by Algorithm 5.1:
+ *   Step 1 (Thm 4.4, eq. fft-Q): FFT of every tube of both halves of A and B
+ *          along the third mode, omega = exp(-2 pi i / p), unnormalised.
+ *   Step 2 (Thm 5.1, eqs. TC/TC2): for every frequency f, with f' = (-f) mod p
+ *          (the paper's 1-based p+2-i),
+ *            C1_f = A1_f B1_f - A2_f conj(B2_f'),  C2_f = A1_f B2_f + A2_f conj(B1_f')
+ *          i.e. one complex m x 2n x 2s product per frequency.  This is the
+ *          paper's eqs. TC/TC2 after absorbing its conjugations into the
+ *          transform (fft(conj x) = conj(fft(x)) reversed in frequency).
+ *   Step 3 (eq. ifft-C): inverse FFT of every tube of C1, C2 with scale 1/p.
+ * A: 2*m*n*p complex, B: 2*n*s*p complex, C: 2*m*s*p complex (layout above).
+ * C may not alias A, B or the workspace.  workspace_bytes must be at least
+ * qtp_workspace_size(plan).  Asynchronous on stream. */
+QTP_API qtp_status qtp_forward(const qtp_plan* plan, const float* A, const float* B, float* C,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* Same product with A, B and C in HOST memory (pinned for full speed).  The
+ * call copies A and B to the device, runs qtp_forward and copies C back, all
+ * asynchronously on stream; the caller synchronises before reading C.
+ * dev_buffer (device, 16-byte aligned) must hold at least
+ * qtp_host_buffer_size(plan) bytes: device copies of A, B, C plus the
+ * workspace. */
+QTP_API qtp_status qtp_host_buffer_size(const qtp_plan* plan, size_t* bytes);
+QTP_API qtp_status qtp_forward_host(const qtp_plan* plan, const float* A_host, const float* B_host,
+                            float* C_host, void* dev_buffer, size_t dev_buffer_bytes, void* stream);
+
+/* Gradients of a real loss L(C), C = A * B, with each quaternion entry taken
+ * as four independent reals (not in the paper; a training-style use of it):
+ *     dA = dC * B^H,   dB = A^H * dC,
+ * where X^H(:,:,1) = X(:,:,1)^*, X^H(:,:,k) = X(:,:,p+2-k)^* (quaternion
+ * conjugate transpose of the slices, Kilmer-Martin convention), so both are
+ * T-products computed by the same three steps.  dC has C's shape, dA A's, dB
+ * B's.  dA or dB may be NULL to skip it.  workspace_bytes must be at least
+ * qtp_backward_workspace_size(plan).  Asynchronous on stream. */
+QTP_API qtp_status qtp_backward(const qtp_plan* plan, const float* dC, const float* A, const float* B,
+                        float* dA, float* dB, void* workspace, size_t workspace_bytes,
+                        void* stream);
+
+/* Synchronise stream, then read and clear the plan's device error word.
+ * Returns QTP_ERR_TIMEOUT if a kernel gave up on a bounded wait since the
+ * last call, QTP_ERR_CUDA if the stream reports an error, else QTP_OK. */
+QTP_API qtp_status qtp_plan_sync(const qtp_plan* plan, void* stream);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+QTP_API const char* qtp_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+QTP_API int qtp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTP_H_ */

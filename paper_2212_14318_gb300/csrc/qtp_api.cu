@@ -1,0 +1,515 @@
+// C ABI of libqtp: plans, argument validation, workspace layout and launch
+// sequencing of Algorithm 5.1 (Steps 1-3) and of its backward pass.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "qtp_internal.h"
+
+using namespace qtp;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+qtp_status fail(qtp_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+qtp_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(QTP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define QTP_CUDA(call, what)                 \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+int spec_format(int precision) {
+  return precision == QTP_PREC_BF16X3 ? FMT_BF16X3 : (precision == QTP_PREC_BF16 ? FMT_BF16 : FMT_C32);
+}
+
+// Leading dimension of a spectra row: TMA needs 16-byte row strides.
+long long spec_ld(int fmt, long long cols) { return fmt == FMT_C32 ? cols : round_up(cols, 8); }
+
+size_t spec_bytes(int fmt, long long p, long long rows, long long cols) {
+  return align256((size_t)2 * spec_parts(fmt) * p * rows * spec_ld(fmt, cols) * spec_elem_bytes(fmt));
+}
+
+size_t c32_bytes(long long p, long long rows, long long cols) {
+  return align256((size_t)2 * p * rows * cols * sizeof(float2));
+}
+
+struct FwdLayout {
+  size_t sa, sb, sc, total;
+};
+
+FwdLayout fwd_layout(const qtp_plan* pl) {
+  const int fmt = spec_format(pl->precision);
+  FwdLayout L;
+  L.sa = 0;
+  L.sb = L.sa + spec_bytes(fmt, pl->p, pl->m, pl->n);
+  L.sc = L.sb + spec_bytes(fmt, pl->p, pl->n, pl->s);
+  L.total = L.sc + c32_bytes(pl->p, pl->m, pl->s);
+  return L;
+}
+
+struct BwdLayout {
+  size_t sa, sb, sg, sda, sdb, total;
+};
+
+BwdLayout bwd_layout(const qtp_plan* pl) {
+  const int fmt = spec_format(pl->precision);
+  BwdLayout L;
+  L.sa = 0;
+  L.sb = L.sa + spec_bytes(fmt, pl->p, pl->m, pl->n);
+  L.sg = L.sb + spec_bytes(fmt, pl->p, pl->n, pl->s);
+  L.sda = L.sg + spec_bytes(fmt, pl->p, pl->m, pl->s);
+  L.sdb = L.sda + c32_bytes(pl->p, pl->m, pl->n);
+  L.total = L.sdb + c32_bytes(pl->p, pl->n, pl->s);
+  return L;
+}
+
+qtp_status check_plan(const qtp_plan* pl) {
+  if (!pl) return fail(QTP_ERR_INVALID_ARG, "plan is NULL");
+  return QTP_OK;
+}
+
+qtp_status check_dev_ptr(const void* ptr, const char* name, bool allow_null = false) {
+  if (!ptr) {
+    if (allow_null) return QTP_OK;
+    return fail(QTP_ERR_INVALID_ARG, "%s is NULL", name);
+  }
+  if (((uintptr_t)ptr & 15) != 0) return fail(QTP_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QTP_ERR_INVALID_ARG, "%s: cudaPointerGetAttributes failed (%s)", name, cudaGetErrorString(e));
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(QTP_ERR_INVALID_ARG, "%s is not device memory", name);
+  return QTP_OK;
+}
+
+qtp_status check_host_ptr(const void* ptr, const char* name) {
+  if (!ptr) return fail(QTP_ERR_INVALID_ARG, "%s is NULL", name);
+  if (((uintptr_t)ptr & 15) != 0) return fail(QTP_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+  return QTP_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int nblocks_for(long long rows, long long cols, int p) {
+  const long long T = fft_tubes_per_block(p);
+  return (int)((2 * rows * cols + T - 1) / T);
+}
+
+// Operand view helpers on complex FP32 spectra [plane][f][rows][cols].
+CView view(const float2* spec, int plane, int p, long long rows, long long cols, bool row_is_first_index,
+           int fneg, int conj) {
+  CView v;
+  v.base = spec + (long long)plane * p * rows * cols;
+  v.fstride = rows * cols;
+  // element (r, k) of the view: either (row, col) = (r, k) or (k, r)
+  v.rstride = row_is_first_index ? cols : 1;
+  v.kstride = row_is_first_index ? 1 : cols;
+  v.fneg = fneg;
+  v.conj = conj;
+  return v;
+}
+
+TcView tcv(int tensor, int plane, int fneg, int conj) {
+  TcView v;
+  v.tensor = tensor;
+  v.plane = plane;
+  v.fneg = fneg;
+  v.conj = conj;
+  return v;
+}
+
+// Step 2 of Alg. 5.1 for the forward product: out half 0 = C1, half 1 = C2.
+//   C1_f = A1_f B1_f - A2_f conj(B2_{-f}),   C2_f = A1_f B2_f + A2_f conj(B1_{-f})
+qtp_status run_products_fwd(const qtp_plan* pl, const void* sa, const void* sb, float2* sc, cudaStream_t st) {
+  const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
+  if (pl->precision == QTP_PREC_FP32) {
+    GemmProblem pr;
+    memset(&pr, 0, sizeof(pr));
+    pr.M = m; pr.N = s; pr.K = n; pr.p = p;
+    const float2* A = (const float2*)sa;
+    const float2* B = (const float2*)sb;
+    for (int h = 0; h < 2; ++h) {
+      pr.a[h][0] = view(A, 0, p, m, n, true, 0, 0);
+      pr.a[h][1] = view(A, 1, p, m, n, true, 0, 0);
+    }
+    // opB element (col c, k j) = B_hat[j][c]
+    pr.b[0][0] = view(B, 0, p, n, s, false, 0, 0); pr.sign[0][0] = 1.f;
+    pr.b[0][1] = view(B, 1, p, n, s, false, 1, 1); pr.sign[0][1] = -1.f;
+    pr.b[1][0] = view(B, 1, p, n, s, false, 0, 0); pr.sign[1][0] = 1.f;
+    pr.b[1][1] = view(B, 0, p, n, s, false, 1, 1); pr.sign[1][1] = 1.f;
+    pr.out = sc;
+    pr.out_hstride = (long long)p * m * s;
+    pr.out_fstride = (long long)m * s;
+    pr.out_rstride = s;
+    QTP_CUDA(launch_gemm_simt(pr, st), "products (fp32)");
+    return QTP_OK;
+  }
+  TcProblem pr;
+  memset(&pr, 0, sizeof(pr));
+  pr.kind = TC_FWD;
+  pr.M = m; pr.N = s; pr.K = n; pr.p = p;
+  pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
+  pr.a_base[0] = sa; pr.a_rows[0] = m; pr.a_cols[0] = n; pr.a_ld[0] = (int)spec_ld(FMT_BF16, n);
+  pr.b_base[0] = sb; pr.b_rows[0] = n; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
+  for (int h = 0; h < 2; ++h) {
+    pr.a[h][0] = tcv(0, 0, 0, 0);
+    pr.a[h][1] = tcv(0, 1, 0, 0);
+  }
+  pr.b[0][0] = tcv(0, 0, 0, 0); pr.sign[0][0] = 1.f;
+  pr.b[0][1] = tcv(0, 1, 1, 1); pr.sign[0][1] = -1.f;
+  pr.b[1][0] = tcv(0, 1, 0, 0); pr.sign[1][0] = 1.f;
+  pr.b[1][1] = tcv(0, 0, 1, 1); pr.sign[1][1] = 1.f;
+  pr.out = sc;
+  pr.out_hstride = (long long)p * m * s;
+  pr.out_fstride = (long long)m * s;
+  pr.out_rstride = s;
+  char msg[256] = "";
+  cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg));
+  if (e != cudaSuccess) return fail(QTP_ERR_CUDA, "products (tensor cores): %s %s", cudaGetErrorString(e), msg);
+  return QTP_OK;
+}
+
+// Backward products.  With G = F(dC) and the spectra of B^H and A^H
+// ((B^H)_1,f = B1_f^*, (B^H)_2,f = -B2_{-f}^T), dA = dC * B^H and
+// dB = A^H * dC by the same per-frequency rule:
+//   dA1_f = G1_f B1_f^* + G2_f B2_f^*,        dA2_f = -G1_f B2_{-f}^T + G2_f B1_{-f}^T
+//   dB1_f = A1_f^* G1_f + A2_{-f}^T conj(G2_{-f}),  dB2_f = A1_f^* G2_f - A2_{-f}^T conj(G1_{-f})
+qtp_status run_products_bwd(const qtp_plan* pl, const void* sa, const void* sb, const void* sg, float2* sda,
+                            float2* sdb, cudaStream_t st) {
+  const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
+  if (pl->precision == QTP_PREC_FP32) {
+    const float2* A = (const float2*)sa;
+    const float2* B = (const float2*)sb;
+    const float2* G = (const float2*)sg;
+    if (sda) {
+      GemmProblem pr;
+      memset(&pr, 0, sizeof(pr));
+      pr.M = m; pr.N = n; pr.K = s; pr.p = p;
+      for (int h = 0; h < 2; ++h) {
+        pr.a[h][0] = view(G, 0, p, m, s, true, 0, 0);
+        pr.a[h][1] = view(G, 1, p, m, s, true, 0, 0);
+      }
+      // opB element (col j, k c) = B_hat[j][c] -> row_is_first_index = true
+      pr.b[0][0] = view(B, 0, p, n, s, true, 0, 1); pr.sign[0][0] = 1.f;
+      pr.b[0][1] = view(B, 1, p, n, s, true, 0, 1); pr.sign[0][1] = 1.f;
+      pr.b[1][0] = view(B, 1, p, n, s, true, 1, 0); pr.sign[1][0] = -1.f;
+      pr.b[1][1] = view(B, 0, p, n, s, true, 1, 0); pr.sign[1][1] = 1.f;
+      pr.out = sda;
+      pr.out_hstride = (long long)p * m * n;
+      pr.out_fstride = (long long)m * n;
+      pr.out_rstride = n;
+      QTP_CUDA(launch_gemm_simt(pr, st), "backward products dA (fp32)");
+    }
+    if (sdb) {
+      GemmProblem pr;
+      memset(&pr, 0, sizeof(pr));
+      pr.M = n; pr.N = s; pr.K = m; pr.p = p;
+      for (int h = 0; h < 2; ++h) {
+        // opA element (row j, k i) = A_hat[i][j]
+        pr.a[h][0] = view(A, 0, p, m, n, false, 0, 1);
+        pr.a[h][1] = view(A, 1, p, m, n, false, 1, 0);
+      }
+      // opB element (col c, k i) = G_hat[i][c]
+      pr.b[0][0] = view(G, 0, p, m, s, false, 0, 0); pr.sign[0][0] = 1.f;
+      pr.b[0][1] = view(G, 1, p, m, s, false, 1, 1); pr.sign[0][1] = 1.f;
+      pr.b[1][0] = view(G, 1, p, m, s, false, 0, 0); pr.sign[1][0] = 1.f;
+      pr.b[1][1] = view(G, 0, p, m, s, false, 1, 1); pr.sign[1][1] = -1.f;
+      pr.out = sdb;
+      pr.out_hstride = (long long)p * n * s;
+      pr.out_fstride = (long long)n * s;
+      pr.out_rstride = s;
+      QTP_CUDA(launch_gemm_simt(pr, st), "backward products dB (fp32)");
+    }
+    return QTP_OK;
+  }
+  char msg[256] = "";
+  if (sda) {
+    TcProblem pr;
+    memset(&pr, 0, sizeof(pr));
+    pr.kind = TC_BWD_A;
+    pr.M = m; pr.N = n; pr.K = s; pr.p = p;
+    pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
+    pr.a_base[0] = sg; pr.a_rows[0] = m; pr.a_cols[0] = s; pr.a_ld[0] = (int)spec_ld(FMT_BF16, s);
+    pr.b_base[0] = sb; pr.b_rows[0] = n; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
+    for (int h = 0; h < 2; ++h) {
+      pr.a[h][0] = tcv(0, 0, 0, 0);
+      pr.a[h][1] = tcv(0, 1, 0, 0);
+    }
+    pr.b[0][0] = tcv(0, 0, 0, 1); pr.sign[0][0] = 1.f;
+    pr.b[0][1] = tcv(0, 1, 0, 1); pr.sign[0][1] = 1.f;
+    pr.b[1][0] = tcv(0, 1, 1, 0); pr.sign[1][0] = -1.f;
+    pr.b[1][1] = tcv(0, 0, 1, 0); pr.sign[1][1] = 1.f;
+    pr.out = sda;
+    pr.out_hstride = (long long)p * m * n;
+    pr.out_fstride = (long long)m * n;
+    pr.out_rstride = n;
+    cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg));
+    if (e != cudaSuccess) return fail(QTP_ERR_CUDA, "backward products dA: %s %s", cudaGetErrorString(e), msg);
+  }
+  if (sdb) {
+    TcProblem pr;
+    memset(&pr, 0, sizeof(pr));
+    pr.kind = TC_BWD_B;
+    pr.M = n; pr.N = s; pr.K = m; pr.p = p;
+    pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
+    pr.a_base[0] = sa; pr.a_rows[0] = m; pr.a_cols[0] = n; pr.a_ld[0] = (int)spec_ld(FMT_BF16, n);
+    pr.b_base[0] = sg; pr.b_rows[0] = m; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
+    for (int h = 0; h < 2; ++h) {
+      pr.a[h][0] = tcv(0, 0, 0, 1);
+      pr.a[h][1] = tcv(0, 1, 1, 0);
+    }
+    pr.b[0][0] = tcv(0, 0, 0, 0); pr.sign[0][0] = 1.f;
+    pr.b[0][1] = tcv(0, 1, 1, 1); pr.sign[0][1] = 1.f;
+    pr.b[1][0] = tcv(0, 1, 0, 0); pr.sign[1][0] = 1.f;
+    pr.b[1][1] = tcv(0, 0, 1, 1); pr.sign[1][1] = -1.f;
+    pr.out = sdb;
+    pr.out_hstride = (long long)p * n * s;
+    pr.out_fstride = (long long)n * s;
+    pr.out_rstride = s;
+    cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg));
+    if (e != cudaSuccess) return fail(QTP_ERR_CUDA, "backward products dB: %s %s", cudaGetErrorString(e), msg);
+  }
+  return QTP_OK;
+}
+
+qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, float* C, char* ws,
+                        cudaStream_t st) {
+  const int fmt = spec_format(pl->precision);
+  const FwdLayout L = fwd_layout(pl);
+  FftFwdJob jobs[2];
+  jobs[0].in = (const float2*)A;
+  jobs[0].out = ws + L.sa;
+  jobs[0].rows = pl->m; jobs[0].cols = pl->n; jobs[0].ld = (int)spec_ld(fmt, pl->n);
+  jobs[0].nblocks = nblocks_for(pl->m, pl->n, pl->p);
+  jobs[1].in = (const float2*)B;
+  jobs[1].out = ws + L.sb;
+  jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
+  jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p);
+  QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "forward tube FFT");
+  qtp_status r = run_products_fwd(pl, ws + L.sa, ws + L.sb, (float2*)(ws + L.sc), st);
+  if (r != QTP_OK) return r;
+  FftInvJob ij;
+  ij.in = (const float2*)(ws + L.sc);
+  ij.out = (float2*)C;
+  ij.rows = pl->m; ij.cols = pl->s;
+  ij.nblocks = nblocks_for(pl->m, pl->s, pl->p);
+  QTP_CUDA(launch_fft_inv(&ij, 1, pl->rp, pl->d_tw, st), "inverse tube FFT");
+  return QTP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qtp_last_error(void) { return g_err; }
+
+int qtp_version(void) { return 100; }
+
+qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int precision, unsigned flags) {
+  g_err[0] = 0;
+  if (!out) return fail(QTP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || n < 1 || s < 1 || p < 1) return fail(QTP_ERR_INVALID_ARG, "dimensions must be >= 1 (m=%d n=%d s=%d p=%d)", m, n, s, p);
+  if (m > (1 << 20) || n > (1 << 20) || s > (1 << 20))
+    return fail(QTP_ERR_INVALID_ARG, "m, n, s must be <= 2^20");
+  if (p > QTP_MAX_P) return fail(QTP_ERR_UNSUPPORTED, "p=%d exceeds the supported maximum %d", p, QTP_MAX_P);
+  const long long lim = 1LL << 31;
+  if ((long long)m * n * p >= lim || (long long)n * s * p >= lim || (long long)m * s * p >= lim)
+    return fail(QTP_ERR_INVALID_ARG, "a tensor plane exceeds 2^31 complex entries");
+  if (flags != 0) return fail(QTP_ERR_INVALID_ARG, "flags must be 0");
+  if (precision != QTP_PREC_FP32 && precision != QTP_PREC_BF16X3 && precision != QTP_PREC_BF16)
+    return fail(QTP_ERR_INVALID_ARG, "unknown precision %d", precision);
+  if (precision != QTP_PREC_FP32 && !tc_supported())
+    return fail(QTP_ERR_UNSUPPORTED, "BF16 tensor-core products need an sm_103 device (tcgen05)");
+  qtp_plan* pl = new qtp_plan();
+  pl->m = m; pl->n = n; pl->s = s; pl->p = p;
+  pl->precision = precision;
+  pl->rp = make_radix_plan(p);
+  pl->d_tw = nullptr;
+  pl->d_err = nullptr;
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_tw, sizeof(float2) * p);
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(pl->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = launch_twiddles(pl->d_tw, p, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    if (pl->d_tw) cudaFree(pl->d_tw);
+    if (pl->d_err) cudaFree(pl->d_err);
+    delete pl;
+    return cuda_fail(e, "plan creation");
+  }
+  *out = pl;
+  return QTP_OK;
+}
+
+qtp_status qtp_plan_destroy(qtp_plan* pl) {
+  if (!pl) return QTP_OK;
+  cudaFree(pl->d_tw);
+  cudaFree(pl->d_err);
+  delete pl;
+  return QTP_OK;
+}
+
+qtp_status qtp_workspace_size(const qtp_plan* pl, size_t* bytes) {
+  if (check_plan(pl) != QTP_OK) return QTP_ERR_INVALID_ARG;
+  if (!bytes) return fail(QTP_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = fwd_layout(pl).total;
+  return QTP_OK;
+}
+
+qtp_status qtp_backward_workspace_size(const qtp_plan* pl, size_t* bytes) {
+  if (check_plan(pl) != QTP_OK) return QTP_ERR_INVALID_ARG;
+  if (!bytes) return fail(QTP_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = bwd_layout(pl).total;
+  return QTP_OK;
+}
+
+qtp_status qtp_forward(const qtp_plan* pl, const float* A, const float* B, float* C, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(A, "A")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(B, "B")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(C, "C")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(workspace, "workspace")) != QTP_OK) return r;
+  const size_t need = fwd_layout(pl).total;
+  if (workspace_bytes < need)
+    return fail(QTP_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, need);
+  return forward_impl(pl, A, B, C, (char*)workspace, as_stream(stream));
+}
+
+qtp_status qtp_host_buffer_size(const qtp_plan* pl, size_t* bytes) {
+  if (check_plan(pl) != QTP_OK) return QTP_ERR_INVALID_ARG;
+  if (!bytes) return fail(QTP_ERR_INVALID_ARG, "bytes is NULL");
+  // device copies of A, B, C (each exactly one tensor, 256-byte aligned) + workspace
+  *bytes = c32_bytes(pl->p, pl->m, pl->n) + c32_bytes(pl->p, pl->n, pl->s) + c32_bytes(pl->p, pl->m, pl->s) +
+           fwd_layout(pl).total;
+  return QTP_OK;
+}
+
+qtp_status qtp_forward_host(const qtp_plan* pl, const float* A_host, const float* B_host, float* C_host,
+                            void* dev_buffer, size_t dev_buffer_bytes, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if ((r = check_host_ptr(A_host, "A_host")) != QTP_OK) return r;
+  if ((r = check_host_ptr(B_host, "B_host")) != QTP_OK) return r;
+  if ((r = check_host_ptr(C_host, "C_host")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dev_buffer, "dev_buffer")) != QTP_OK) return r;
+  size_t need = 0;
+  qtp_host_buffer_size(pl, &need);
+  if (dev_buffer_bytes < need)
+    return fail(QTP_ERR_WORKSPACE, "dev_buffer has %zu bytes, %zu needed", dev_buffer_bytes, need);
+  const size_t bA = (size_t)2 * pl->m * pl->n * pl->p * sizeof(float2);
+  const size_t bB = (size_t)2 * pl->n * pl->s * pl->p * sizeof(float2);
+  const size_t bC = (size_t)2 * pl->m * pl->s * pl->p * sizeof(float2);
+  char* base = (char*)dev_buffer;
+  float* dA = (float*)base;
+  float* dB = (float*)(base + c32_bytes(pl->p, pl->m, pl->n));
+  float* dC = (float*)(base + c32_bytes(pl->p, pl->m, pl->n) + c32_bytes(pl->p, pl->n, pl->s));
+  char* ws = base + c32_bytes(pl->p, pl->m, pl->n) + c32_bytes(pl->p, pl->n, pl->s) + c32_bytes(pl->p, pl->m, pl->s);
+  cudaStream_t st = as_stream(stream);
+  QTP_CUDA(cudaMemcpyAsync(dA, A_host, bA, cudaMemcpyHostToDevice, st), "copy A to device");
+  QTP_CUDA(cudaMemcpyAsync(dB, B_host, bB, cudaMemcpyHostToDevice, st), "copy B to device");
+  r = forward_impl(pl, dA, dB, dC, ws, st);
+  if (r != QTP_OK) return r;
+  QTP_CUDA(cudaMemcpyAsync(C_host, dC, bC, cudaMemcpyDeviceToHost, st), "copy C to host");
+  return QTP_OK;
+}
+
+qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, const float* B, float* dA,
+                        float* dB, void* workspace, size_t workspace_bytes, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dC, "dC")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(A, "A")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(B, "B")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dA, "dA", true)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dB, "dB", true)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(workspace, "workspace")) != QTP_OK) return r;
+  if (!dA && !dB) return QTP_OK;
+  const BwdLayout L = bwd_layout(pl);
+  if (workspace_bytes < L.total)
+    return fail(QTP_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
+  cudaStream_t st = as_stream(stream);
+  char* ws = (char*)workspace;
+  const int fmt = spec_format(pl->precision);
+  // Step 1 on A, B and dC.
+  FftFwdJob jobs[2];
+  jobs[0].in = (const float2*)A;
+  jobs[0].out = ws + L.sa;
+  jobs[0].rows = pl->m; jobs[0].cols = pl->n; jobs[0].ld = (int)spec_ld(fmt, pl->n);
+  jobs[0].nblocks = nblocks_for(pl->m, pl->n, pl->p);
+  jobs[1].in = (const float2*)B;
+  jobs[1].out = ws + L.sb;
+  jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
+  jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p);
+  QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "backward FFT of A, B");
+  FftFwdJob gj;
+  gj.in = (const float2*)dC;
+  gj.out = ws + L.sg;
+  gj.rows = pl->m; gj.cols = pl->s; gj.ld = (int)spec_ld(fmt, pl->s);
+  gj.nblocks = nblocks_for(pl->m, pl->s, pl->p);
+  QTP_CUDA(launch_fft_fwd(&gj, 1, fmt, pl->rp, pl->d_tw, st), "backward FFT of dC");
+  // Step 2.
+  r = run_products_bwd(pl, ws + L.sa, ws + L.sb, ws + L.sg, dA ? (float2*)(ws + L.sda) : nullptr,
+                       dB ? (float2*)(ws + L.sdb) : nullptr, st);
+  if (r != QTP_OK) return r;
+  // Step 3 on dA and dB.
+  FftInvJob ij[2];
+  int nj = 0;
+  if (dA) {
+    ij[nj].in = (const float2*)(ws + L.sda);
+    ij[nj].out = (float2*)dA;
+    ij[nj].rows = pl->m; ij[nj].cols = pl->n;
+    ij[nj].nblocks = nblocks_for(pl->m, pl->n, pl->p);
+    ++nj;
+  }
+  if (dB) {
+    ij[nj].in = (const float2*)(ws + L.sdb);
+    ij[nj].out = (float2*)dB;
+    ij[nj].rows = pl->n; ij[nj].cols = pl->s;
+    ij[nj].nblocks = nblocks_for(pl->n, pl->s, pl->p);
+    ++nj;
+  }
+  QTP_CUDA(launch_fft_inv(ij, nj, pl->rp, pl->d_tw, st), "backward inverse FFT");
+  return QTP_OK;
+}
+
+qtp_status qtp_plan_sync(const qtp_plan* pl, void* stream) {
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  QTP_CUDA(cudaStreamSynchronize(as_stream(stream)), "stream synchronize");
+  int v = 0;
+  QTP_CUDA(cudaMemcpy(&v, pl->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+  if (v != 0) {
+    cudaMemset(pl->d_err, 0, sizeof(int));
+    return fail(QTP_ERR_TIMEOUT, "a device-side wait gave up (code %d)", v);
+  }
+  return QTP_OK;
+}
+
+}  // extern "C"

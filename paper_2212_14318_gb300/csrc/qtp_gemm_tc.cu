@@ -1,0 +1,494 @@
+// Per-frequency complex products of Algorithm 5.1 Step 2 on the fifth-
+// generation tensor cores (tcgen05, sm_103a), split-BF16.
+//
+// Each FP32 spectrum value x was stored by the forward FFT as two bf16 parts,
+// hi = bf16(x) and lo = bf16(x - hi), real and imaginary parts in separate
+// planes.  A complex product a * b with a = ar + i ai, b = br + i bi becomes
+// the four real products ar.br, ai.bi, ar.bi, ai.br, and each real product
+// X.Y the three tensor-core products Xhi.Yhi + Xhi.Ylo + Xlo.Yhi (the lo.lo
+// term is below FP32 rounding), accumulated in FP32 in tensor memory.  Signs
+// (from the paper's "-" in eq. TC and from conjugations) are applied with the
+// instruction descriptor's negate-A bit, so no operand is ever rewritten.
+//
+// For frequency f and output half h the CTA computes a 128 x 128 complex tile
+//   Out_h(f) = sum_kh sign[h][kh] * opA[h][kh](f) . opB[h][kh](f)
+// with two accumulators in TMEM (real part: columns 0..127, imaginary part:
+// columns 128..255).  Operands stream through a 3-stage TMA -> shared memory
+// pipeline (mbarrier full/empty pairs); one thread issues tcgen05.mma, four
+// warps drain TMEM with tcgen05.ld.  K-major operands use the 64-byte swizzle
+// (32 bf16 of K per row); MN-major operands the 128-byte swizzle (64 bf16 of
+// M or N per row, 32 rows of K).  Every wait is bounded: on expiry the kernel
+// records an error code in the plan's error word and unwinds.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdio.h>
+
+#include "qtp_internal.h"
+
+namespace qtp {
+
+namespace {
+
+constexpr int BM = 128;                 // output rows per tile (UMMA M)
+constexpr int BN = 128;                 // complex output columns per tile (UMMA N)
+constexpr int BK = 32;                  // K per pipeline stage
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = 8192;        // one bf16 part tile: 128 x 32 or 32 x 128
+constexpr int kThreads = 192;           // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr uint32_t TMEM_COLS = 2 * BN;  // real + imaginary accumulators
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
+
+struct TcArgs {
+  CUtensorMap tmA;  // spectra tensor of the A operand
+  CUtensorMap tmB;  // spectra tensor of the B operand
+  int M, N, K, p, nparts;
+  int a_plane[2][2], a_fneg[2][2];
+  int b_plane[2][2], b_fneg[2][2];
+  uint32_t negmask[2][2];  // bit q: product q (ar.br, ai.bi, ar.bi, ai.br) is subtracted
+  float2* out;
+  long long out_hstride, out_fstride, out_rstride;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 1023u) == 0 && globaltimer() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (all >> 4), version 1 at bit 46, swizzle at bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)layout << 61;
+  return d;
+}
+
+constexpr uint32_t kLayoutSw128 = 2;
+constexpr uint32_t kLayoutSw64 = 4;
+
+// Descriptor of one bf16 part tile for the MMA at K offset k16 (0 or 1).
+//   K-major: rows of 32 bf16 (64 B, 64-byte swizzle); 8-row groups 512 B apart.
+//   MN-major: K rows of 64 bf16 (128 B, 128-byte swizzle); the two 64-wide
+//             halves of M/N are 4096 B apart, 8-row K groups 1024 B apart.
+template <bool MN_MAJOR>
+__device__ __forceinline__ uint64_t part_desc(uint32_t tile, int k16) {
+  if (MN_MAJOR) return smem_desc(tile + (uint32_t)k16 * 2048u, 4096u, 1024u, kLayoutSw128);
+  return smem_desc(tile + (uint32_t)k16 * 32u, 16u, 512u, kLayoutSw64);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), negate A at bit 13, A/B major at bits 15/16,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+constexpr uint32_t kNegA = 1u << 13;
+
+struct Smem {
+  uint32_t a;        // stage s, part q tile at a + (s * nparts + q) * TILE_BYTES
+  uint32_t b;
+  uint32_t full, empty, acc_full, mma_done;  // mbarrier addresses (8 B each)
+};
+
+template <bool A_MN, bool B_MN, int NP>
+__global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_constant__ TcArgs args) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ int abort_flag;
+
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  Smem S;
+  S.a = base;
+  S.b = base + STAGES * NP * TILE_BYTES;
+  const uint32_t bars = S.b + STAGES * NP * TILE_BYTES;
+  S.full = bars;
+  S.empty = bars + 8 * STAGES;
+  S.acc_full = bars + 16 * STAGES;
+  S.mma_done = S.acc_full + 8;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nt = blockIdx.x;
+  const int mt = blockIdx.y;
+  const int f = blockIdx.z >> 1;
+  const int h = blockIdx.z & 1;
+  const int p = args.p;
+  const int nkb = (args.K + BK - 1) / BK;
+  const int total = 2 * nkb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(S.full + 8 * s, 1);
+      mbar_init(S.empty + 8 * s, 1);
+    }
+    mbar_init(S.acc_full, 1);
+    mbar_init(S.mma_done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&args.tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&args.tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < total; ++it) {
+        const int kh = it / nkb;
+        const int kb = it - kh * nkb;
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(S.empty + 8 * s, ph ^ 1u)) {
+          atomicExch(args.err, QTP_DEVERR_TIMEOUT_EMPTY);
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int*)&abort_flag) break;
+        mbar_expect_tx(S.full + 8 * s, (uint32_t)(2 * NP * TILE_BYTES));
+        const int ga = args.a_fneg[h][kh] ? (p - f) % p : f;
+        const int gb = args.b_fneg[h][kh] ? (p - f) % p : f;
+        const int k0 = kb * BK;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const uint32_t ta = S.a + (uint32_t)(s * NP + q) * TILE_BYTES;
+          const uint32_t tb = S.b + (uint32_t)(s * NP + q) * TILE_BYTES;
+          const int ca = args.a_plane[h][kh] * NP + q;
+          const int cb = args.b_plane[h][kh] * NP + q;
+          if (A_MN) {
+            tma_load_4d(ta, &args.tmA, S.full + 8 * s, mt * BM, k0, ga, ca);
+            tma_load_4d(ta + 4096u, &args.tmA, S.full + 8 * s, mt * BM + 64, k0, ga, ca);
+          } else {
+            tma_load_4d(ta, &args.tmA, S.full + 8 * s, k0, mt * BM, ga, ca);
+          }
+          if (B_MN) {
+            tma_load_4d(tb, &args.tmB, S.full + 8 * s, nt * BN, k0, gb, cb);
+            tma_load_4d(tb + 4096u, &args.tmB, S.full + 8 * s, nt * BN + 64, k0, gb, cb);
+          } else {
+            tma_load_4d(tb, &args.tmB, S.full + 8 * s, k0, nt * BN, gb, cb);
+          }
+        }
+        issued = it + 1;
+      }
+      // Never leave with copies in flight: wait (bounded) for the last stages issued.
+      if (*(volatile int*)&abort_flag) {
+        for (int it = issued - STAGES < 0 ? 0 : issued - STAGES; it < issued; ++it)
+          mbar_wait(S.full + 8 * (it % STAGES), (uint32_t)(it / STAGES) & 1u);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(A_MN, B_MN);
+      const uint32_t d_re = tmem;
+      const uint32_t d_im = tmem + (uint32_t)BN;
+      uint32_t acc_re = 0, acc_im = 0;
+      bool ok = true;
+      for (int it = 0; it < total; ++it) {
+        const int kh = it / nkb;
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(S.full + 8 * s, ph)) {
+          atomicExch(args.err, QTP_DEVERR_TIMEOUT_FULL);
+          atomicExch(&abort_flag, 1);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t neg = args.negmask[h][kh];
+        const uint32_t ta = S.a + (uint32_t)(s * NP) * TILE_BYTES;
+        const uint32_t tb = S.b + (uint32_t)(s * NP) * TILE_BYTES;
+#pragma unroll
+        for (int k16 = 0; k16 < BK / 16; ++k16) {
+          // part tiles: NP == 4: re_hi, re_lo, im_hi, im_lo; NP == 2: re, im
+          const int RE = 0, IM = NP / 2;
+#pragma unroll
+          for (int prod = 0; prod < 4; ++prod) {
+            const int xa = (prod == 0 || prod == 2) ? RE : IM;  // ar, ai, ar, ai
+            const int yb = (prod == 0 || prod == 3) ? RE : IM;  // br, bi, bi, br
+            const bool to_re = prod < 2;
+            const uint32_t id = idesc | (((neg >> prod) & 1u) ? kNegA : 0u);
+            const uint32_t d = to_re ? d_re : d_im;
+            uint32_t& acc = to_re ? acc_re : acc_im;
+            const uint64_t a_hi = part_desc<A_MN>(ta + (uint32_t)xa * TILE_BYTES, k16);
+            const uint64_t b_hi = part_desc<B_MN>(tb + (uint32_t)yb * TILE_BYTES, k16);
+            mma_bf16(d, a_hi, b_hi, id, acc);
+            acc = 1;
+            if (NP == 4) {
+              const uint64_t a_lo = part_desc<A_MN>(ta + (uint32_t)(xa + 1) * TILE_BYTES, k16);
+              const uint64_t b_lo = part_desc<B_MN>(tb + (uint32_t)(yb + 1) * TILE_BYTES, k16);
+              mma_bf16(d, a_hi, b_lo, id, 1);
+              mma_bf16(d, a_lo, b_hi, id, 1);
+            }
+          }
+        }
+        mma_commit(S.empty + 8 * s);  // frees the stage when these MMAs complete
+      }
+      if (ok) {
+        mma_commit(S.acc_full);
+      } else {
+        // Unwind: wait (bounded) for MMAs already issued before freeing TMEM.
+        mma_commit(S.mma_done);
+        mbar_wait(S.mma_done, 0);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = mt * BM + q * 32 + lane;
+    bool ok = mbar_wait(S.acc_full, 0);
+    if (!ok) {
+      if (lane == 0) {
+        atomicExch(args.err, QTP_DEVERR_TIMEOUT_ACC);
+        atomicExch(&abort_flag, 1);
+      }
+    } else {
+      fence_after();
+      float2* out = args.out + (long long)h * args.out_hstride + (long long)f * args.out_fstride;
+      const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t re[32], im[32];
+        tmem_ld32(tmem + lane_off + (uint32_t)c0, re);
+        tmem_ld32(tmem + lane_off + (uint32_t)(BN + c0), im);
+        tmem_wait_ld();
+        if (row < args.M) {
+          float2* o = out + (long long)row * args.out_rstride;
+          const int col0 = nt * BN + c0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (col0 + j < args.N) o[col0 + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+          }
+        }
+      }
+    }
+    fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Spectra tensor [plane][part][f][rows][ld] as a 4-D bf16 tensor map:
+// dims (cols, rows, p, 2 * nparts); box (32, 128) for a K-major operand
+// (K = cols) and (64, 32) for an MN-major one (M or N = cols).
+bool encode_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int p, int nparts, bool mn_major,
+                char* msg, size_t msglen) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) {
+    snprintf(msg, msglen, "cuTensorMapEncodeTiled unavailable");
+    return false;
+  }
+  cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)p, (cuuint64_t)(2 * nparts)};
+  cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * rows, (cuuint64_t)ld * 2 * rows * p};
+  cuuint32_t box[4];
+  if (mn_major) {
+    box[0] = 64; box[1] = BK;
+  } else {
+    box[0] = BK; box[1] = 128;
+  }
+  box[2] = 1;
+  box[3] = 1;
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   mn_major ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    snprintf(msg, msglen, "cuTensorMapEncodeTiled failed (%d) rows=%d cols=%d ld=%d", (int)r, rows, cols, ld);
+    return false;
+  }
+  return true;
+}
+
+size_t smem_bytes(int np) { return (size_t)2 * STAGES * np * TILE_BYTES + 1024 /*align*/ + 256 /*barriers*/; }
+
+template <bool A_MN, bool B_MN, int NP>
+cudaError_t launch_kind(const TcArgs& args, dim3 grid, cudaStream_t st) {
+  auto kfn = gemm_tc_kernel<A_MN, B_MN, NP>;
+  const size_t smem = smem_bytes(NP);
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kfn<<<grid, kThreads, smem, st>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3;
+}
+
+cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, char* msg, size_t msglen) {
+  if (pr.M <= 0 || pr.N <= 0 || pr.p <= 0) return cudaSuccess;
+  if (pr.nparts != 4 && pr.nparts != 2) return cudaErrorInvalidValue;
+  const bool a_mn = pr.kind == TC_BWD_B;
+  const bool b_mn = pr.kind != TC_BWD_A;
+  TcArgs args;
+  memset(&args, 0, sizeof(args));
+  if (!encode_map(&args.tmA, pr.a_base[0], pr.a_rows[0], pr.a_cols[0], pr.a_ld[0], pr.p, pr.nparts, a_mn, msg,
+                  msglen))
+    return cudaErrorInvalidValue;
+  if (!encode_map(&args.tmB, pr.b_base[0], pr.b_rows[0], pr.b_cols[0], pr.b_ld[0], pr.p, pr.nparts, b_mn, msg,
+                  msglen))
+    return cudaErrorInvalidValue;
+  args.M = pr.M; args.N = pr.N; args.K = pr.K; args.p = pr.p; args.nparts = pr.nparts;
+  for (int h = 0; h < 2; ++h)
+    for (int kh = 0; kh < 2; ++kh) {
+      const TcView& va = pr.a[h][kh];
+      const TcView& vb = pr.b[h][kh];
+      args.a_plane[h][kh] = va.plane;
+      args.a_fneg[h][kh] = va.fneg;
+      args.b_plane[h][kh] = vb.plane;
+      args.b_fneg[h][kh] = vb.fneg;
+      // (tau ar + i tau sa ai)(br + i sb bi):
+      //   re += tau ar.br - tau sa sb ai.bi,  im += tau sb ar.bi + tau sa ai.br
+      const float tau = pr.sign[h][kh];
+      const float sa = va.conj ? -1.f : 1.f;
+      const float sb = vb.conj ? -1.f : 1.f;
+      const float c[4] = {tau, -tau * sa * sb, tau * sb, tau * sa};
+      uint32_t mask = 0;
+      for (int q = 0; q < 4; ++q)
+        if (c[q] < 0) mask |= 1u << q;
+      args.negmask[h][kh] = mask;
+    }
+  args.out = pr.out;
+  args.out_hstride = pr.out_hstride;
+  args.out_fstride = pr.out_fstride;
+  args.out_rstride = pr.out_rstride;
+  args.err = d_err;
+  dim3 grid((pr.N + BN - 1) / BN, (pr.M + BM - 1) / BM, 2 * pr.p);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+  const bool x3 = pr.nparts == 4;
+  switch (pr.kind) {
+    case TC_FWD: return x3 ? launch_kind<false, true, 4>(args, grid, st) : launch_kind<false, true, 2>(args, grid, st);
+    case TC_BWD_A: return x3 ? launch_kind<false, false, 4>(args, grid, st) : launch_kind<false, false, 2>(args, grid, st);
+    case TC_BWD_B: return x3 ? launch_kind<true, true, 4>(args, grid, st) : launch_kind<true, true, 2>(args, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace qtp

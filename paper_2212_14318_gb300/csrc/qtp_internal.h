@@ -1,0 +1,132 @@
+// Internal declarations of libqtp (CUDA sources only; not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qtp.h"
+
+#define QTP_MAX_P 4096
+#define QTP_MAX_RADIX_STAGES 16
+
+// Error codes written to a plan's device error word by bounded waits.
+#define QTP_DEVERR_TIMEOUT_FULL 1   // consumer gave up waiting for a TMA stage
+#define QTP_DEVERR_TIMEOUT_EMPTY 2  // producer gave up waiting for a free stage
+#define QTP_DEVERR_TIMEOUT_ACC 3    // epilogue gave up waiting for the accumulator
+
+namespace qtp {
+
+// Output formats of the forward tube FFT (Alg. 5.1 Step 1).
+enum SpecFormat : int {
+  FMT_C32 = 0,     // complex FP32, [plane][f][row][ld]
+  FMT_BF16X3 = 1,  // 4 bf16 parts (re_hi, re_lo, im_hi, im_lo), [plane][part][f][row][ld]
+  FMT_BF16 = 2,    // 2 bf16 parts (re, im), [plane][part][f][row][ld]
+};
+
+inline int spec_parts(int fmt) { return fmt == FMT_BF16X3 ? 4 : (fmt == FMT_BF16 ? 2 : 1); }
+inline int spec_elem_bytes(int fmt) { return fmt == FMT_C32 ? 8 : 2; }
+
+// Radix plan of a length-p transform: p = prod(radix[i]).
+struct RadixPlan {
+  int p;
+  int nstages;
+  int radix[QTP_MAX_RADIX_STAGES];
+};
+
+RadixPlan make_radix_plan(int p);
+
+// One tensor transformed by the forward FFT: tubes in[plane][row][col][0..p).
+struct FftFwdJob {
+  const float2* in;
+  void* out;         // spectra, format given by the launch
+  int rows, cols;    // tensor is (rows x cols x p) per plane
+  int ld;            // row stride (elements) of the spectra, >= cols
+  int nblocks;       // CTAs assigned to this job
+};
+
+// Inverse transform: spectra in[plane][f][row][col] (complex FP32, ld = cols)
+// back to tubes out[plane][row][col][0..p), scaled by 1/p.
+struct FftInvJob {
+  const float2* in;
+  float2* out;
+  int rows, cols;
+  int nblocks;
+};
+
+int fft_tubes_per_block(int p);
+
+cudaError_t launch_twiddles(float2* tw, int p, cudaStream_t st);
+cudaError_t launch_fft_fwd(const FftFwdJob* jobs, int njobs, int fmt, const RadixPlan& rp,
+                           const float2* tw, cudaStream_t st);
+cudaError_t launch_fft_inv(const FftInvJob* jobs, int njobs, const RadixPlan& rp,
+                           const float2* tw, cudaStream_t st);
+
+// ----------------------------------------------------------------------------
+// Per-frequency complex products (Alg. 5.1 Step 2), generic operand views.
+//
+// Output half h in {0,1} of frequency f is
+//   Out_h(f) = sum_{kh in {0,1}} sign[h][kh] * opA[h][kh](f) . opB[h][kh](f)
+// where opA is M x K and opB is K x N complex.  Element (r, k) of an operand
+// view at frequency f reads base[g*fstride + r*rstride + k*kstride] with
+// g = fneg ? (p - f) % p : f, conjugated when conj != 0.
+// ----------------------------------------------------------------------------
+struct CView {
+  const float2* base;
+  long long fstride, rstride, kstride;
+  int fneg, conj;
+};
+
+struct GemmProblem {
+  int M, N, K, p;
+  CView a[2][2];  // [h][kh], rows = M index
+  CView b[2][2];  // [h][kh], "rows" = N index (element (n, k) = opB(k, n))
+  float sign[2][2];
+  float2* out;    // out[h][f][row][col]
+  long long out_hstride, out_fstride, out_rstride;
+};
+
+cudaError_t launch_gemm_simt(const GemmProblem& pr, cudaStream_t st);
+
+// Tensor-core variant: operands are bf16 part planes written by the forward
+// FFT in FMT_BF16X3 / FMT_BF16.  A plane view is (tensor, plane, fneg, conj),
+// with the major-ness of each operand fixed per problem kind.
+struct TcView {
+  int tensor;     // index into TcProblem::tmap_* (0 or 1)
+  int plane;      // Cayley-Dickson half, 0 or 1
+  int fneg;       // read frequency (p - f) % p
+  int conj;       // negate the imaginary part
+};
+
+enum TcKind : int {
+  TC_FWD = 0,     // A K-major (A[f][i][j]),  B MN-major (B[f][j][c])
+  TC_BWD_A = 1,   // A K-major (G[f][i][c]),  B K-major  (B[f][j][c], k = c)
+  TC_BWD_B = 2,   // A MN-major (A[f][i][j], m = j, k = i), B MN-major (G[f][i][c])
+};
+
+struct TcProblem {
+  int kind;
+  int M, N, K, p;
+  int nparts;          // 4 (bf16x3) or 2 (bf16)
+  TcView a[2][2];
+  TcView b[2][2];
+  float sign[2][2];
+  float2* out;
+  long long out_hstride, out_fstride, out_rstride;
+  // Spectra tensors (bf16 parts): base, rows, cols, ld (elements).
+  const void* a_base[2]; int a_rows[2], a_cols[2], a_ld[2];
+  const void* b_base[2]; int b_rows[2], b_cols[2], b_ld[2];
+};
+
+bool tc_supported();
+cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, char* msg, size_t msglen);
+
+}  // namespace qtp
+
+struct qtp_plan {
+  int m, n, s, p;
+  int precision;
+  int device;
+  float2* d_tw;      // w^e = exp(-2 pi i e / p), e in [0, p)
+  int* d_err;        // device error word written by bounded waits
+  qtp::RadixPlan rp;
+};

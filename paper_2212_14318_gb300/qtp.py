@@ -1,0 +1,204 @@
+"""Thin ctypes binding of libqtp (include/qtp.h).
+
+Argument marshalling only: every step of the T-product runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors of shape (2, rows, cols, p, 2),
+dtype float32, contiguous ("tube-contiguous complex-pair planes": plane 0 is
+a + b i, plane 1 is c + d i of the quaternion a + b i + c j + d k).
+
+There is no CPU fallback: if the library is not built, or no GPU is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libqtp.so")
+
+QTP_OK = 0
+STATUS_NAMES = {0: "QTP_OK", 1: "QTP_ERR_INVALID_ARG", 2: "QTP_ERR_UNSUPPORTED", 3: "QTP_ERR_WORKSPACE",
+                4: "QTP_ERR_CUDA", 5: "QTP_ERR_TIMEOUT", 6: "QTP_ERR_INTERNAL"}
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+
+# Every function the C header declares, with (restype, argtypes).
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_sz = ctypes.c_size_t
+SIGNATURES = {
+    "qtp_plan_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, ctypes.c_uint]),
+    "qtp_plan_destroy": (_i, [_vp]),
+    "qtp_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
+    "qtp_backward_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
+    "qtp_forward": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "qtp_host_buffer_size": (_i, [_vp, ctypes.POINTER(_sz)]),
+    "qtp_forward_host": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "qtp_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "qtp_plan_sync": (_i, [_vp, _vp]),
+    "qtp_last_error": (ctypes.c_char_p, []),
+    "qtp_version": (_i, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class QtpError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libqtp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libqtp is not built ({LIB_PATH} missing); run "
+                                   "`python -m paper_2212_14318_gb300.build` or __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != QTP_OK:
+        msg = lib().qtp_last_error()
+        raise QtpError(status, where, msg.decode() if msg else "")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check_tensor(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float32")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+class Plan:
+    """A qtp_plan for C = A * B with A in Q^{m x n x p}, B in Q^{n x s x p}."""
+
+    def __init__(self, m: int, n: int, s: int, p: int, precision: str = "bf16x3"):
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {list(PRECISIONS)}")
+        self.m, self.n, self.s, self.p = m, n, s, p
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(lib().qtp_plan_create(ctypes.byref(h), m, n, s, p, PRECISIONS[precision], 0), "qtp_plan_create")
+        self._h = h
+        self._ws = None
+        self._bws = None
+
+    # ------------------------------------------------------------------ sizes
+    def _size(self, fn) -> int:
+        v = ctypes.c_size_t()
+        _check(getattr(lib(), fn)(self._h, ctypes.byref(v)), fn)
+        return int(v.value)
+
+    def workspace_size(self) -> int:
+        return self._size("qtp_workspace_size")
+
+    def backward_workspace_size(self) -> int:
+        return self._size("qtp_backward_workspace_size")
+
+    def host_buffer_size(self) -> int:
+        return self._size("qtp_host_buffer_size")
+
+    def _workspace(self, which: str, nbytes: int, device):
+        import torch
+        cur = getattr(self, which)
+        if cur is None or cur.numel() < nbytes or cur.device != device:
+            cur = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+            setattr(self, which, cur)
+        return cur
+
+    # ------------------------------------------------------------------ calls
+    def forward(self, A, B, C=None, workspace=None, stream=None):
+        import torch
+        _check_tensor(A, (2, self.m, self.n, self.p, 2), "A")
+        _check_tensor(B, (2, self.n, self.s, self.p, 2), "B")
+        if C is None:
+            C = torch.empty((2, self.m, self.s, self.p, 2), dtype=torch.float32, device=A.device)
+        _check_tensor(C, (2, self.m, self.s, self.p, 2), "C")
+        need = self.workspace_size()
+        ws = workspace if workspace is not None else self._workspace("_ws", need, A.device)
+        _check(lib().qtp_forward(self._h, _ptr(A), _ptr(B), _ptr(C), _ptr(ws), ws.numel() * ws.element_size(),
+                                 _stream(stream)), "qtp_forward")
+        return C
+
+    def forward_host(self, A_host, B_host, C_host, dev_buffer, stream=None):
+        """A, B, C are pinned CPU tensors; dev_buffer a CUDA byte tensor."""
+        for t, nm in ((A_host, "A_host"), (B_host, "B_host"), (C_host, "C_host")):
+            if t.is_cuda or not t.is_contiguous():
+                raise TypeError(f"{nm} must be a contiguous host tensor")
+        _check(lib().qtp_forward_host(self._h, _ptr(A_host), _ptr(B_host), _ptr(C_host), _ptr(dev_buffer),
+                                      dev_buffer.numel() * dev_buffer.element_size(), _stream(stream)),
+               "qtp_forward_host")
+        return C_host
+
+    def backward(self, dC, A, B, need_dA=True, need_dB=True, workspace=None, stream=None):
+        import torch
+        _check_tensor(dC, (2, self.m, self.s, self.p, 2), "dC")
+        _check_tensor(A, (2, self.m, self.n, self.p, 2), "A")
+        _check_tensor(B, (2, self.n, self.s, self.p, 2), "B")
+        dA = torch.empty_like(A) if need_dA else None
+        dB = torch.empty_like(B) if need_dB else None
+        need = self.backward_workspace_size()
+        ws = workspace if workspace is not None else self._workspace("_bws", need, A.device)
+        _check(lib().qtp_backward(self._h, _ptr(dC), _ptr(A), _ptr(B), _ptr(dA), _ptr(dB), _ptr(ws),
+                                  ws.numel() * ws.element_size(), _stream(stream)), "qtp_backward")
+        return dA, dB
+
+    def sync(self, stream=None):
+        _check(lib().qtp_plan_sync(self._h, _stream(stream)), "qtp_plan_sync")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().qtp_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_plan_cache = {}
+
+
+def plan_for(m, n, s, p, precision="bf16x3") -> Plan:
+    key = (m, n, s, p, precision)
+    pl = _plan_cache.get(key)
+    if pl is None:
+        pl = Plan(m, n, s, p, precision)
+        _plan_cache[key] = pl
+    return pl
+
+
+def tprod(A, B, precision: str = "bf16x3", stream=None):
+    """C = A * B for CUDA tensors in plane layout (2, m, n, p, 2) and (2, n, s, p, 2)."""
+    _, m, n, p, _ = A.shape
+    s = B.shape[2]
+    return plan_for(m, n, s, p, precision).forward(A, B, stream=stream)

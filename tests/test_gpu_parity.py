@@ -1,0 +1,140 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every case feeds the same seeded FP32 inputs to libqtp and (cast to FP64) to
+the oracle's definition-based T-product, then compares element by element.
+Tolerance: relative Frobenius error <= 1e-5 (FP32 outputs) and every element
+within 1e-4 * rms of the reference.
+"""
+import numpy as np
+import pytest
+
+import oracle as Q
+from paper_2212_14318_gb300 import synth
+from tests._gpu import assert_close, to_dev, to_host
+from tests._qlayout import planes_to_comp
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+ELEM_TOL = 1e-4
+PRECISIONS = ["fp32", "bf16x3"]
+
+# (m, n, s, p): edge sizes, ragged tails over several tiles, every radix path
+SHAPES = [
+    (1, 1, 1, 1), (3, 5, 7, 1), (5, 3, 4, 2), (17, 9, 13, 3), (8, 8, 8, 16), (20, 30, 40, 12),
+    (16, 16, 16, 31), (33, 65, 31, 7), (1, 70, 1, 8), (70, 1, 70, 5), (130, 40, 260, 8),
+    (40, 24, 36, 64), (13, 7, 11, 100), (64, 48, 80, 128), (9, 11, 10, 97),
+]
+
+
+def _qtp():
+    import torch
+    from paper_2212_14318_gb300 import qtp
+    assert torch.cuda.is_available()
+    return qtp
+
+
+def _inputs(m, n, s, p, seed):
+    A = synth.quat_normal(m, n, p, seed)
+    B = synth.quat_normal(n, s, p, seed + 1000)
+    return A, B
+
+
+def _oracle(A, B, cols=None):
+    Aq, Bq = planes_to_comp(A), planes_to_comp(B)
+    if cols is None:
+        return Q.tprod_def(Aq, Bq)
+    return Q.tprod_def_columns(Aq, Bq, cols)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("m,n,s,p", SHAPES)
+def test_forward_matches_oracle(precision, m, n, s, p):
+    qtp = _qtp()
+    A, B = _inputs(m, n, s, p, seed=m * 7 + n * 3 + p)
+    plan = qtp.Plan(m, n, s, p, precision)
+    C = to_host(plan.forward(to_dev(A), to_dev(B)))
+    plan.sync()
+    if p <= 32:
+        ref = _oracle(A, B)
+        assert_close(C, ref, REL_TOL, ELEM_TOL, f"{precision} {m}x{n}x{s}x{p}")
+    else:
+        cols = synth.sample_columns(s, 8)
+        ref = _oracle(A, B, cols)
+        assert_close(C[:, :, cols], ref, REL_TOL, ELEM_TOL, f"{precision} {m}x{n}x{s}x{p} cols")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_small_workload_full(precision):
+    qtp = _qtp()
+    A, B = synth.workload("small")
+    plan = qtp.Plan(8, 8, 8, 16, precision)
+    C = to_host(plan.forward(to_dev(A), to_dev(B)))
+    assert_close(C, _oracle(A, B), REL_TOL, ELEM_TOL, "small")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_video_workload_sampled_columns(precision):
+    """240x320x64 pixel-like pure quaternion A times 320x240x64 N(0,1) B; 64 sampled columns."""
+    qtp = _qtp()
+    A, B = synth.workload("video")
+    w = synth.WORKLOADS["video"]
+    plan = qtp.Plan(w["m"], w["n"], w["s"], w["p"], precision)
+    C = to_host(plan.forward(to_dev(A), to_dev(B)))
+    plan.sync()
+    cols = synth.sample_columns(w["s"], 64)
+    ref = _oracle(A, B, cols)
+    assert_close(C[:, :, cols], ref, REL_TOL, ELEM_TOL, "video")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_repeated_calls_are_identical(precision):
+    qtp = _qtp()
+    A, B = _inputs(50, 60, 70, 12, seed=5)
+    plan = qtp.Plan(50, 60, 70, 12, precision)
+    dA, dB = to_dev(A), to_dev(B)
+    C1 = to_host(plan.forward(dA, dB))
+    C2 = to_host(plan.forward(dA, dB))
+    np.testing.assert_array_equal(C1, C2)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("m,n,s,p", [(5, 4, 3, 1), (6, 9, 7, 4), (12, 10, 14, 7), (33, 17, 40, 32)])
+def test_backward_matches_oracle(precision, m, n, s, p):
+    qtp = _qtp()
+    A, B = _inputs(m, n, s, p, seed=11 + p)
+    G = synth.quat_normal(m, s, p, seed=77 + p)
+    plan = qtp.Plan(m, n, s, p, precision)
+    dA, dB = plan.backward(to_dev(G), to_dev(A), to_dev(B))
+    plan.sync()
+    Aq, Bq, Gq = planes_to_comp(A), planes_to_comp(B), planes_to_comp(G)
+    assert_close(to_host(dA), Q.tprod_def(Gq, Q.conj_transpose(Bq)), REL_TOL, ELEM_TOL, "dA")
+    assert_close(to_host(dB), Q.tprod_def(Q.conj_transpose(Aq), Gq), REL_TOL, ELEM_TOL, "dB")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_backward_single_output(precision):
+    qtp = _qtp()
+    A, B = _inputs(7, 6, 5, 6, seed=3)
+    G = synth.quat_normal(7, 5, 6, seed=4)
+    plan = qtp.Plan(7, 6, 5, 6, precision)
+    dA, dB = plan.backward(to_dev(G), to_dev(A), to_dev(B), need_dA=False)
+    assert dA is None
+    Aq, Gq = planes_to_comp(A), planes_to_comp(G)
+    assert_close(to_host(dB), Q.tprod_def(Q.conj_transpose(Aq), Gq), REL_TOL, ELEM_TOL, "dB only")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_forward_host_buffers(precision):
+    import torch
+    qtp = _qtp()
+    m, n, s, p = 24, 20, 28, 16
+    A, B = _inputs(m, n, s, p, seed=9)
+    plan = qtp.Plan(m, n, s, p, precision)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.empty((2, m, s, p, 2), dtype=torch.float32).pin_memory()
+    buf = torch.empty(plan.host_buffer_size(), dtype=torch.uint8, device="cuda")
+    plan.forward_host(hA, hB, hC, buf)
+    plan.sync()
+    assert_close(hC.numpy(), _oracle(A, B), REL_TOL, ELEM_TOL, "host buffers")
