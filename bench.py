@@ -1,0 +1,425 @@
+#!/usr/bin/env python3
+"""Benchmark of the fast quaternion T-product (Algorithm 5.1) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one forward T-product C = A * B of the colour-video-shaped
+workload (A: 240 x 320 x 64 pure quaternion, pixel-like U[0,1] i/j/k parts;
+B: 320 x 240 x 64 N(0,1); FP32 storage) through the C ABI, inputs resident in
+HBM, L2 flushed (256 MB write) before every step, each step timed with CUDA
+events on the launching stream.  Metric: effective TFLOP/s counting the
+fast-route work, 32 m n s p (Thm 5.2) + 5 p log2(p) per complex tube
+transform x 2 (mn + ns + ms) transforms.  Split-BF16 (bf16x3) products are
+the main path; the plain FP32 path on the same workload is reported beside
+it, with the relative error of both against the FP64 oracle on sampled
+entries.  For N > 1 (torchrun) every rank runs its own replica (the products
+are independent; no collective on the data path): weak scaling, value = total
+work of all ranks / max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle (Definition 2.3) on the host
+cores on a bounded sample of the same workload each step (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "T-product effective TFLOP/s, % roofline; mixed-prec vs FP32 at rel err<=1e-5"
+UNIT = "TFLOP/s"
+WORKLOAD = "video"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "bf16"])
+    ap.add_argument("--fp32-steps", type=int, default=100, help="steps of the plain FP32 comparison leg")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    return ap.parse_args()
+
+
+def dims():
+    from paper_2212_14318_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    return w["m"], w["n"], w["s"], w["p"]
+
+
+def effective_flops(m, n, s, p):
+    return 32.0 * m * n * s * p + 10.0 * p * math.log2(p) * (m * n + n * s + m * s) if p > 1 else 32.0 * m * n * s
+
+
+def workload_desc():
+    m, n, s, p = dims()
+    return (f"colour-video T-product: A {m}x{n}x{p} pure quaternion (pixel-like, i/j/k ~ U[0,1]) * "
+            f"B {n}x{s}x{p} N(0,1), FP32 storage")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- oracle legs
+
+
+def oracle_inputs():
+    import numpy as np
+    from paper_2212_14318_gb300 import synth
+    A, B = synth.workload(WORKLOAD)
+
+    def comp(x):
+        x = np.asarray(x, dtype=np.float64)
+        return np.stack([x[0, ..., 0], x[0, ..., 1], x[1, ..., 0], x[1, ..., 1]])
+    return A, B, comp(A), comp(B)
+
+
+def oracle_entries_rate(Aq, Bq, count, seed):
+    """Time the oracle on `count` random entries C(i, t, k); return (seconds, entries)."""
+    import oracle as Q
+    from paper_2212_14318_gb300 import synth
+    m, n, s, p = dims()
+    ii, tt, kk = synth.sample_positions(m, s, p, count, seed=seed)
+    t0 = time.perf_counter()
+    Q.tprod_def_entries(Aq, Bq, ii, tt, kk)
+    return time.perf_counter() - t0, count
+
+
+def cpu_baseline(Aq, Bq, budget_s=15.0):
+    """Oracle (definition, FP64 NumPy) on a bounded sample: whole lateral columns."""
+    import oracle as Q
+    from paper_2212_14318_gb300 import synth
+    m, n, s, p = dims()
+    cols = list(synth.sample_columns(s, s))
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(cols):
+        Q.tprod_def_columns(Aq, Bq, [cols[done]])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    full_s = dt * s / done
+    return {
+        "value": effective_flops(m, n, s, p) / full_s / 1e12,
+        "unit": UNIT,
+        "cores": cores_used(),
+        "kind": "oracle",
+        "sample": f"{done} of {s} lateral columns C(:,t,:) by Definition 2.3 (FP64 NumPy) in {dt:.1f} s; "
+                  f"full product extrapolated to {full_s:.0f} s",
+    }
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- traffic record
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2212_14318_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2212_14318_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(stage):
+    """DRAM bytes per launch from the committed ncu record, if the sources have not changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if rec.get("source_digest") != kernel_source_digest():
+        return None
+    ent = rec.get("stages", {}).get(stage)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------- ours
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2212_14318_gb300 import qtp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    m, n, s, p = dims()
+    A_np, B_np, Aq, Bq = oracle_inputs() if rank == 0 else (None, None, None, None)
+    if rank != 0:
+        from paper_2212_14318_gb300 import synth
+        A_np, B_np = synth.workload(WORKLOAD)
+    A = torch.from_numpy(A_np).to(dev)
+    B = torch.from_numpy(B_np).to(dev)
+    C = torch.empty((2, m, s, p, 2), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flops = effective_flops(m, n, s, p)
+
+    def timed_leg(precision, steps, warmup, trace):
+        plan = qtp.Plan(m, n, s, p, precision)
+        if trace:
+            plan.set_tracing(True)
+        for _ in range(warmup):
+            plan.forward(A, B, C)
+        plan.sync()
+        stage_ms = [0.0, 0.0, 0.0]
+        step_ms = []
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record()
+            plan.forward(A, B, C)
+            evs[i][1].record()
+            if trace:
+                st = plan.stage_times()
+                for j in range(3):
+                    stage_ms[j] += st[j]
+        barrier()
+        plan.sync()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        return plan, sum(step_ms), stage_ms
+
+    # main leg (split-BF16 by default)
+    sampler = ClockSampler(local)
+    sampler.start()
+    plan, total_ms, stage_ms = timed_leg(args.precision, args.steps, args.warmup, trace=True)
+    clocks = sampler.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * flops / (ms_per_step * 1e-3) / 1e12
+
+    # accuracy of the main leg on sampled entries (FP64 oracle)
+    def sampled_rel_err(Cdev):
+        import oracle as Q
+        from paper_2212_14318_gb300 import synth
+        ii, tt, kk = synth.sample_positions(m, s, p, 1000, seed=11)
+        ref = Q.tprod_def_entries(Aq, Bq, ii, tt, kk)
+        Ch = Cdev.cpu().numpy().astype(np.float64)
+        got = np.stack([Ch[0, ii, tt, kk, 0], Ch[0, ii, tt, kk, 1], Ch[1, ii, tt, kk, 0], Ch[1, ii, tt, kk, 1]])
+        return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    out = {}
+    if rank == 0:
+        plan.forward(A, B, C)
+        plan.sync()
+        out["rel_err"] = sampled_rel_err(C)
+
+    # plain FP32 GPU path on the same workload (context for the mixed-precision claim)
+    fp32_plan, fp32_ms, fp32_stage = timed_leg("fp32", args.fp32_steps, 3, trace=True)
+    fp32 = {"ms_per_step": fp32_ms / args.fp32_steps,
+            "value": flops / (fp32_ms / args.fp32_steps * 1e-3) / 1e12,
+            "products_ms": fp32_stage[1] / args.fp32_steps}
+    if rank == 0:
+        fp32_plan.forward(A, B, C)
+        fp32_plan.sync()
+        fp32["rel_err"] = sampled_rel_err(C)
+    del fp32_plan
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    hA = torch.from_numpy(A_np).pin_memory()
+    hB = torch.from_numpy(B_np).pin_memory()
+    hC = torch.empty((2, m, s, p, 2), dtype=torch.float32).pin_memory()
+    dbuf = torch.empty(plan.host_buffer_size(), dtype=torch.uint8, device=dev)
+    plan.set_tracing(False)
+    for _ in range(3):
+        plan.forward_host(hA, hB, hC, dbuf)
+    plan.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record()
+    for _ in range(args.e2e_steps):
+        plan.forward_host(hA, hB, hC, dbuf)
+    e1.record()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+
+    if rank == 0:
+        peaks, peak_src = load_peaks()
+        st = [x / args.steps for x in stage_ms]   # ms per launch
+        alg_flops_issued = (3.0 if args.precision == "bf16x3" else 1.0) * 32.0 * m * n * s * p
+        bytes_s1 = 32.0 * p * (m * n + n * s)      # read 16 B + write 16 B per quaternion entry
+        bytes_s3 = 32.0 * p * (m * s)
+        hbm = peaks["hbm_gbs"]
+        tc_peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        stages = {
+            "fft_forward": {"ms": st[0], "bound": "hbm", "achieved": bytes_s1 / (st[0] * 1e-3) / 1e9,
+                            "peak": hbm, "unit": "GB/s", "traffic": recorded_traffic("fft_forward")},
+            "products": {"ms": st[1], "bound": "tensor", "achieved": alg_flops_issued / (st[1] * 1e-3) / 1e12,
+                         "peak": tc_peak, "unit": "TFLOP/s", "traffic": recorded_traffic("products")},
+            "fft_inverse": {"ms": st[2], "bound": "hbm", "achieved": bytes_s3 / (st[2] * 1e-3) / 1e9,
+                            "peak": hbm, "unit": "GB/s", "traffic": recorded_traffic("fft_inverse")},
+        }
+        for v in stages.values():
+            v["frac"] = v["achieved"] / v["peak"]
+        dom = max(stages, key=lambda k: stages[k]["ms"])
+        roof = dict(stages[dom])
+        roof.pop("ms")
+        roof["kernel"] = dom
+        roof["peak_source"] = f"{peak_src} ({'bf16_tflops_sustained' if roof['bound'] == 'tensor' else 'hbm_gbs'})"
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16x3": "bf16x3+f32", "bf16": "bf16+f32", "fp32": "f32"}[args.precision],
+            "data": "synthetic (seeded)",
+            "config": {"workload": workload_desc(), "m": m, "n": n, "s": s, "p": p,
+                       "precision": args.precision, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "rel_err": out["rel_err"],
+            "roofline": roof,
+            "stages": stages,
+            "fp32_path": fp32,
+            "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+                    "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(A.numel() * 4 + B.numel() * 4),
+                    "d2h_bytes_per_step": int(C.numel() * 4)},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(Aq, Bq)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    m, n, s, p = dims()
+    _, _, Aq, Bq = oracle_inputs()
+    # per-step sample sized so that warmup + steps end within ~3 minutes
+    per_step_budget = max(0.01, min(5.0, 150.0 / max(1, args.steps + args.warmup)))
+    dt, cnt = oracle_entries_rate(Aq, Bq, 32, seed=100)
+    per_entry = dt / cnt
+    entries = max(1, int(per_step_budget / per_entry))
+    for w in range(args.warmup):
+        oracle_entries_rate(Aq, Bq, entries, seed=200 + w)
+    total = 0.0
+    for k in range(args.steps):
+        d, _ = oracle_entries_rate(Aq, Bq, entries, seed=1000 + k)
+        total += d
+    sec_per_step = total / args.steps
+    full_s = sec_per_step * (m * s * p) / entries
+    value = effective_flops(m, n, s, p) / full_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
+        "config": {"workload": workload_desc(), "m": m, "n": n, "s": s, "p": p},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores_used(),
+                         "sample": f"{entries} random entries C(i,t,k) per step by Definition 2.3 (FP64 NumPy); "
+                                   f"full product extrapolated to {full_s:.0f} s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -136,6 +136,15 @@ QTP_API qtp_status qtp_backward(const qtp_plan* plan, const float* dC, const flo
  * last call, QTP_ERR_CUDA if the stream reports an error, else QTP_OK. */
 QTP_API qtp_status qtp_plan_sync(const qtp_plan* plan, void* stream);
 
+/* Tracing.  While enabled, every qtp_forward / qtp_forward_host /
+ * qtp_backward call records four CUDA events on its stream: before Step 1,
+ * after Step 1 (tube FFTs), after Step 2 (per-frequency products) and after
+ * Step 3 (inverse FFTs).  qtp_plan_stage_times waits for the events of the
+ * last traced call and writes the three stage durations (ms) to ms3[0..2].
+ * Enabling creates the events (no device memory); disabling destroys them. */
+QTP_API qtp_status qtp_plan_set_tracing(qtp_plan* plan, int enable);
+QTP_API qtp_status qtp_plan_stage_times(const qtp_plan* plan, float* ms3);
+
 /* Thread-local description of the last failure in this thread ("" if none). */
 QTP_API const char* qtp_last_error(void);
 

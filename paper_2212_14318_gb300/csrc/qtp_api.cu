@@ -292,6 +292,10 @@ qtp_status run_products_bwd(const qtp_plan* pl, const void* sa, const void* sb, 
   return QTP_OK;
 }
 
+void trace(const qtp_plan* pl, int i, cudaStream_t st) {
+  if (pl->tracing) cudaEventRecord(pl->ev[i], st);
+}
+
 qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, float* C, char* ws,
                         cudaStream_t st) {
   const int fmt = spec_format(pl->precision);
@@ -305,15 +309,19 @@ qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, floa
   jobs[1].out = ws + L.sb;
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
   jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p);
+  trace(pl, 0, st);
   QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "forward tube FFT");
+  trace(pl, 1, st);
   qtp_status r = run_products_fwd(pl, ws + L.sa, ws + L.sb, (float2*)(ws + L.sc), st);
   if (r != QTP_OK) return r;
+  trace(pl, 2, st);
   FftInvJob ij;
   ij.in = (const float2*)(ws + L.sc);
   ij.out = (float2*)C;
   ij.rows = pl->m; ij.cols = pl->s;
   ij.nblocks = nblocks_for(pl->m, pl->s, pl->p);
   QTP_CUDA(launch_fft_inv(&ij, 1, pl->rp, pl->d_tw, st), "inverse tube FFT");
+  trace(pl, 3, st);
   return QTP_OK;
 }
 
@@ -347,6 +355,7 @@ qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int preci
   pl->rp = make_radix_plan(p);
   pl->d_tw = nullptr;
   pl->d_err = nullptr;
+  pl->tracing = 0;
   cudaError_t e = cudaGetDevice(&pl->device);
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_tw, sizeof(float2) * p);
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_err, sizeof(int));
@@ -365,6 +374,7 @@ qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int preci
 
 qtp_status qtp_plan_destroy(qtp_plan* pl) {
   if (!pl) return QTP_OK;
+  qtp_plan_set_tracing(pl, 0);
   cudaFree(pl->d_tw);
   cudaFree(pl->d_err);
   delete pl;
@@ -467,6 +477,7 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
   jobs[1].out = ws + L.sb;
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
   jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p);
+  trace(pl, 0, st);
   QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "backward FFT of A, B");
   FftFwdJob gj;
   gj.in = (const float2*)dC;
@@ -474,10 +485,12 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
   gj.rows = pl->m; gj.cols = pl->s; gj.ld = (int)spec_ld(fmt, pl->s);
   gj.nblocks = nblocks_for(pl->m, pl->s, pl->p);
   QTP_CUDA(launch_fft_fwd(&gj, 1, fmt, pl->rp, pl->d_tw, st), "backward FFT of dC");
+  trace(pl, 1, st);
   // Step 2.
   r = run_products_bwd(pl, ws + L.sa, ws + L.sb, ws + L.sg, dA ? (float2*)(ws + L.sda) : nullptr,
                        dB ? (float2*)(ws + L.sdb) : nullptr, st);
   if (r != QTP_OK) return r;
+  trace(pl, 2, st);
   // Step 3 on dA and dB.
   FftInvJob ij[2];
   int nj = 0;
@@ -496,6 +509,30 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
     ++nj;
   }
   QTP_CUDA(launch_fft_inv(ij, nj, pl->rp, pl->d_tw, st), "backward inverse FFT");
+  trace(pl, 3, st);
+  return QTP_OK;
+}
+
+qtp_status qtp_plan_set_tracing(qtp_plan* pl, int enable) {
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if (enable && !pl->tracing) {
+    for (int i = 0; i < 4; ++i) QTP_CUDA(cudaEventCreate(&pl->ev[i]), "create trace event");
+    pl->tracing = 1;
+  } else if (!enable && pl->tracing) {
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(pl->ev[i]);
+    pl->tracing = 0;
+  }
+  return QTP_OK;
+}
+
+qtp_status qtp_plan_stage_times(const qtp_plan* pl, float* ms3) {
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if (!ms3) return fail(QTP_ERR_INVALID_ARG, "ms3 is NULL");
+  if (!pl->tracing) return fail(QTP_ERR_INVALID_ARG, "tracing is not enabled on this plan");
+  QTP_CUDA(cudaEventSynchronize(pl->ev[3]), "wait for trace events");
+  for (int i = 0; i < 3; ++i) QTP_CUDA(cudaEventElapsedTime(&ms3[i], pl->ev[i], pl->ev[i + 1]), "stage time");
   return QTP_OK;
 }
 

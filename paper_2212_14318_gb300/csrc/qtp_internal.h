@@ -129,4 +129,6 @@ struct qtp_plan {
   float2* d_tw;      // w^e = exp(-2 pi i e / p), e in [0, p)
   int* d_err;        // device error word written by bounded waits
   qtp::RadixPlan rp;
+  int tracing;
+  cudaEvent_t ev[4];  // stage boundaries of the last traced call
 };

@@ -36,6 +36,8 @@ SIGNATURES = {
     "qtp_forward_host": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_plan_sync": (_i, [_vp, _vp]),
+    "qtp_plan_set_tracing": (_i, [_vp, _i]),
+    "qtp_plan_stage_times": (_i, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "qtp_last_error": (ctypes.c_char_p, []),
     "qtp_version": (_i, []),
 }
@@ -169,6 +171,15 @@ class Plan:
         _check(lib().qtp_backward(self._h, _ptr(dC), _ptr(A), _ptr(B), _ptr(dA), _ptr(dB), _ptr(ws),
                                   ws.numel() * ws.element_size(), _stream(stream)), "qtp_backward")
         return dA, dB
+
+    def set_tracing(self, enable: bool = True):
+        _check(lib().qtp_plan_set_tracing(self._h, 1 if enable else 0), "qtp_plan_set_tracing")
+
+    def stage_times(self):
+        """Durations (ms) of Steps 1, 2, 3 of the last traced call."""
+        buf = (ctypes.c_float * 3)()
+        _check(lib().qtp_plan_stage_times(self._h, buf), "qtp_plan_stage_times")
+        return [float(x) for x in buf]
 
     def sync(self, stream=None):
         _check(lib().qtp_plan_sync(self._h, _stream(stream)), "qtp_plan_sync")
