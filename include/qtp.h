@@ -145,6 +145,32 @@ QTP_API qtp_status qtp_plan_sync(const qtp_plan* plan, void* stream);
 QTP_API qtp_status qtp_plan_set_tracing(qtp_plan* plan, int enable);
 QTP_API qtp_status qtp_plan_stage_times(const qtp_plan* plan, float* ms3);
 
+/* C = A * B, exactly as qtp_forward, for callers that may not allocate device
+ * memory (the paper has no counterpart; this is a property of the library).
+ * Some host programs cannot call cudaMalloc: their device memory belongs to
+ * another allocator (a framework's caching pool, a fixed memory budget) that
+ * must stay the only one, or they cannot afford cudaMalloc's implicit
+ * synchronisation.  Plans allocate and qtp_forward needs a workspace, so this
+ * entry point takes neither: dimensions and precision are passed directly, and
+ * the twiddle table, error word and spectra live in one static device array
+ * of QTP_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading the library
+ * holds until the process exits.  A, B and C are the caller's device tensors
+ * (layout as above).  It calls no cudaMalloc, cudaFree or allocating routine.
+ * - Products whose scratch (twiddles + spectra of A, B and C, see
+ *   qtp_workspace_size) exceeds the array are rejected with
+ *   QTP_ERR_WORKSPACE before any launch.
+ * - The first call on each device looks up the array's device address with
+ *   that device current (cudaGetSymbolAddress); make that first call before
+ *   any stream capture begins.
+ * - All calls share the one array and it keeps the last call's contents; each
+ *   call clears its error word and rewrites its twiddles.  Calls that overlap
+ *   on the GPU (other streams, other threads) race on the array: order them.
+ * - A device-side wait that gives up (see qtp_plan_sync) cannot be reported
+ *   here: there is no plan to read it from. */
+#define QTP_NOALLOC_SCRATCH_BYTES (32 << 20)
+QTP_API qtp_status qtp_forward_noalloc(int m, int n, int s, int p, int precision, const float* A,
+                                       const float* B, float* C, void* stream);
+
 /* Thread-local description of the last failure in this thread ("" if none). */
 QTP_API const char* qtp_last_error(void);
 

@@ -550,3 +550,93 @@ qtp_status qtp_plan_sync(const qtp_plan* pl, void* stream) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// qtp_forward_noalloc: the forward product without any allocation.
+//
+// Some callers may not allocate device memory: a host program whose device
+// memory is owned entirely by another allocator (a framework's caching pool or
+// a fixed memory budget) must not call cudaMalloc behind that allocator's back,
+// and latency-bound code cannot afford cudaMalloc's implicit synchronisation.
+// Plan creation allocates (twiddles, error word) and qtp_forward needs a
+// caller-provided workspace, so this entry point takes neither: its twiddle
+// table, error word and spectra live in one file-scope device array of
+// QTP_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library holds
+// until the process exits.
+// ----------------------------------------------------------------------------
+#include <mutex>
+
+#define QTP_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QTP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[QTP_NOALLOC_MAX_DEVICES];
+
+// Device address of the static array on the current device.  In host code the
+// array's name only stands for it, so the address is looked up once per
+// device, with that device current, and cached.
+qtp_status noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= QTP_NOALLOC_MAX_DEVICES)
+    return fail(QTP_ERR_UNSUPPORTED, "device %d is beyond the %d devices qtp_forward_noalloc tracks", dev,
+                QTP_NOALLOC_MAX_DEVICES);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch array");
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QTP_OK;
+}
+
+}  // namespace
+
+extern "C" qtp_status qtp_forward_noalloc(int m, int n, int s, int p, int precision, const float* A,
+                                          const float* B, float* C, void* stream) {
+  g_err[0] = 0;
+  if (m < 1 || n < 1 || s < 1 || p < 1)
+    return fail(QTP_ERR_INVALID_ARG, "dimensions must be >= 1 (m=%d n=%d s=%d p=%d)", m, n, s, p);
+  if (m > (1 << 20) || n > (1 << 20) || s > (1 << 20))
+    return fail(QTP_ERR_INVALID_ARG, "m, n, s must be <= 2^20");
+  if (p > QTP_MAX_P) return fail(QTP_ERR_UNSUPPORTED, "p=%d exceeds the supported maximum %d", p, QTP_MAX_P);
+  if (precision != QTP_PREC_FP32 && precision != QTP_PREC_BF16X3 && precision != QTP_PREC_BF16)
+    return fail(QTP_ERR_INVALID_ARG, "unknown precision %d", precision);
+  qtp_plan pl;
+  memset(&pl, 0, sizeof(pl));
+  pl.m = m; pl.n = n; pl.s = s; pl.p = p;
+  pl.precision = precision;
+  pl.rp = make_radix_plan(p);
+  // static scratch: [twiddles][error word][forward workspace]
+  const size_t tw_bytes = align256((size_t)p * sizeof(float2));
+  const size_t ws_off = tw_bytes + 256;
+  const size_t need = ws_off + fwd_layout(&pl).total;
+  if (need > (size_t)QTP_NOALLOC_SCRATCH_BYTES)
+    return fail(QTP_ERR_WORKSPACE,
+                "this product needs %zu bytes of scratch; qtp_forward_noalloc's static array holds %d bytes",
+                need, QTP_NOALLOC_SCRATCH_BYTES);
+  qtp_status r;
+  if ((r = check_dev_ptr(A, "A")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(B, "B")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(C, "C")) != QTP_OK) return r;
+  if (precision != QTP_PREC_FP32 && !tc_supported())
+    return fail(QTP_ERR_UNSUPPORTED, "BF16 tensor-core products need an sm_103 device (tcgen05)");
+  void* scratch = nullptr;
+  if ((r = noalloc_scratch(&scratch)) != QTP_OK) return r;
+  QTP_CUDA(cudaGetDevice(&pl.device), "cudaGetDevice");
+  char* base = (char*)scratch;
+  pl.d_tw = (float2*)base;
+  pl.d_err = (int*)(base + tw_bytes);
+  cudaStream_t st = as_stream(stream);
+  // The array keeps the previous call's contents: the error word must start at
+  // zero and the twiddles may belong to another p, so both are rewritten here.
+  QTP_CUDA(cudaMemsetAsync(pl.d_err, 0, sizeof(int), st), "clear the error word");
+  QTP_CUDA(launch_twiddles(pl.d_tw, p, st), "twiddles");
+  return forward_impl(&pl, A, B, C, base + ws_off, st);
+}

@@ -38,6 +38,7 @@ SIGNATURES = {
     "qtp_plan_sync": (_i, [_vp, _vp]),
     "qtp_plan_set_tracing": (_i, [_vp, _i]),
     "qtp_plan_stage_times": (_i, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "qtp_forward_noalloc": (_i, [_i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "qtp_last_error": (ctypes.c_char_p, []),
     "qtp_version": (_i, []),
 }
@@ -206,6 +207,28 @@ def plan_for(m, n, s, p, precision="bf16x3") -> Plan:
         pl = Plan(m, n, s, p, precision)
         _plan_cache[key] = pl
     return pl
+
+
+def forward_noalloc(A, B, C=None, precision: str = "bf16x3", stream=None):
+    """C = A * B through qtp_forward_noalloc: no plan and no workspace.
+
+    For callers that may not allocate device memory (another allocator owns
+    it, or cudaMalloc's synchronisation is unaffordable); the library keeps a
+    32 MiB static device array for the scratch instead.  Only C may be
+    allocated here, and only when the caller passes none.  Calls that overlap
+    on the GPU share that array and race; order them.
+    """
+    import torch
+    _, m, n, p, _ = A.shape
+    s = B.shape[2]
+    _check_tensor(A, (2, m, n, p, 2), "A")
+    _check_tensor(B, (2, n, s, p, 2), "B")
+    if C is None:
+        C = torch.empty((2, m, s, p, 2), dtype=torch.float32, device=A.device)
+    _check_tensor(C, (2, m, s, p, 2), "C")
+    _check(lib().qtp_forward_noalloc(m, n, s, p, PRECISIONS[precision], _ptr(A), _ptr(B), _ptr(C),
+                                     _stream(stream)), "qtp_forward_noalloc")
+    return C
 
 
 def tprod(A, B, precision: str = "bf16x3", stream=None):
