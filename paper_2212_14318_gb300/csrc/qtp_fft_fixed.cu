@@ -1,0 +1,365 @@
+// Tube FFTs of Algorithm 5.1 (Steps 1 and 3) specialised for a compile-time
+// tube length P (the lengths of the workloads: 8, 12, 16, 31, 32, 64, 100,
+// 128).  Same data flow as the generic kernels in qtp_fft.cu - contiguous
+// tube loads, Stockham stages in shared memory at an odd tube stride,
+// frequency-major stores with the bf16 hi/lo split fused in - but with the
+// radix plan, tube count per CTA and every index computation known to the
+// compiler, so a stage is a handful of shared-memory accesses plus the
+// butterfly arithmetic instead of runtime integer divisions.  When the tensor
+// has an even number of columns, two neighbouring tubes are stored (and, in the
+// inverse, gathered) together: 16-byte complex pairs or 4-byte bf16 pairs.
+#include "qtp_fft_common.cuh"
+#include "qtp_internal.h"
+
+namespace qtp {
+
+namespace {
+
+using namespace fftdev;
+
+constexpr int kThreads = 256;
+
+struct Radices {
+  int n;
+  int r[12];
+};
+
+// Greedy factorisation of P: radix 8 first, then 4, 2, then odd primes.
+__host__ __device__ constexpr Radices radices_of(int p) {
+  Radices rl{0, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}};
+  int q = p;
+  while (q % 8 == 0) { rl.r[rl.n++] = 8; q /= 8; }
+  if (q % 4 == 0) { rl.r[rl.n++] = 4; q /= 4; }
+  if (q % 2 == 0) { rl.r[rl.n++] = 2; q /= 2; }
+  for (int f = 3; q > 1; f += 2)
+    while (q % f == 0) { rl.r[rl.n++] = f; q /= f; }
+  return rl;
+}
+
+// Tubes per CTA: about 4.5 K complex per buffer, a multiple of 32 tubes.
+__host__ __device__ constexpr int tubes_for(int p) {
+  int t = 4608 / (p | 1);
+  if (t > 512) t = 512;
+  if (t >= 32) t = t / 32 * 32;
+  return t < 2 ? 2 : t;
+}
+
+template <int P>
+constexpr size_t smem_for() {
+  return (size_t)2 * tubes_for(P) * (P | 1) * sizeof(float2) + (size_t)tubes_for(P) * sizeof(long long);
+}
+
+// Radix-R Stockham butterfly j of one tube, Ns = length already transformed.
+template <int R, int NS, int P, bool INV>
+__device__ __forceinline__ void bfly(const float2* __restrict__ in, float2* __restrict__ out, int j,
+                                     const float2* __restrict__ tw) {
+  constexpr int stride = P / R;
+  constexpr int twstep = P / (NS * R);
+  const int k = j % NS;
+  const int base = (j / NS) * NS * R + k;
+  if constexpr (R <= 8) {
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      v[r] = in[j + r * stride];
+      if (NS > 1 && r > 0) v[r] = cmul(v[r], twid<INV>(tw, r * k * twstep));
+    }
+    Dft<R, INV>::run(v, tw, P);
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[base + r * NS] = v[r];
+  } else {
+    // prime radix > 8: direct DFT of length R from shared memory
+#pragma unroll 1
+    for (int u = 0; u < R; ++u) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        float2 x = in[j + r * stride];
+        if (NS > 1 && r > 0) x = cmul(x, twid<INV>(tw, r * k * twstep));
+        const int e = ((r * u) % R) * stride;
+        acc = cadd(acc, cmul(x, twid<INV>(tw, e)));
+      }
+      out[base + u * NS] = acc;
+    }
+  }
+}
+
+// Stages ST.. of the plan over the CTA's tubes; returns the buffer holding the result.
+template <int P, int ST, int NS, bool INV>
+__device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const float2* __restrict__ tw) {
+  constexpr Radices RL = radices_of(P);
+  if constexpr (ST == RL.n) {
+    return in;
+  } else {
+    constexpr int R = RL.r[ST];
+    constexpr int NB = P / R;
+    constexpr int T = tubes_for(P);
+    constexpr int PP = P | 1;
+    // tube-fastest: consecutive threads take consecutive tubes (odd stride PP: no bank conflicts)
+    for (int idx = threadIdx.x; idx < T * NB; idx += kThreads) {
+      const int j = idx / T;
+      const int tube = idx - j * T;
+      if (tube < Tb) bfly<R, NS, P, INV>(in + tube * PP, out + tube * PP, j, tw);
+    }
+    __syncthreads();
+    return stages<P, ST + 1, NS * R, INV>(out, in, Tb, tw);
+  }
+}
+
+template <int P, int FMT>
+__global__ void __launch_bounds__(kThreads) fft_fwd_fixed(FftFwdJob job0, FftFwdJob job1, int njobs,
+                                                          const float2* __restrict__ tw) {
+  constexpr int T = tubes_for(P);
+  constexpr int PP = P | 1;
+  constexpr int NPARTS = FMT == FMT_BF16X3 ? 4 : (FMT == FMT_BF16 ? 2 : 1);
+  extern __shared__ float4 smem_f4[];
+  float2* buf0 = reinterpret_cast<float2*>(smem_f4);
+  float2* buf1 = buf0 + T * PP;
+  long long* tube_off = reinterpret_cast<long long*>(buf1 + T * PP);
+
+  int b = blockIdx.x;
+  const bool second = njobs > 1 && b >= job0.nblocks;
+  const FftFwdJob& job = second ? job1 : job0;
+  if (second) b -= job0.nblocks;
+  const long long per_plane = (long long)job.rows * job.cols;
+  const long long ntubes = 2 * per_plane;
+  const long long t0 = (long long)b * T;
+  if (t0 >= ntubes) return;
+  const int Tb = (int)min((long long)T, ntubes - t0);
+
+  // contiguous load of the CTA's tubes
+  const float2* src = job.in + t0 * P;
+  if constexpr (P % 2 == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (int i = threadIdx.x; i < Tb * (P / 2); i += kThreads) {
+      const float4 v = __ldg(s4 + i);
+      const int tube = (2 * i) / P;
+      const int k = 2 * i - tube * P;
+      buf0[tube * PP + k] = make_float2(v.x, v.y);
+      buf0[tube * PP + k + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+    for (int i = threadIdx.x; i < Tb * P; i += kThreads) {
+      const int tube = i / P;
+      buf0[tube * PP + (i - tube * P)] = __ldg(src + i);
+    }
+  }
+  const long long ld = job.ld;
+  const long long slab = (long long)job.rows * ld;  // one (plane, part, f) slab
+  for (int tube = threadIdx.x; tube < Tb; tube += kThreads) {
+    const long long t = t0 + tube;
+    const long long plane = t / per_plane;
+    const long long rem = t - plane * per_plane;
+    const long long row = rem / job.cols;
+    tube_off[tube] = plane * NPARTS * P * slab + row * ld + (rem - row * job.cols);
+  }
+  __syncthreads();
+  const float2* X = stages<P, 0, 1, false>(buf0, buf1, Tb, tw);
+
+  const long long part = (long long)P * slab;
+  if ((job.cols & 1) == 0) {
+    // pairs of neighbouring tubes share a row: 16-byte / 4-byte stores
+    constexpr int TH = T / 2;
+    for (int i = threadIdx.x; i < TH * P; i += kThreads) {
+      const int f = i / TH;
+      const int tube = 2 * (i - f * TH);
+      if (tube >= Tb) continue;
+      const float2 v0 = X[tube * PP + f];
+      const float2 v1 = X[(tube + 1) * PP + f];
+      const long long o = tube_off[tube] + (long long)f * slab;
+      if constexpr (FMT == FMT_C32) {
+        *reinterpret_cast<float4*>(reinterpret_cast<float2*>(job.out) + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
+      } else if constexpr (FMT == FMT_BF16X3) {
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
+        __nv_bfloat16 rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
+        split_bf16(v0.x, rh0, rl0);
+        split_bf16(v0.y, ih0, il0);
+        split_bf16(v1.x, rh1, rl1);
+        split_bf16(v1.y, ih1, il1);
+        *reinterpret_cast<__nv_bfloat162*>(out + o) = __halves2bfloat162(rh0, rh1);
+        *reinterpret_cast<__nv_bfloat162*>(out + o + part) = __halves2bfloat162(rl0, rl1);
+        *reinterpret_cast<__nv_bfloat162*>(out + o + 2 * part) = __halves2bfloat162(ih0, ih1);
+        *reinterpret_cast<__nv_bfloat162*>(out + o + 3 * part) = __halves2bfloat162(il0, il1);
+      } else {
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
+        *reinterpret_cast<__nv_bfloat162*>(out + o) =
+            __halves2bfloat162(__float2bfloat16_rn(v0.x), __float2bfloat16_rn(v1.x));
+        *reinterpret_cast<__nv_bfloat162*>(out + o + part) =
+            __halves2bfloat162(__float2bfloat16_rn(v0.y), __float2bfloat16_rn(v1.y));
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < T * P; i += kThreads) {
+      const int f = i / T;
+      const int tube = i - f * T;
+      if (tube >= Tb) continue;
+      const float2 v = X[tube * PP + f];
+      const long long o = tube_off[tube] + (long long)f * slab;
+      if constexpr (FMT == FMT_C32) {
+        reinterpret_cast<float2*>(job.out)[o] = v;
+      } else if constexpr (FMT == FMT_BF16X3) {
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
+        __nv_bfloat16 rh, rl, ih, il;
+        split_bf16(v.x, rh, rl);
+        split_bf16(v.y, ih, il);
+        out[o] = rh;
+        out[o + part] = rl;
+        out[o + 2 * part] = ih;
+        out[o + 3 * part] = il;
+      } else {
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
+        out[o] = __float2bfloat16_rn(v.x);
+        out[o + part] = __float2bfloat16_rn(v.y);
+      }
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
+                                                          const float2* __restrict__ tw) {
+  constexpr int T = tubes_for(P);
+  constexpr int PP = P | 1;
+  extern __shared__ float4 smem_f4[];
+  float2* buf0 = reinterpret_cast<float2*>(smem_f4);
+  float2* buf1 = buf0 + T * PP;
+  long long* tube_off = reinterpret_cast<long long*>(buf1 + T * PP);
+
+  int b = blockIdx.x;
+  const bool second = njobs > 1 && b >= job0.nblocks;
+  const FftInvJob& job = second ? job1 : job0;
+  if (second) b -= job0.nblocks;
+  const long long per_plane = (long long)job.rows * job.cols;
+  const long long ntubes = 2 * per_plane;
+  const long long t0 = (long long)b * T;
+  if (t0 >= ntubes) return;
+  const int Tb = (int)min((long long)T, ntubes - t0);
+
+  for (int tube = threadIdx.x; tube < Tb; tube += kThreads) {
+    const long long t = t0 + tube;
+    const long long plane = t / per_plane;
+    tube_off[tube] = plane * P * per_plane + (t - plane * per_plane);
+  }
+  __syncthreads();
+  // frequency-major gather of C_hat[plane][f][row][col]
+  if ((job.cols & 1) == 0) {
+    constexpr int TH = T / 2;
+    for (int i = threadIdx.x; i < TH * P; i += kThreads) {
+      const int f = i / TH;
+      const int tube = 2 * (i - f * TH);
+      if (tube >= Tb) continue;
+      const float4 v = __ldg(reinterpret_cast<const float4*>(job.in + tube_off[tube] + (long long)f * per_plane));
+      buf0[tube * PP + f] = make_float2(v.x, v.y);
+      buf0[(tube + 1) * PP + f] = make_float2(v.z, v.w);
+    }
+  } else {
+    for (int i = threadIdx.x; i < T * P; i += kThreads) {
+      const int f = i / T;
+      const int tube = i - f * T;
+      if (tube >= Tb) continue;
+      buf0[tube * PP + f] = __ldg(job.in + tube_off[tube] + (long long)f * per_plane);
+    }
+  }
+  __syncthreads();
+  const float2* X = stages<P, 0, 1, true>(buf0, buf1, Tb, tw);
+
+  const float scale = 1.0f / (float)P;
+  float2* dst = job.out + t0 * P;
+  if constexpr (P % 2 == 0) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int i = threadIdx.x; i < Tb * (P / 2); i += kThreads) {
+      const int tube = (2 * i) / P;
+      const int k = 2 * i - tube * P;
+      const float2 a = X[tube * PP + k];
+      const float2 c = X[tube * PP + k + 1];
+      d4[i] = make_float4(a.x * scale, a.y * scale, c.x * scale, c.y * scale);
+    }
+  } else {
+    for (int i = threadIdx.x; i < Tb * P; i += kThreads) {
+      const int tube = i / P;
+      const float2 a = X[tube * PP + (i - tube * P)];
+      dst[i] = make_float2(a.x * scale, a.y * scale);
+    }
+  }
+}
+
+template <int P, int FMT>
+cudaError_t fwd_launch(const FftFwdJob* jobs, int njobs, const float2* tw, cudaStream_t st) {
+  constexpr size_t smem = smem_for<P>();
+  cudaError_t e = cudaFuncSetAttribute(fft_fwd_fixed<P, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int nb = 0;
+  for (int i = 0; i < njobs; ++i) nb += jobs[i].nblocks;
+  if (nb == 0) return cudaSuccess;
+  fft_fwd_fixed<P, FMT><<<nb, kThreads, smem, st>>>(jobs[0], njobs > 1 ? jobs[1] : jobs[0], njobs, tw);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t fwd_fmt(const FftFwdJob* jobs, int njobs, int fmt, const float2* tw, cudaStream_t st) {
+  switch (fmt) {
+    case FMT_C32: return fwd_launch<P, FMT_C32>(jobs, njobs, tw, st);
+    case FMT_BF16X3: return fwd_launch<P, FMT_BF16X3>(jobs, njobs, tw, st);
+    case FMT_BF16: return fwd_launch<P, FMT_BF16>(jobs, njobs, tw, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int P>
+cudaError_t inv_launch(const FftInvJob* jobs, int njobs, const float2* tw, cudaStream_t st) {
+  constexpr size_t smem = smem_for<P>();
+  cudaError_t e = cudaFuncSetAttribute(fft_inv_fixed<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int nb = 0;
+  for (int i = 0; i < njobs; ++i) nb += jobs[i].nblocks;
+  if (nb == 0) return cudaSuccess;
+  fft_inv_fixed<P><<<nb, kThreads, smem, st>>>(jobs[0], njobs > 1 ? jobs[1] : jobs[0], njobs, tw);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int fft_fixed_tubes(int p) {
+  switch (p) {
+    case 8: return tubes_for(8);
+    case 12: return tubes_for(12);
+    case 16: return tubes_for(16);
+    case 31: return tubes_for(31);
+    case 32: return tubes_for(32);
+    case 64: return tubes_for(64);
+    case 100: return tubes_for(100);
+    case 128: return tubes_for(128);
+    default: return 0;
+  }
+}
+
+cudaError_t launch_fft_fwd_fixed(const FftFwdJob* jobs, int njobs, int fmt, int p, const float2* tw,
+                                 cudaStream_t st) {
+  switch (p) {
+    case 8: return fwd_fmt<8>(jobs, njobs, fmt, tw, st);
+    case 12: return fwd_fmt<12>(jobs, njobs, fmt, tw, st);
+    case 16: return fwd_fmt<16>(jobs, njobs, fmt, tw, st);
+    case 31: return fwd_fmt<31>(jobs, njobs, fmt, tw, st);
+    case 32: return fwd_fmt<32>(jobs, njobs, fmt, tw, st);
+    case 64: return fwd_fmt<64>(jobs, njobs, fmt, tw, st);
+    case 100: return fwd_fmt<100>(jobs, njobs, fmt, tw, st);
+    case 128: return fwd_fmt<128>(jobs, njobs, fmt, tw, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t launch_fft_inv_fixed(const FftInvJob* jobs, int njobs, int p, const float2* tw, cudaStream_t st) {
+  switch (p) {
+    case 8: return inv_launch<8>(jobs, njobs, tw, st);
+    case 12: return inv_launch<12>(jobs, njobs, tw, st);
+    case 16: return inv_launch<16>(jobs, njobs, tw, st);
+    case 31: return inv_launch<31>(jobs, njobs, tw, st);
+    case 32: return inv_launch<32>(jobs, njobs, tw, st);
+    case 64: return inv_launch<64>(jobs, njobs, tw, st);
+    case 100: return inv_launch<100>(jobs, njobs, tw, st);
+    case 128: return inv_launch<128>(jobs, njobs, tw, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace qtp

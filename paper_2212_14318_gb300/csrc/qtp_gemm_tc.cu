@@ -10,10 +10,13 @@
 // (from the paper's "-" in eq. TC and from conjugations) are applied with the
 // instruction descriptor's negate-A bit, so no operand is ever rewritten.
 //
-// For frequency f and output half h the CTA computes a 128 x 128 complex tile
+// For frequency f and output half h the CTA computes a 128 x BN complex tile
+// (BN = 256 for wide products, 128 otherwise)
 //   Out_h(f) = sum_kh sign[h][kh] * opA[h][kh](f) . opB[h][kh](f)
-// with two accumulators in TMEM (real part: columns 0..127, imaginary part:
-// columns 128..255).  Operands stream through a 3-stage TMA -> shared memory
+// with two accumulators in TMEM (real part: columns 0..BN-1, imaginary part:
+// columns BN..2BN-1).  The 256-wide MMA reads 96 B of operands per clock from
+// shared memory where two 128-wide ones read 128 B, which leaves room for the
+// TMA fills.  Operands stream through a 2-4 stage TMA -> shared memory
 // pipeline (mbarrier full/empty pairs); one thread issues tcgen05.mma, four
 // warps drain TMEM with tcgen05.ld.  K-major operands use the 64-byte swizzle
 // (32 bf16 of K per row); MN-major operands the 128-byte swizzle (64 bf16 of
@@ -22,6 +25,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include "qtp_internal.h"
 
@@ -30,13 +34,17 @@ namespace qtp {
 namespace {
 
 constexpr int BM = 128;                 // output rows per tile (UMMA M)
-constexpr int BN = 128;                 // complex output columns per tile (UMMA N)
-constexpr int BK = 32;                  // K per pipeline stage
-constexpr int STAGES = 3;
-constexpr int TILE_BYTES = 8192;        // one bf16 part tile: 128 x 32 or 32 x 128
+constexpr int kSmemBudget = 196608;     // operand stages per CTA
+constexpr int kMaxStages = 6;
 constexpr int kThreads = 192;           // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-constexpr uint32_t TMEM_COLS = 2 * BN;  // real + imaginary accumulators
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
+
+// Pipeline depth for a tile of BN complex columns, K depth BK and NP bf16 parts.
+__host__ __device__ constexpr int stages_for(int np, int bn, int bk) {
+  const int per = np * (BM * bk * 2 + bk * bn * 2);
+  const int st = kSmemBudget / per;
+  return st > kMaxStages ? kMaxStages : st;
+}
 
 struct TcArgs {
   CUtensorMap tmA;  // spectra tensor of the A operand
@@ -116,15 +124,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 
 constexpr uint32_t kLayoutSw128 = 2;
 constexpr uint32_t kLayoutSw64 = 4;
+constexpr uint32_t kLayoutSw32 = 6;
 
-// Descriptor of one bf16 part tile for the MMA at K offset k16 (0 or 1).
-//   K-major: rows of 32 bf16 (64 B, 64-byte swizzle); 8-row groups 512 B apart.
-//   MN-major: K rows of 64 bf16 (128 B, 128-byte swizzle); the two 64-wide
-//             halves of M/N are 4096 B apart, 8-row K groups 1024 B apart.
-template <bool MN_MAJOR>
+// Descriptor of one bf16 part tile for the MMA at K offset 16 * k16.
+//   K-major: rows of BK bf16 (2 BK bytes, swizzled over the row: 64-byte
+//            pattern for BK = 32, 32-byte for BK = 16); 8-row groups 16 BK
+//            bytes apart; the k16 step moves 32 B along the row.
+//   MN-major: K rows of 64 bf16 (128 B, 128-byte swizzle); consecutive 64-wide
+//             blocks of M/N are 128 BK bytes apart, 8-row K groups 1024 B apart.
+template <bool MN_MAJOR, int BK>
 __device__ __forceinline__ uint64_t part_desc(uint32_t tile, int k16) {
-  if (MN_MAJOR) return smem_desc(tile + (uint32_t)k16 * 2048u, 4096u, 1024u, kLayoutSw128);
-  return smem_desc(tile + (uint32_t)k16 * 32u, 16u, 512u, kLayoutSw64);
+  if (MN_MAJOR) return smem_desc(tile + (uint32_t)k16 * 2048u, 128u * BK, 1024u, kLayoutSw128);
+  return smem_desc(tile + (uint32_t)k16 * 32u, 16u, 16u * BK, BK == 32 ? kLayoutSw64 : kLayoutSw32);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -158,20 +169,24 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9, 10-12 = 1), negate A at bit 13, A/B major at bits 15/16,
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn) {
+__host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn, int bn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 constexpr uint32_t kNegA = 1u << 13;
 
 struct Smem {
-  uint32_t a;        // stage s, part q tile at a + (s * nparts + q) * TILE_BYTES
-  uint32_t b;
+  uint32_t a;        // stage s, part q tile at a + (s * NP + q) * A_TILE
+  uint32_t b;        // stage s, part q tile at b + (s * NP + q) * B_TILE
   uint32_t full, empty, acc_full, mma_done;  // mbarrier addresses (8 B each)
 };
 
-template <bool A_MN, bool B_MN, int NP>
+template <bool A_MN, bool B_MN, int NP, int BN, int BK>
 __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_constant__ TcArgs args) {
+  constexpr int A_TILE = BM * BK * 2;
+  constexpr int B_TILE = BK * BN * 2;
+  constexpr int STAGES = stages_for(NP, BN, BK);
+  constexpr uint32_t TMEM_COLS = 2 * BN;  // real + imaginary accumulators
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint32_t tmem_base_slot;
   __shared__ int abort_flag;
@@ -180,8 +195,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   const uint32_t base = (raw + 1023u) & ~1023u;
   Smem S;
   S.a = base;
-  S.b = base + STAGES * NP * TILE_BYTES;
-  const uint32_t bars = S.b + STAGES * NP * TILE_BYTES;
+  S.b = base + STAGES * NP * A_TILE;
+  const uint32_t bars = S.b + STAGES * NP * B_TILE;
   S.full = bars;
   S.empty = bars + 8 * STAGES;
   S.acc_full = bars + 16 * STAGES;
@@ -235,25 +250,26 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           break;
         }
         if (*(volatile int*)&abort_flag) break;
-        mbar_expect_tx(S.full + 8 * s, (uint32_t)(2 * NP * TILE_BYTES));
+        mbar_expect_tx(S.full + 8 * s, (uint32_t)(NP * (A_TILE + B_TILE)));
         const int ga = args.a_fneg[h][kh] ? (p - f) % p : f;
         const int gb = args.b_fneg[h][kh] ? (p - f) % p : f;
         const int k0 = kb * BK;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-          const uint32_t ta = S.a + (uint32_t)(s * NP + q) * TILE_BYTES;
-          const uint32_t tb = S.b + (uint32_t)(s * NP + q) * TILE_BYTES;
+          const uint32_t ta = S.a + (uint32_t)(s * NP + q) * A_TILE;
+          const uint32_t tb = S.b + (uint32_t)(s * NP + q) * B_TILE;
           const int ca = args.a_plane[h][kh] * NP + q;
           const int cb = args.b_plane[h][kh] * NP + q;
           if (A_MN) {
             tma_load_4d(ta, &args.tmA, S.full + 8 * s, mt * BM, k0, ga, ca);
-            tma_load_4d(ta + 4096u, &args.tmA, S.full + 8 * s, mt * BM + 64, k0, ga, ca);
+            tma_load_4d(ta + 128u * BK, &args.tmA, S.full + 8 * s, mt * BM + 64, k0, ga, ca);
           } else {
             tma_load_4d(ta, &args.tmA, S.full + 8 * s, k0, mt * BM, ga, ca);
           }
           if (B_MN) {
-            tma_load_4d(tb, &args.tmB, S.full + 8 * s, nt * BN, k0, gb, cb);
-            tma_load_4d(tb + 4096u, &args.tmB, S.full + 8 * s, nt * BN + 64, k0, gb, cb);
+#pragma unroll
+            for (int c = 0; c < BN / 64; ++c)
+              tma_load_4d(tb + 128u * BK * c, &args.tmB, S.full + 8 * s, nt * BN + 64 * c, k0, gb, cb);
           } else {
             tma_load_4d(tb, &args.tmB, S.full + 8 * s, k0, nt * BN, gb, cb);
           }
@@ -269,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(A_MN, B_MN);
+      const uint32_t idesc = make_idesc(A_MN, B_MN, BN);
       const uint32_t d_re = tmem;
       const uint32_t d_im = tmem + (uint32_t)BN;
       uint32_t acc_re = 0, acc_im = 0;
@@ -286,8 +302,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         }
         fence_after();
         const uint32_t neg = args.negmask[h][kh];
-        const uint32_t ta = S.a + (uint32_t)(s * NP) * TILE_BYTES;
-        const uint32_t tb = S.b + (uint32_t)(s * NP) * TILE_BYTES;
+        const uint32_t ta = S.a + (uint32_t)(s * NP) * A_TILE;
+        const uint32_t tb = S.b + (uint32_t)(s * NP) * B_TILE;
 #pragma unroll
         for (int k16 = 0; k16 < BK / 16; ++k16) {
           // part tiles: NP == 4: re_hi, re_lo, im_hi, im_lo; NP == 2: re, im
@@ -300,13 +316,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             const uint32_t id = idesc | (((neg >> prod) & 1u) ? kNegA : 0u);
             const uint32_t d = to_re ? d_re : d_im;
             uint32_t& acc = to_re ? acc_re : acc_im;
-            const uint64_t a_hi = part_desc<A_MN>(ta + (uint32_t)xa * TILE_BYTES, k16);
-            const uint64_t b_hi = part_desc<B_MN>(tb + (uint32_t)yb * TILE_BYTES, k16);
+            const uint64_t a_hi = part_desc<A_MN, BK>(ta + (uint32_t)xa * A_TILE, k16);
+            const uint64_t b_hi = part_desc<B_MN, BK>(tb + (uint32_t)yb * B_TILE, k16);
             mma_bf16(d, a_hi, b_hi, id, acc);
             acc = 1;
             if (NP == 4) {
-              const uint64_t a_lo = part_desc<A_MN>(ta + (uint32_t)(xa + 1) * TILE_BYTES, k16);
-              const uint64_t b_lo = part_desc<B_MN>(tb + (uint32_t)(yb + 1) * TILE_BYTES, k16);
+              const uint64_t a_lo = part_desc<A_MN, BK>(ta + (uint32_t)(xa + 1) * A_TILE, k16);
+              const uint64_t b_lo = part_desc<B_MN, BK>(tb + (uint32_t)(yb + 1) * B_TILE, k16);
               mma_bf16(d, a_hi, b_lo, id, 1);
               mma_bf16(d, a_lo, b_hi, id, 1);
             }
@@ -385,10 +401,10 @@ EncodeTiledFn get_encode_fn() {
 }
 
 // Spectra tensor [plane][part][f][rows][ld] as a 4-D bf16 tensor map:
-// dims (cols, rows, p, 2 * nparts); box (32, 128) for a K-major operand
+// dims (cols, rows, p, 2 * nparts); box (32, box_rows) for a K-major operand
 // (K = cols) and (64, 32) for an MN-major one (M or N = cols).
 bool encode_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int p, int nparts, bool mn_major,
-                char* msg, size_t msglen) {
+                int box_rows, int bk, char* msg, size_t msglen) {
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) {
     snprintf(msg, msglen, "cuTensorMapEncodeTiled unavailable");
@@ -398,16 +414,17 @@ bool encode_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, i
   cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * rows, (cuuint64_t)ld * 2 * rows * p};
   cuuint32_t box[4];
   if (mn_major) {
-    box[0] = 64; box[1] = BK;
+    box[0] = 64; box[1] = (cuuint32_t)bk;
   } else {
-    box[0] = BK; box[1] = 128;
+    box[0] = (cuuint32_t)bk; box[1] = (cuuint32_t)box_rows;
   }
   box[2] = 1;
   box[3] = 1;
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   mn_major ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   mn_major ? CU_TENSOR_MAP_SWIZZLE_128B
+                            : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     snprintf(msg, msglen, "cuTensorMapEncodeTiled failed (%d) rows=%d cols=%d ld=%d", (int)r, rows, cols, ld);
@@ -416,12 +433,11 @@ bool encode_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, i
   return true;
 }
 
-size_t smem_bytes(int np) { return (size_t)2 * STAGES * np * TILE_BYTES + 1024 /*align*/ + 256 /*barriers*/; }
-
-template <bool A_MN, bool B_MN, int NP>
+template <bool A_MN, bool B_MN, int NP, int BN, int BK>
 cudaError_t launch_kind(const TcArgs& args, dim3 grid, cudaStream_t st) {
-  auto kfn = gemm_tc_kernel<A_MN, B_MN, NP>;
-  const size_t smem = smem_bytes(NP);
+  auto kfn = gemm_tc_kernel<A_MN, B_MN, NP, BN, BK>;
+  const size_t smem =
+      (size_t)stages_for(NP, BN, BK) * NP * (BM * BK * 2 + BK * BN * 2) + 1024 /*align*/ + 256 /*barriers*/;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kfn<<<grid, kThreads, smem, st>>>(args);
@@ -447,13 +463,25 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
   if (pr.nparts != 4 && pr.nparts != 2) return cudaErrorInvalidValue;
   const bool a_mn = pr.kind == TC_BWD_B;
   const bool b_mn = pr.kind != TC_BWD_A;
+  // 256-wide tiles halve the shared-memory operand traffic per MMA; narrow
+  // products keep 128-wide tiles to avoid padding waste.  QTP_TC_TILE
+  // ("<BN>x<BK>", e.g. "256x16") overrides the choice for tuning.
+  int bn = pr.N > 160 ? 256 : 128;
+  int bk = 16;
+  if (const char* env = getenv("QTP_TC_TILE")) {
+    int a = 0, b = 0;
+    if (sscanf(env, "%dx%d", &a, &b) == 2 && (a == 128 || a == 256) && (b == 16 || b == 32)) {
+      bn = a;
+      bk = b;
+    }
+  }
   TcArgs args;
   memset(&args, 0, sizeof(args));
-  if (!encode_map(&args.tmA, pr.a_base[0], pr.a_rows[0], pr.a_cols[0], pr.a_ld[0], pr.p, pr.nparts, a_mn, msg,
-                  msglen))
+  if (!encode_map(&args.tmA, pr.a_base[0], pr.a_rows[0], pr.a_cols[0], pr.a_ld[0], pr.p, pr.nparts, a_mn, BM,
+                  bk, msg, msglen))
     return cudaErrorInvalidValue;
-  if (!encode_map(&args.tmB, pr.b_base[0], pr.b_rows[0], pr.b_cols[0], pr.b_ld[0], pr.p, pr.nparts, b_mn, msg,
-                  msglen))
+  if (!encode_map(&args.tmB, pr.b_base[0], pr.b_rows[0], pr.b_cols[0], pr.b_ld[0], pr.p, pr.nparts, b_mn, bn,
+                  bk, msg, msglen))
     return cudaErrorInvalidValue;
   args.M = pr.M; args.N = pr.N; args.K = pr.K; args.p = pr.p; args.nparts = pr.nparts;
   for (int h = 0; h < 2; ++h)
@@ -480,15 +508,25 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
   args.out_fstride = pr.out_fstride;
   args.out_rstride = pr.out_rstride;
   args.err = d_err;
-  dim3 grid((pr.N + BN - 1) / BN, (pr.M + BM - 1) / BM, 2 * pr.p);
+  dim3 grid((pr.N + bn - 1) / bn, (pr.M + BM - 1) / BM, 2 * pr.p);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
   const bool x3 = pr.nparts == 4;
+#define QTP_TC_LAUNCH_BK(AMN, BMN, BK)                                                     \
+  return x3 ? (bn == 256 ? launch_kind<AMN, BMN, 4, 256, BK>(args, grid, st)              \
+                         : launch_kind<AMN, BMN, 4, 128, BK>(args, grid, st))             \
+            : (bn == 256 ? launch_kind<AMN, BMN, 2, 256, BK>(args, grid, st)              \
+                         : launch_kind<AMN, BMN, 2, 128, BK>(args, grid, st))
+#define QTP_TC_LAUNCH(AMN, BMN)        \
+  if (bk == 16) QTP_TC_LAUNCH_BK(AMN, BMN, 16); \
+  QTP_TC_LAUNCH_BK(AMN, BMN, 32)
   switch (pr.kind) {
-    case TC_FWD: return x3 ? launch_kind<false, true, 4>(args, grid, st) : launch_kind<false, true, 2>(args, grid, st);
-    case TC_BWD_A: return x3 ? launch_kind<false, false, 4>(args, grid, st) : launch_kind<false, false, 2>(args, grid, st);
-    case TC_BWD_B: return x3 ? launch_kind<true, true, 4>(args, grid, st) : launch_kind<true, true, 2>(args, grid, st);
+    case TC_FWD: QTP_TC_LAUNCH(false, true);
+    case TC_BWD_A: QTP_TC_LAUNCH(false, false);
+    case TC_BWD_B: QTP_TC_LAUNCH(true, true);
     default: return cudaErrorInvalidValue;
   }
+#undef QTP_TC_LAUNCH
+#undef QTP_TC_LAUNCH_BK
 }
 
 }  // namespace qtp

@@ -55,6 +55,14 @@ struct FftInvJob {
 
 int fft_tubes_per_block(int p);
 
+// Compile-time specialisations (qtp_fft_fixed.cu) for the common tube lengths:
+// tubes per CTA, or 0 when p has none; the launches return
+// cudaErrorNotSupported for other p.
+int fft_fixed_tubes(int p);
+cudaError_t launch_fft_fwd_fixed(const FftFwdJob* jobs, int njobs, int fmt, int p, const float2* tw,
+                                 cudaStream_t st);
+cudaError_t launch_fft_inv_fixed(const FftInvJob* jobs, int njobs, int p, const float2* tw, cudaStream_t st);
+
 cudaError_t launch_twiddles(float2* tw, int p, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdJob* jobs, int njobs, int fmt, const RadixPlan& rp,
                            const float2* tw, cudaStream_t st);
