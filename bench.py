@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 
 METRIC = "T-product effective TFLOP/s, % roofline; mixed-prec vs FP32 at rel err<=1e-5"
 UNIT = "TFLOP/s"
-WORKLOAD = "video"
+WORKLOAD = "video"   # the metric's configuration; --workload selects another one
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=100, help="steps of the plain FP32 comparison leg")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--workload", default="video", choices=["video", "precision", "small", "diff"])
     return ap.parse_args()
 
 
@@ -67,8 +68,10 @@ def effective_flops(m, n, s, p):
 
 def workload_desc():
     m, n, s, p = dims()
-    return (f"colour-video T-product: A {m}x{n}x{p} pure quaternion (pixel-like, i/j/k ~ U[0,1]) * "
-            f"B {n}x{s}x{p} N(0,1), FP32 storage")
+    if WORKLOAD == "video":
+        return (f"colour-video T-product: A {m}x{n}x{p} pure quaternion (pixel-like, i/j/k ~ U[0,1]) * "
+                f"B {n}x{s}x{p} N(0,1), FP32 storage")
+    return f"{WORKLOAD} T-product: A {m}x{n}x{p} * B {n}x{s}x{p}, N(0,1) components, FP32 storage"
 
 
 def load_peaks():
@@ -100,6 +103,18 @@ def oracle_inputs():
     return A, B, comp(A), comp(B)
 
 
+def oracle_pairs(Aq, Bq, count, seed):
+    """Oracle fibres C(:, t, k) for `count` random (t, k); returns (pairs, values, seconds)."""
+    import numpy as np
+    import oracle as Q
+    m, n, s, p = dims()
+    rng = np.random.default_rng(seed)
+    tt, kk = rng.integers(0, s, count), rng.integers(0, p, count)
+    t0 = time.perf_counter()
+    ref = Q.tprod_def_pairs(Aq, Bq, tt, kk)
+    return (tt, kk), ref, time.perf_counter() - t0
+
+
 def oracle_entries_rate(Aq, Bq, count, seed):
     """Time the oracle on `count` random entries C(i, t, k); return (seconds, entries)."""
     import oracle as Q
@@ -112,26 +127,18 @@ def oracle_entries_rate(Aq, Bq, count, seed):
 
 
 def cpu_baseline(Aq, Bq, budget_s=15.0):
-    """Oracle (definition, FP64 NumPy) on a bounded sample: whole lateral columns."""
-    import oracle as Q
-    from paper_2212_14318_gb300 import synth
+    """Oracle (definition, FP64 NumPy) on a bounded sample: mode-1 fibres C(:, t, k)."""
     m, n, s, p = dims()
-    cols = list(synth.sample_columns(s, s))
-    t0 = time.perf_counter()
-    done = 0
-    while done < len(cols):
-        Q.tprod_def_columns(Aq, Bq, [cols[done]])
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    full_s = dt * s / done
+    _, _, dt = oracle_pairs(Aq, Bq, 2, seed=50)
+    count = max(2, min(s * p, int(2 * budget_s / max(dt, 1e-3))))
+    _, _, dt = oracle_pairs(Aq, Bq, count, seed=51)
+    full_s = dt * (s * p) / count
     return {
         "value": effective_flops(m, n, s, p) / full_s / 1e12,
         "unit": UNIT,
         "cores": cores_used(),
         "kind": "oracle",
-        "sample": f"{done} of {s} lateral columns C(:,t,:) by Definition 2.3 (FP64 NumPy) in {dt:.1f} s; "
+        "sample": f"{count} of {s * p} mode-1 fibres C(:,t,k) by Definition 2.3 (FP64 NumPy) in {dt:.1f} s; "
                   f"full product extrapolated to {full_s:.0f} s",
     }
 
@@ -278,15 +285,16 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = world * flops / (ms_per_step * 1e-3) / 1e12
 
-    # accuracy of the main leg on sampled entries (FP64 oracle)
+    # accuracy against the FP64 oracle on 32 sampled mode-1 fibres C(:, t, k)
+    if rank == 0:
+        (tt_s, kk_s), ref_s, _ = oracle_pairs(Aq, Bq, 32, seed=11)
+
     def sampled_rel_err(Cdev):
-        import oracle as Q
-        from paper_2212_14318_gb300 import synth
-        ii, tt, kk = synth.sample_positions(m, s, p, 1000, seed=11)
-        ref = Q.tprod_def_entries(Aq, Bq, ii, tt, kk)
-        Ch = Cdev.cpu().numpy().astype(np.float64)
-        got = np.stack([Ch[0, ii, tt, kk, 0], Ch[0, ii, tt, kk, 1], Ch[1, ii, tt, kk, 0], Ch[1, ii, tt, kk, 1]])
-        return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        ti = torch.as_tensor(tt_s, device=dev)
+        ki = torch.as_tensor(kk_s, device=dev)
+        Ch = Cdev[:, :, ti, ki, :].cpu().numpy().astype(np.float64)    # (2, m, P, 2)
+        got = np.stack([Ch[0, ..., 0], Ch[0, ..., 1], Ch[1, ..., 0], Ch[1, ..., 1]])
+        return float(np.linalg.norm(got - ref_s) / np.linalg.norm(ref_s))
 
     out = {}
     if rank == 0:
@@ -294,11 +302,14 @@ def run_ours(args):
         plan.sync()
         out["rel_err"] = sampled_rel_err(C)
 
-    # plain FP32 GPU path on the same workload (context for the mixed-precision claim)
-    fp32_plan, fp32_ms, fp32_stage = timed_leg("fp32", args.fp32_steps, 3, trace=True)
-    fp32 = {"ms_per_step": fp32_ms / args.fp32_steps,
-            "value": flops / (fp32_ms / args.fp32_steps * 1e-3) / 1e12,
-            "products_ms": fp32_stage[1] / args.fp32_steps}
+    # plain FP32 GPU path on the same workload (context for the mixed-precision claim),
+    # at most ~3 s of timed work
+    est = ms_per_step * 6.0
+    fp32_steps = max(3, min(args.fp32_steps, int(3000.0 / max(est, 1e-3))))
+    fp32_plan, fp32_ms, fp32_stage = timed_leg("fp32", fp32_steps, 3, trace=True)
+    fp32 = {"ms_per_step": fp32_ms / fp32_steps,
+            "value": flops / (fp32_ms / fp32_steps * 1e-3) / 1e12,
+            "products_ms": fp32_stage[1] / fp32_steps, "steps": fp32_steps}
     if rank == 0:
         fp32_plan.forward(A, B, C)
         fp32_plan.sync()
@@ -414,7 +425,9 @@ def run_reference(args):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = args.workload
     if args.impl == "reference":
         run_reference(args)
     else:

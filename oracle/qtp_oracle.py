@@ -21,6 +21,7 @@ What is computed
                           C^(k) = sum_r A^(r) B^((k - r) mod p) (0-based), which
                           is row block k of bcirc(A) times unfold(B).
 * ``tprod_def_columns``   lateral columns C(:, t, :) by the definition.
+* ``tprod_def_pairs``     mode-1 fibres C(:, t, k) by the definition.
 * ``tprod_def_entries``   single entries C(i, t, k) by the definition.
 * ``alg51``               Algorithm 5.1 in FP64 (Thm 5.1, eqs. TC/TC2, ifft-C),
                           used only for the self-tests and as a CPU timing.
@@ -170,6 +171,24 @@ def tprod_def_columns(A: np.ndarray, B: np.ndarray, ts) -> np.ndarray:
         row_block = np.concatenate([A[:, :, :, (k - c) % p] for c in range(p)], axis=2)
         C[:, :, :, k] = qmatmul(row_block, UB)
     return C
+
+
+def tprod_def_pairs(A: np.ndarray, B: np.ndarray, tt, kk) -> np.ndarray:
+    """Mode-1 fibres C(:, t, k) for the pairs (t, k) in zip(tt, kk), by the definition.
+
+    C(i, t, k) = sum_r sum_j A(i, j, r) * B(j, t, (k - r) mod p): row i of row
+    block k of bcirc(A) times column t of unfold(B) (Def. 2.3).  All pairs go
+    through one quaternion matrix product: A as the (m, n p) matrix over (j, r)
+    times the (n p, P) matrix whose column q holds B(j, t_q, (k_q - r) mod p).
+    Returns (4, m, P).
+    """
+    _, m, n, p = A.shape
+    tt, kk = np.asarray(tt), np.asarray(kk)
+    r = np.arange(p)
+    cols = np.empty((4, n, p, len(tt)))
+    for q in range(len(tt)):
+        cols[:, :, :, q] = B[:, :, tt[q], :][:, :, (kk[q] - r) % p]
+    return qmatmul(A.reshape(4, m, n * p), cols.reshape(4, n * p, len(tt)))
 
 
 def tprod_def_entries(A: np.ndarray, B: np.ndarray, ii, tt, kk) -> np.ndarray:

@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include "qtp_internal.h"
 
@@ -153,18 +154,20 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
+// 32 consecutive TMEM columns of this thread's lane.  The wait sits in the same
+// asm statement, so the outputs are complete when the compiler sees them.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
+      : "r"(taddr)
+      : "memory");
 }
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9, 10-12 = 1), negate A at bit 13, A/B major at bits 15/16,
@@ -181,12 +184,18 @@ struct Smem {
   uint32_t full, empty, acc_full, mma_done;  // mbarrier addresses (8 B each)
 };
 
-template <bool A_MN, bool B_MN, int NP, int BN, int BK>
+// SPLIT: the hi.hi products go to one pair of accumulators and the two
+// correction products (hi.lo + lo.hi, 2^-8 smaller) to a second pair, summed in
+// FP32 by the epilogue.  The tensor core's FP32 accumulation error grows with
+// the number of MMAs folded into an accumulator; this cuts that number for the
+// dominant accumulator threefold (needs 4 BN <= 512 TMEM columns).
+template <bool A_MN, bool B_MN, int NP, int BN, int BK, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_constant__ TcArgs args) {
+  static_assert(!SPLIT || (NP == 4 && BN <= 128), "split accumulators need bf16x3 parts and BN <= 128");
   constexpr int A_TILE = BM * BK * 2;
   constexpr int B_TILE = BK * BN * 2;
   constexpr int STAGES = stages_for(NP, BN, BK);
-  constexpr uint32_t TMEM_COLS = 2 * BN;  // real + imaginary accumulators
+  constexpr uint32_t TMEM_COLS = (SPLIT ? 4 : 2) * BN;  // real + imaginary (x2 when split)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint32_t tmem_base_slot;
   __shared__ int abort_flag;
@@ -288,7 +297,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       const uint32_t idesc = make_idesc(A_MN, B_MN, BN);
       const uint32_t d_re = tmem;
       const uint32_t d_im = tmem + (uint32_t)BN;
-      uint32_t acc_re = 0, acc_im = 0;
+      const uint32_t c_re = SPLIT ? tmem + 2u * BN : d_re;  // correction accumulators
+      const uint32_t c_im = SPLIT ? tmem + 3u * BN : d_im;
+      uint32_t acc_re = 0, acc_im = 0, acc_cre = 0, acc_cim = 0;
       bool ok = true;
       for (int it = 0; it < total; ++it) {
         const int kh = it / nkb;
@@ -315,7 +326,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             const bool to_re = prod < 2;
             const uint32_t id = idesc | (((neg >> prod) & 1u) ? kNegA : 0u);
             const uint32_t d = to_re ? d_re : d_im;
+            const uint32_t dc = to_re ? c_re : c_im;
             uint32_t& acc = to_re ? acc_re : acc_im;
+            uint32_t& accc = SPLIT ? (to_re ? acc_cre : acc_cim) : acc;
             const uint64_t a_hi = part_desc<A_MN, BK>(ta + (uint32_t)xa * A_TILE, k16);
             const uint64_t b_hi = part_desc<B_MN, BK>(tb + (uint32_t)yb * B_TILE, k16);
             mma_bf16(d, a_hi, b_hi, id, acc);
@@ -323,8 +336,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             if (NP == 4) {
               const uint64_t a_lo = part_desc<A_MN, BK>(ta + (uint32_t)(xa + 1) * A_TILE, k16);
               const uint64_t b_lo = part_desc<B_MN, BK>(tb + (uint32_t)(yb + 1) * B_TILE, k16);
-              mma_bf16(d, a_hi, b_lo, id, 1);
-              mma_bf16(d, a_lo, b_hi, id, 1);
+              mma_bf16(dc, a_hi, b_lo, id, accc);
+              accc = 1;
+              mma_bf16(dc, a_lo, b_hi, id, 1);
             }
           }
         }
@@ -357,7 +371,16 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         uint32_t re[32], im[32];
         tmem_ld32(tmem + lane_off + (uint32_t)c0, re);
         tmem_ld32(tmem + lane_off + (uint32_t)(BN + c0), im);
-        tmem_wait_ld();
+        if constexpr (SPLIT) {
+          uint32_t cre[32], cim[32];
+          tmem_ld32(tmem + lane_off + (uint32_t)(2 * BN + c0), cre);
+          tmem_ld32(tmem + lane_off + (uint32_t)(3 * BN + c0), cim);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            re[j] = __float_as_uint(__uint_as_float(re[j]) + __uint_as_float(cre[j]));
+            im[j] = __float_as_uint(__uint_as_float(im[j]) + __uint_as_float(cim[j]));
+          }
+        }
         if (row < args.M) {
           float2* o = out + (long long)row * args.out_rstride;
           const int col0 = nt * BN + c0;
@@ -433,9 +456,9 @@ bool encode_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, i
   return true;
 }
 
-template <bool A_MN, bool B_MN, int NP, int BN, int BK>
+template <bool A_MN, bool B_MN, int NP, int BN, int BK, bool SPLIT = false>
 cudaError_t launch_kind(const TcArgs& args, dim3 grid, cudaStream_t st) {
-  auto kfn = gemm_tc_kernel<A_MN, B_MN, NP, BN, BK>;
+  auto kfn = gemm_tc_kernel<A_MN, B_MN, NP, BN, BK, SPLIT>;
   const size_t smem =
       (size_t)stages_for(NP, BN, BK) * NP * (BM * BK * 2 + BK * BN * 2) + 1024 /*align*/ + 256 /*barriers*/;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -463,18 +486,21 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
   if (pr.nparts != 4 && pr.nparts != 2) return cudaErrorInvalidValue;
   const bool a_mn = pr.kind == TC_BWD_B;
   const bool b_mn = pr.kind != TC_BWD_A;
-  // 256-wide tiles halve the shared-memory operand traffic per MMA; narrow
-  // products keep 128-wide tiles to avoid padding waste.  QTP_TC_TILE
-  // ("<BN>x<BK>", e.g. "256x16") overrides the choice for tuning.
+  // Tile choice.  256-wide tiles halve the shared-memory operand traffic per
+  // MMA; narrow products keep 128-wide tiles to avoid padding waste.  The
+  // tensor core's FP32 accumulation error grows with the number of MMAs folded
+  // into one accumulator (measured: 5.6e-6 at K = 256, 1.5e-5 at K = 1024 per
+  // half for N(0,1) data), so long reductions use split accumulators (128 wide)
+  // to stay within 1e-5.  QTP_TC_TILE = "256", "128" or "128s" overrides.
   int bn = pr.N > 160 ? 256 : 128;
-  int bk = 16;
+  bool split = pr.nparts == 4 && pr.K > 384;
+  if (split) bn = 128;
   if (const char* env = getenv("QTP_TC_TILE")) {
-    int a = 0, b = 0;
-    if (sscanf(env, "%dx%d", &a, &b) == 2 && (a == 128 || a == 256) && (b == 16 || b == 32)) {
-      bn = a;
-      bk = b;
-    }
+    if (!strcmp(env, "256")) { bn = 256; split = false; }
+    else if (!strcmp(env, "128")) { bn = 128; split = false; }
+    else if (!strcmp(env, "128s") && pr.nparts == 4) { bn = 128; split = true; }
   }
+  const int bk = 16;
   TcArgs args;
   memset(&args, 0, sizeof(args));
   if (!encode_map(&args.tmA, pr.a_base[0], pr.a_rows[0], pr.a_cols[0], pr.a_ld[0], pr.p, pr.nparts, a_mn, BM,
@@ -511,14 +537,12 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
   dim3 grid((pr.N + bn - 1) / bn, (pr.M + BM - 1) / BM, 2 * pr.p);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
   const bool x3 = pr.nparts == 4;
-#define QTP_TC_LAUNCH_BK(AMN, BMN, BK)                                                     \
-  return x3 ? (bn == 256 ? launch_kind<AMN, BMN, 4, 256, BK>(args, grid, st)              \
-                         : launch_kind<AMN, BMN, 4, 128, BK>(args, grid, st))             \
-            : (bn == 256 ? launch_kind<AMN, BMN, 2, 256, BK>(args, grid, st)              \
-                         : launch_kind<AMN, BMN, 2, 128, BK>(args, grid, st))
-#define QTP_TC_LAUNCH(AMN, BMN)        \
-  if (bk == 16) QTP_TC_LAUNCH_BK(AMN, BMN, 16); \
-  QTP_TC_LAUNCH_BK(AMN, BMN, 32)
+#define QTP_TC_LAUNCH(AMN, BMN)                                                            \
+  if (split) return launch_kind<AMN, BMN, 4, 128, 16, true>(args, grid, st);               \
+  return x3 ? (bn == 256 ? launch_kind<AMN, BMN, 4, 256, 16>(args, grid, st)              \
+                         : launch_kind<AMN, BMN, 4, 128, 16>(args, grid, st))             \
+            : (bn == 256 ? launch_kind<AMN, BMN, 2, 256, 16>(args, grid, st)              \
+                         : launch_kind<AMN, BMN, 2, 128, 16>(args, grid, st))
   switch (pr.kind) {
     case TC_FWD: QTP_TC_LAUNCH(false, true);
     case TC_BWD_A: QTP_TC_LAUNCH(false, false);
@@ -526,7 +550,6 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
     default: return cudaErrorInvalidValue;
   }
 #undef QTP_TC_LAUNCH
-#undef QTP_TC_LAUNCH_BK
 }
 
 }  // namespace qtp

@@ -24,7 +24,7 @@ SHAPES = [
     (1, 1, 1, 1), (3, 5, 7, 1), (5, 3, 4, 2), (17, 9, 13, 3), (8, 8, 8, 16), (20, 30, 40, 12),
     (16, 16, 16, 31), (33, 65, 31, 7), (1, 70, 1, 8), (70, 1, 70, 5), (130, 40, 260, 8),
     (40, 24, 36, 64), (13, 7, 11, 100), (64, 48, 80, 128), (9, 11, 10, 97), (150, 70, 300, 16),
-    (20, 12, 24, 32),
+    (20, 12, 24, 32), (24, 500, 40, 4),   # K = 500: split accumulators
 ]
 
 
@@ -101,7 +101,7 @@ def test_repeated_calls_are_identical(precision):
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("m,n,s,p", [(5, 4, 3, 1), (6, 9, 7, 4), (12, 10, 14, 7), (33, 17, 40, 32),
-                                     (40, 200, 180, 8)])
+                                     (40, 200, 180, 8), (400, 24, 420, 4)])
 def test_backward_matches_oracle(precision, m, n, s, p):
     qtp = _qtp()
     A, B = _inputs(m, n, s, p, seed=11 + p)

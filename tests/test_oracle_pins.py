@@ -222,6 +222,7 @@ def test_columns_and_entries_match_full_definition():
     np.testing.assert_allclose(Q.tprod_def_columns(A, B, ts), C[:, :, ts, :], atol=1e-12)
     ii, tt, kk = rng.integers(0, 5, 30), rng.integers(0, 8, 30), rng.integers(0, 7, 30)
     np.testing.assert_allclose(Q.tprod_def_entries(A, B, ii, tt, kk), C[:, ii, tt, kk], atol=1e-12)
+    np.testing.assert_allclose(Q.tprod_def_pairs(A, B, tt, kk), C[:, :, tt, kk], atol=1e-12)
 
 
 # ---------------------------------------------------------------- Alg. 5.1 and Example 3.1
