@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=100, help="steps of the plain FP32 comparison leg")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
-    ap.add_argument("--workload", default="video", choices=["video", "precision", "small", "diff"])
+    ap.add_argument("--workload", default="video", choices=["video", "precision", "small", "diff", "batch"])
     return ap.parse_args()
 
 
@@ -388,6 +388,128 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- batch workload
+
+
+def run_batch(args):
+    """4096 products of uneven shapes through qtp_forward_batched (single GPU)."""
+    import numpy as np
+    import torch
+    import oracle as Q
+    from paper_2212_14318_gb300 import qtp, synth
+    dev = torch.device("cuda", 0)
+    shapes = synth.batch_shapes()
+    As, Bs = synth.batch_tensors(shapes)
+    flops = sum(effective_flops(*sh) for sh in shapes)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def leg(precision, steps, warmup):
+        plan = qtp.BatchPlan(shapes, precision)
+        plan.set_tracing(True)
+        Cs = plan.forward(As, Bs)
+        for _ in range(warmup):
+            plan.forward(As, Bs, Cs)
+        plan.sync()
+        st = [0.0, 0.0, 0.0]
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.forward(As, Bs, Cs)
+            e1.record()
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            t3 = plan.stage_times()
+            for j in range(3):
+                st[j] += t3[j]
+        plan.sync()
+        return plan, Cs, total / steps, [x / steps for x in st]
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    plan, Cs, ms, st = leg(args.precision, args.steps, args.warmup)
+    clocks = sampler.stop()
+
+    def sampled_err(Cs):
+        rng = np.random.default_rng(7)
+        num = den = 0.0
+        for i in rng.choice(len(shapes), 256, replace=False):
+            m, n, s, p = shapes[i]
+            ii, tt, kk = rng.integers(0, m), rng.integers(0, s), rng.integers(0, p)
+            a = As[i][:, ii:ii + 1].cpu().numpy().astype(np.float64)
+            b = Bs[i][:, :, tt:tt + 1].cpu().numpy().astype(np.float64)
+            comp = lambda x: np.stack([x[0, ..., 0], x[0, ..., 1], x[1, ..., 0], x[1, ..., 1]])
+            ref = Q.tprod_def_entries(comp(a), comp(b), [0], [0], [kk])[:, 0]
+            c = Cs[i][:, ii, tt, kk].cpu().numpy().astype(np.float64)
+            got = np.array([c[0, 0], c[0, 1], c[1, 0], c[1, 1]])
+            num += np.sum((got - ref) ** 2)
+            den += np.sum(ref ** 2)
+        return float(np.sqrt(num / den))
+
+    rel = sampled_err(Cs)
+    del Cs, plan
+    fplan, fCs, fms, fst = leg("fp32", 2, 1)
+    fp32 = {"ms_per_step": fms, "value": flops / (fms * 1e-3) / 1e12, "products_ms": fst[1], "steps": 2,
+            "rel_err": sampled_err(fCs)}
+    del fCs, fplan
+    # end to end: pinned host inputs -> device, batched product, result back to the host
+    hA = [a.cpu().pin_memory() for a in As]
+    hB = [b.cpu().pin_memory() for b in Bs]
+    hC = [torch.empty((2, m, s, p, 2), dtype=torch.float32).pin_memory() for (m, _, s, p) in shapes]
+    dC = [torch.empty((2, m, s, p, 2), dtype=torch.float32, device=dev) for (m, _, s, p) in shapes]
+    eplan = qtp.BatchPlan(shapes, args.precision)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(max(1, args.e2e_steps // 10)):
+        for a, h in zip(As, hA):
+            a.copy_(h, non_blocking=True)
+        for b, h in zip(Bs, hB):
+            b.copy_(h, non_blocking=True)
+        eplan.forward(As, Bs, dC)
+        for c, h in zip(dC, hC):
+            h.copy_(c, non_blocking=True)
+    e1.record()
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / max(1, args.e2e_steps // 10)
+    peaks, src = load_peaks()
+    tc_peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    gemm_issued = sum((3.0 if args.precision == "bf16x3" else 1.0) * 32.0 * m * n * s * p for (m, n, s, p) in shapes)
+    b1 = sum(32.0 * p * (m * n + n * s) for (m, n, s, p) in shapes)
+    b3 = sum(32.0 * p * m * s for (m, n, s, p) in shapes)
+    stages = {
+        "fft_forward": {"ms": st[0], "bound": "hbm", "achieved": b1 / (st[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s"},
+        "products": {"ms": st[1], "bound": "tensor", "achieved": gemm_issued / (st[1] * 1e-3) / 1e12, "peak": tc_peak,
+                     "unit": "TFLOP/s"},
+        "fft_inverse": {"ms": st[2], "bound": "hbm", "achieved": b3 / (st[2] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s"},
+    }
+    for v in stages.values():
+        v["frac"] = v["achieved"] / v["peak"]
+        v["traffic"] = None
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    roof = dict(stages[dom])
+    roof.pop("ms")
+    roof["kernel"] = dom
+    roof["peak_source"] = src
+    line = {
+        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16x3+f32", "bf16": "bf16+f32", "fp32": "f32"}[args.precision],
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"batch: {len(shapes)} products, m,n,s log-uniform [16,256], "
+                               "p in {8,12,16,31,32,64,100,128}, N(0,1), one grouped launch per stage, CUDA graph",
+                   "precision": args.precision, "l2": "inputs larger than L2; 256 MB flush before every step"},
+        "rel_err": rel, "roofline": roof, "stages": stages, "fp32_path": fp32,
+        "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(sum(a.numel() * 4 for a in As) + sum(b.numel() * 4 for b in Bs)),
+                "d2h_bytes_per_step": int(sum(c.numel() * 4 for c in dC))},
+        "gpu_launches": 3 * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 
@@ -430,6 +552,8 @@ def main():
     WORKLOAD = args.workload
     if args.impl == "reference":
         run_reference(args)
+    elif WORKLOAD == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -131,6 +131,52 @@ QTP_API qtp_status qtp_backward(const qtp_plan* plan, const float* dC, const flo
                         float* dA, float* dB, void* workspace, size_t workspace_bytes,
                         void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: thousands of independent products of uneven shapes in one call
+ * ------------------------------------------------------------------------ */
+
+/* Shape of one product of a batch: A is m x n x p, B is n x s x p. */
+typedef struct {
+  int m, n, s, p;
+} qtp_shape;
+
+typedef struct qtp_batch_plan qtp_batch_plan;
+
+/* Flags of qtp_batch_plan_create. */
+#define QTP_BATCH_NO_GRAPH 1u  /* launch the kernels directly instead of replaying a CUDA graph */
+
+/* Plan a batch of `count` products C_i = A_i * B_i (Definition 2.3, each by
+ * Algorithm 5.1).  Shapes are copied; each must satisfy the limits of
+ * qtp_plan_create.  The plan orders the products by tube length p and then
+ * size (the order the grouped kernels walk them; results are unaffected),
+ * lays out every product's spectra in one workspace, builds the device job
+ * and tile tables and the twiddle tables of every distinct p, and
+ * synchronises the device.  Each forward call runs three grouped launches
+ * (all tube FFTs of A and B; all per-frequency products in one persistent
+ * tensor-core launch, or one FP32 launch; all inverse FFTs), replayed from a
+ * CUDA graph captured on the first call (and again after the workspace
+ * pointer changes) on a stream the plan owns, ordered after and before the
+ * caller's stream with events. */
+QTP_API qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, int count,
+                                         int precision, unsigned flags);
+QTP_API qtp_status qtp_batch_plan_destroy(qtp_batch_plan* plan);
+QTP_API qtp_status qtp_batch_workspace_size(const qtp_batch_plan* plan, size_t* bytes);
+
+/* A, B, C: HOST arrays of `count` DEVICE pointers (product i in the order of
+ * the shapes given to qtp_batch_plan_create), each 16-byte aligned, layout as
+ * for qtp_forward.  The pointer arrays are copied before the call returns.
+ * Asynchronous on stream. */
+QTP_API qtp_status qtp_forward_batched(qtp_batch_plan* plan, const float* const* A, const float* const* B,
+                                       float* const* C, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Tracing of batched calls: four events around the three grouped launches;
+ * ms3 receives their durations for the last traced call (waits for it). */
+QTP_API qtp_status qtp_batch_plan_set_tracing(qtp_batch_plan* plan, int enable);
+QTP_API qtp_status qtp_batch_stage_times(const qtp_batch_plan* plan, float* ms3);
+
+/* As qtp_plan_sync, for a batch plan. */
+QTP_API qtp_status qtp_batch_plan_sync(const qtp_batch_plan* plan, void* stream);
+
 /* Synchronise stream, then read and clear the plan's device error word.
  * Returns QTP_ERR_TIMEOUT if a kernel gave up on a bounded wait since the
  * last call, QTP_ERR_CUDA if the stream reports an error, else QTP_OK. */

@@ -327,6 +327,21 @@ qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, floa
 
 }  // namespace
 
+namespace qtp {
+qtp_status set_error(qtp_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+void clear_error() { g_err[0] = 0; }
+int spec_format_of(int precision) { return spec_format(precision); }
+long long spec_ld_of(int fmt, long long cols) { return spec_ld(fmt, cols); }
+size_t spec_bytes_of(int fmt, long long p, long long rows, long long cols) { return spec_bytes(fmt, p, rows, cols); }
+size_t c32_bytes_of(long long p, long long rows, long long cols) { return c32_bytes(p, rows, cols); }
+}  // namespace qtp
+
 extern "C" {
 
 const char* qtp_last_error(void) { return g_err; }

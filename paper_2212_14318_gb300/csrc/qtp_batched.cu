@@ -1,0 +1,428 @@
+// Batched T-products (qtp_batch_plan_*, qtp_forward_batched): thousands of
+// independent products C_i = A_i * B_i of uneven (m, n, s, p), each by
+// Algorithm 5.1, in three grouped launches replayed from a CUDA graph.
+//
+//   1. fft_fwd_grouped  - every tube of every A_i and B_i (Step 1)
+//   2. products         - all frequencies of all products (Step 2): one
+//                         persistent tcgen05 launch, or one FP32 launch
+//   3. fft_inv_grouped  - every tube of every C_i (Step 3)
+//
+// The plan buckets the products by tube length p, then by size, so that CTAs
+// working at the same time share a kernel specialisation and their
+// products' spectra stay in L2; the pointer table keeps the caller's order.
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "qtp_internal.h"
+
+using namespace qtp;
+
+struct qtp_batch_plan {
+  int count = 0;
+  int precision = 0;
+  int fmt = 0;
+  unsigned flags = 0;
+  int device = 0;
+  int num_sms = 0;
+  std::vector<qtp_shape> shapes;
+  size_t ws_bytes = 0;
+  // device tables
+  float2* d_tw = nullptr;
+  FftGroupJob* d_fwd = nullptr;
+  FftGroupJob* d_inv = nullptr;
+  GroupProblem* d_probs = nullptr;
+  void* d_tmaps = nullptr;  // 2 x 128 B per product (tensor-core path)
+  const float2** d_ptrs = nullptr;
+  int* d_err = nullptr;
+  int n_fwd = 0, n_inv = 0, n_probs = 0;
+  long long fwd_blocks = 0, inv_blocks = 0, total_tiles = 0;
+  size_t fft_smem = 0;
+  // host copies needed to encode tensor maps
+  std::vector<GroupProblem> h_probs;
+  std::vector<int> prod_of_prob;  // product index of each GroupProblem
+  void* h_tmaps = nullptr;        // pinned
+  char* tmaps_for_ws = nullptr;   // workspace base the device tensor maps point into
+  // per-call pointer staging (pinned, 2 slots) and stream plumbing
+  const float2** h_ptrs[2] = {nullptr, nullptr};
+  cudaEvent_t staged[2] = {nullptr, nullptr};
+  int slot = 0;
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  char* graph_ws = nullptr;
+  int graph_tracing = 0;
+  int tracing = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+#define BP_CUDA(call, what)                                                                              \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess) return set_error(QTP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e_));      \
+  } while (0)
+
+void free_plan(qtp_batch_plan* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (int i = 0; i < 4; ++i)
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  for (int i = 0; i < 2; ++i) {
+    if (b->staged[i]) cudaEventDestroy(b->staged[i]);
+    if (b->h_ptrs[i]) cudaFreeHost(b->h_ptrs[i]);
+  }
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->h_tmaps) cudaFreeHost(b->h_tmaps);
+  cudaFree(b->d_tw);
+  cudaFree(b->d_fwd);
+  cudaFree(b->d_inv);
+  cudaFree(b->d_probs);
+  cudaFree(b->d_tmaps);
+  cudaFree(b->d_ptrs);
+  cudaFree(b->d_err);
+  delete b;
+}
+
+// The three grouped launches of one forward call, on stream st.
+qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st) {
+  if (b->tracing) cudaEventRecord(b->ev[0], st);
+  BP_CUDA(launch_fft_fwd_grouped(b->d_fwd, b->n_fwd, b->fwd_blocks, b->fmt, b->d_ptrs, ws, b->d_tw, b->fft_smem, st),
+          "batched forward FFT");
+  if (b->tracing) cudaEventRecord(b->ev[1], st);
+  if (b->precision == QTP_PREC_FP32) {
+    BP_CUDA(launch_gemm_simt_grouped(b->d_probs, b->n_probs, b->total_tiles, ws, st), "batched products (fp32)");
+  } else {
+    BP_CUDA(launch_gemm_tc_grouped(b->d_probs, b->n_probs, b->total_tiles, b->fmt == FMT_BF16X3 ? 4 : 2, ws,
+                                   b->d_err, b->num_sms, st),
+            "batched products (tensor cores)");
+  }
+  if (b->tracing) cudaEventRecord(b->ev[2], st);
+  BP_CUDA(launch_fft_inv_grouped(b->d_inv, b->n_inv, b->inv_blocks, b->d_ptrs, ws, b->d_tw, b->fft_smem, st),
+          "batched inverse FFT");
+  if (b->tracing) cudaEventRecord(b->ev[3], st);
+  return QTP_OK;
+}
+
+// Tensor maps of every product's spectra for the workspace at ws (async upload on st).
+qtp_status encode_tmaps(qtp_batch_plan* b, char* ws, cudaStream_t st) {
+  const int np = b->fmt == FMT_BF16X3 ? 4 : 2;
+  char msg[256];
+  for (int i = 0; i < b->n_probs; ++i) {
+    const GroupProblem& P = b->h_probs[i];
+    char* tA = (char*)b->h_tmaps + (size_t)i * 256;
+    if (!encode_group_map(tA, ws + P.sa_off, P.M, P.K, P.lda, P.p, np, false, msg, sizeof(msg)))
+      return set_error(QTP_ERR_CUDA, "batched tensor map (A of product %d): %s", b->prod_of_prob[i], msg);
+    if (!encode_group_map(tA + 128, ws + P.sb_off, P.K, P.N, P.ldb, P.p, np, true, msg, sizeof(msg)))
+      return set_error(QTP_ERR_CUDA, "batched tensor map (B of product %d): %s", b->prod_of_prob[i], msg);
+  }
+  BP_CUDA(cudaMemcpyAsync(b->d_tmaps, b->h_tmaps, (size_t)b->n_probs * 256, cudaMemcpyHostToDevice, st),
+          "upload tensor maps");
+  b->tmaps_for_ws = ws;
+  return QTP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, int count, int precision,
+                                 unsigned flags) {
+  clear_error();
+  if (!out) return set_error(QTP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!shapes || count < 1) return set_error(QTP_ERR_INVALID_ARG, "need at least one shape");
+  if (count > (1 << 20)) return set_error(QTP_ERR_INVALID_ARG, "at most 2^20 products per batch");
+  if (precision != QTP_PREC_FP32 && precision != QTP_PREC_BF16X3 && precision != QTP_PREC_BF16)
+    return set_error(QTP_ERR_INVALID_ARG, "unknown precision %d", precision);
+  if (flags & ~QTP_BATCH_NO_GRAPH) return set_error(QTP_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  const long long lim = 1LL << 31;
+  for (int i = 0; i < count; ++i) {
+    const qtp_shape& q = shapes[i];
+    if (q.m < 1 || q.n < 1 || q.s < 1 || q.p < 1)
+      return set_error(QTP_ERR_INVALID_ARG, "product %d: dimensions must be >= 1", i);
+    if (q.m > (1 << 20) || q.n > (1 << 20) || q.s > (1 << 20))
+      return set_error(QTP_ERR_INVALID_ARG, "product %d: m, n, s must be <= 2^20", i);
+    if (q.p > QTP_MAX_P) return set_error(QTP_ERR_UNSUPPORTED, "product %d: p=%d exceeds %d", i, q.p, QTP_MAX_P);
+    if ((long long)q.m * q.n * q.p >= lim || (long long)q.n * q.s * q.p >= lim || (long long)q.m * q.s * q.p >= lim)
+      return set_error(QTP_ERR_INVALID_ARG, "product %d: a tensor plane exceeds 2^31 entries", i);
+  }
+  if (precision != QTP_PREC_FP32 && !tc_supported())
+    return set_error(QTP_ERR_UNSUPPORTED, "BF16 tensor-core products need an sm_103 device (tcgen05)");
+
+  qtp_batch_plan* b = new qtp_batch_plan();
+  b->count = count;
+  b->precision = precision;
+  b->fmt = spec_format_of(precision);
+  b->flags = flags;
+  b->shapes.assign(shapes, shapes + count);
+  const int fmt = b->fmt;
+  const bool tc = precision != QTP_PREC_FP32;
+  const int BMt = tc ? kGroupTcBM : kGroupSimtBM;
+  const int BNt = tc ? kGroupTcBN : kGroupSimtBN;
+
+  // bucket by p, then by work (largest first)
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const qtp_shape& a = shapes[x];
+    const qtp_shape& c = shapes[y];
+    if (a.p != c.p) return a.p < c.p;
+    return (long long)a.m * a.n * a.s > (long long)c.m * c.n * c.s;
+  });
+
+  // twiddle tables of the distinct tube lengths
+  std::map<int, int> tw_off;
+  int tw_total = 0;
+  for (int i = 0; i < count; ++i)
+    if (!tw_off.count(shapes[i].p)) {
+      tw_off[shapes[i].p] = tw_total;
+      tw_total += shapes[i].p;
+    }
+
+  // workspace layout, FFT jobs, product tiles
+  std::vector<FftGroupJob> fwd, inv;
+  size_t off = 0;
+  long long fb = 0, ib = 0, tiles = 0;
+  size_t smem = 0;
+  for (int idx : order) {
+    const qtp_shape& q = shapes[idx];
+    const int T = fft_tubes_per_block(q.p);
+    smem = std::max(smem, fft_smem_bytes_for(q.p));
+    const RadixPlan rp = make_radix_plan(q.p);
+    const size_t sa = off;
+    off += spec_bytes_of(fmt, q.p, q.m, q.n);
+    const size_t sb = off;
+    off += spec_bytes_of(fmt, q.p, q.n, q.s);
+    const size_t sc = off;
+    off += c32_bytes_of(q.p, q.m, q.s);
+    auto job = [&](int which, int rows, int cols, size_t spec, long long& counter) {
+      FftGroupJob j;
+      memset(&j, 0, sizeof(j));
+      j.block_begin = counter;
+      j.spec_off = (long long)spec;
+      j.prod = idx;
+      j.which = which;
+      j.rows = rows;
+      j.cols = cols;
+      j.ld = which == 2 ? cols : (int)spec_ld_of(fmt, cols);
+      j.p = q.p;
+      j.T = T;
+      j.tw_off = tw_off[q.p];
+      j.rp = rp;
+      counter += (2LL * rows * cols + T - 1) / T;
+      return j;
+    };
+    fwd.push_back(job(0, q.m, q.n, sa, fb));
+    fwd.push_back(job(1, q.n, q.s, sb, fb));
+    inv.push_back(job(2, q.m, q.s, sc, ib));
+    GroupProblem P;
+    memset(&P, 0, sizeof(P));
+    P.tile_begin = tiles;
+    P.sa_off = (long long)sa;
+    P.sb_off = (long long)sb;
+    P.out_off = (long long)sc;
+    P.M = q.m;
+    P.N = q.s;
+    P.K = q.n;
+    P.p = q.p;
+    P.tiles_m = (q.m + BMt - 1) / BMt;
+    P.tiles_n = (q.s + BNt - 1) / BNt;
+    P.lda = (int)spec_ld_of(fmt, q.n);
+    P.ldb = (int)spec_ld_of(fmt, q.s);
+    tiles += (long long)P.tiles_m * P.tiles_n * 2 * q.p;
+    b->h_probs.push_back(P);
+    b->prod_of_prob.push_back(idx);
+  }
+  if (fb > 0x7fffffffLL || ib > 0x7fffffffLL || (!tc && tiles > 0x7fffffffLL)) {
+    free_plan(b);
+    return set_error(QTP_ERR_UNSUPPORTED, "batch too large for one grouped launch");
+  }
+  b->ws_bytes = off;
+  b->n_fwd = (int)fwd.size();
+  b->n_inv = (int)inv.size();
+  b->n_probs = (int)b->h_probs.size();
+  b->fwd_blocks = fb;
+  b->inv_blocks = ib;
+  b->total_tiles = tiles;
+  b->fft_smem = smem;
+
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tw, sizeof(float2) * tw_total);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_fwd, sizeof(FftGroupJob) * fwd.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_inv, sizeof(FftGroupJob) * inv.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, sizeof(GroupProblem) * b->n_probs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(float2*) * 3 * count);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+  if (e == cudaSuccess && tc) e = cudaMalloc(&b->d_tmaps, (size_t)b->n_probs * 256);
+  if (e == cudaSuccess && tc) e = cudaMallocHost(&b->h_tmaps, (size_t)b->n_probs * 256);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaMallocHost(&b->h_ptrs[i], sizeof(float2*) * 3 * count);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_plan(b);
+    return set_error(QTP_ERR_CUDA, "batch plan allocation: %s", cudaGetErrorString(e));
+  }
+  if (tc)  // tensor maps live in d_tmaps: product i's pair at 256 i
+    for (int i = 0; i < b->n_probs; ++i) {
+      b->h_probs[i].tmA = (char*)b->d_tmaps + (size_t)i * 256;
+      b->h_probs[i].tmB = (char*)b->d_tmaps + (size_t)i * 256 + 128;
+    }
+  for (auto& kv : tw_off) {
+    e = launch_twiddles(b->d_tw + kv.second, kv.first, 0);
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_fwd, fwd.data(), sizeof(FftGroupJob) * fwd.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_inv, inv.data(), sizeof(FftGroupJob) * inv.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_probs, b->h_probs.data(), sizeof(GroupProblem) * b->n_probs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_plan(b);
+    return set_error(QTP_ERR_CUDA, "batch plan set-up: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return QTP_OK;
+}
+
+qtp_status qtp_batch_plan_destroy(qtp_batch_plan* b) {
+  if (!b) return QTP_OK;
+  if (b->cap) cudaStreamSynchronize(b->cap);
+  free_plan(b);
+  return QTP_OK;
+}
+
+qtp_status qtp_batch_workspace_size(const qtp_batch_plan* b, size_t* bytes) {
+  if (!b) return set_error(QTP_ERR_INVALID_ARG, "plan is NULL");
+  if (!bytes) return set_error(QTP_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = b->ws_bytes;
+  return QTP_OK;
+}
+
+qtp_status qtp_forward_batched(qtp_batch_plan* b, const float* const* A, const float* const* B, float* const* C,
+                               void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!b) return set_error(QTP_ERR_INVALID_ARG, "plan is NULL");
+  if (!A || !B || !C) return set_error(QTP_ERR_INVALID_ARG, "pointer arrays must not be NULL");
+  if (!workspace || ((uintptr_t)workspace & 255) != 0)
+    return set_error(QTP_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < b->ws_bytes)
+    return set_error(QTP_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, b->ws_bytes);
+  for (int i = 0; i < b->count; ++i) {
+    const void* ps[3] = {A[i], B[i], C[i]};
+    for (int k = 0; k < 3; ++k)
+      if (!ps[k] || ((uintptr_t)ps[k] & 15) != 0)
+        return set_error(QTP_ERR_INVALID_ARG, "product %d: %c is NULL or not 16-byte aligned", i, "ABC"[k]);
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = (char*)workspace;
+  // stage this call's pointers (the slot's previous copy has finished once its event has)
+  const int slot = b->slot;
+  b->slot ^= 1;
+  BP_CUDA(cudaEventSynchronize(b->staged[slot]), "wait for pointer staging");
+  const float2** hp = b->h_ptrs[slot];
+  for (int i = 0; i < b->count; ++i) {
+    hp[3 * i] = reinterpret_cast<const float2*>(A[i]);
+    hp[3 * i + 1] = reinterpret_cast<const float2*>(B[i]);
+    hp[3 * i + 2] = reinterpret_cast<const float2*>(C[i]);
+  }
+  // the plan's stream follows the caller's stream
+  BP_CUDA(cudaEventRecord(b->ev_in, st), "record entry event");
+  BP_CUDA(cudaStreamWaitEvent(b->cap, b->ev_in, 0), "join plan stream");
+  BP_CUDA(cudaMemcpyAsync(b->d_ptrs, hp, sizeof(float2*) * 3 * b->count, cudaMemcpyHostToDevice, b->cap),
+          "upload pointer table");
+  BP_CUDA(cudaEventRecord(b->staged[slot], b->cap), "record staging event");
+  const bool tc = b->precision != QTP_PREC_FP32;
+  if (tc && b->tmaps_for_ws != ws) {
+    qtp_status r = encode_tmaps(b, ws, b->cap);
+    if (r != QTP_OK) return r;
+    // the next copy into h_tmaps must wait for this one: make it synchronous
+    BP_CUDA(cudaStreamSynchronize(b->cap), "tensor-map upload");
+  }
+  if (b->flags & QTP_BATCH_NO_GRAPH) {
+    qtp_status r = enqueue(b, ws, b->cap);
+    if (r != QTP_OK) return r;
+  } else {
+    if (!b->graph || b->graph_ws != ws || b->graph_tracing != b->tracing) {
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      BP_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+      qtp_status r = enqueue(b, ws, b->cap);
+      cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+      if (r != QTP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (ce != cudaSuccess) return set_error(QTP_ERR_CUDA, "end capture: %s", cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) return set_error(QTP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+      b->graph_ws = ws;
+      b->graph_tracing = b->tracing;
+    }
+    BP_CUDA(cudaGraphLaunch(b->graph, b->cap), "graph launch");
+  }
+  BP_CUDA(cudaEventRecord(b->ev_out, b->cap), "record exit event");
+  BP_CUDA(cudaStreamWaitEvent(st, b->ev_out, 0), "join caller stream");
+  return QTP_OK;
+}
+
+qtp_status qtp_batch_plan_set_tracing(qtp_batch_plan* b, int enable) {
+  if (!b) return set_error(QTP_ERR_INVALID_ARG, "plan is NULL");
+  if (enable && !b->tracing) {
+    for (int i = 0; i < 4; ++i) BP_CUDA(cudaEventCreate(&b->ev[i]), "create trace event");
+    b->tracing = 1;
+  } else if (!enable && b->tracing) {
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    for (int i = 0; i < 4; ++i) {
+      cudaEventDestroy(b->ev[i]);
+      b->ev[i] = nullptr;
+    }
+    b->tracing = 0;
+  }
+  return QTP_OK;
+}
+
+qtp_status qtp_batch_stage_times(const qtp_batch_plan* b, float* ms3) {
+  if (!b) return set_error(QTP_ERR_INVALID_ARG, "plan is NULL");
+  if (!ms3) return set_error(QTP_ERR_INVALID_ARG, "ms3 is NULL");
+  if (!b->tracing) return set_error(QTP_ERR_INVALID_ARG, "tracing is not enabled on this plan");
+  BP_CUDA(cudaEventSynchronize(b->ev[3]), "wait for trace events");
+  for (int i = 0; i < 3; ++i) BP_CUDA(cudaEventElapsedTime(&ms3[i], b->ev[i], b->ev[i + 1]), "stage time");
+  return QTP_OK;
+}
+
+qtp_status qtp_batch_plan_sync(const qtp_batch_plan* b, void* stream) {
+  if (!b) return set_error(QTP_ERR_INVALID_ARG, "plan is NULL");
+  BP_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)), "stream synchronize");
+  BP_CUDA(cudaStreamSynchronize(b->cap), "plan stream synchronize");
+  int v = 0;
+  BP_CUDA(cudaMemcpy(&v, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+  if (v != 0) {
+    cudaMemset(b->d_err, 0, sizeof(int));
+    return set_error(QTP_ERR_TIMEOUT, "a device-side wait gave up (code %d)", v);
+  }
+  return QTP_OK;
+}
+
+}  // extern "C"

@@ -33,223 +33,25 @@ constexpr int kFftThreads = 256;
 constexpr int kFftElemsPerBuf = 4096;  // complex entries per ping-pong buffer
 constexpr int kFftMaxTubes = 512;
 
-// One radix-R Stockham stage for butterfly j of one tube: the inputs sit at
-// stride p/R, are twiddled by w_{Ns R}^(r (j mod Ns)), transformed, and written
-// to (j / Ns) Ns R + (j mod Ns) + r Ns.  Ns is the length already transformed.
-template <int R, bool INV>
-__device__ __forceinline__ void butterfly(const float2* __restrict__ in, float2* __restrict__ out, int j,
-                                          int Ns, int p, const float2* __restrict__ tw) {
-  const int stride = p / R;
-  const int k = j % Ns;
-  const int twstep = p / (Ns * R);
-  float2 v[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    v[r] = in[j + r * stride];
-    if (r > 0 && k > 0) v[r] = cmul(v[r], twid<INV>(tw, r * k * twstep));
-  }
-  Dft<R, INV>::run(v, tw, p);
-  const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-  for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
-}
-
-// Radix that is a prime > 8: direct DFT of length R straight from shared memory.
-template <bool INV>
-__device__ __forceinline__ void butterfly_generic(const float2* __restrict__ in, float2* __restrict__ out,
-                                                  int j, int Ns, int R, int p,
-                                                  const float2* __restrict__ tw) {
-  const int stride = p / R;
-  const int k = j % Ns;
-  const int twstep = p / (Ns * R);
-  const int base = (j / Ns) * Ns * R + k;
-  for (int u = 0; u < R; ++u) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int r = 0; r < R; ++r) {
-      float2 x = in[j + r * stride];
-      if (r > 0 && k > 0) x = cmul(x, twid<INV>(tw, r * k * twstep));
-      const int e = ((r * u) % R) * stride;
-      acc = cadd(acc, e ? cmul(x, twid<INV>(tw, e)) : x);
-    }
-    out[base + u * Ns] = acc;
-  }
-}
-
-// All stages over T tubes held at tube stride P in buf0.  Returns the buffer
-// that holds the result (natural order).
-template <bool INV>
-__device__ float2* run_stages(float2* buf0, float2* buf1, int T, int P, const RadixPlan& rp,
-                              const float2* __restrict__ tw) {
-  const int p = rp.p;
-  float2* in = buf0;
-  float2* out = buf1;
-  int Ns = 1;
-  for (int st = 0; st < rp.nstages; ++st) {
-    const int R = rp.radix[st];
-    const int nb = p / R;  // butterflies per tube
-    const int total = T * nb;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      // tube-fastest: with an odd tube stride P consecutive threads hit
-      // distinct banks for every radix and stage
-      const int j = idx / T;
-      const int tube = idx - j * T;
-      const float2* ti = in + tube * P;
-      float2* to = out + tube * P;
-      switch (R) {
-        case 2: butterfly<2, INV>(ti, to, j, Ns, p, tw); break;
-        case 3: butterfly<3, INV>(ti, to, j, Ns, p, tw); break;
-        case 4: butterfly<4, INV>(ti, to, j, Ns, p, tw); break;
-        case 5: butterfly<5, INV>(ti, to, j, Ns, p, tw); break;
-        case 7: butterfly<7, INV>(ti, to, j, Ns, p, tw); break;
-        case 8: butterfly<8, INV>(ti, to, j, Ns, p, tw); break;
-        default: butterfly_generic<INV>(ti, to, j, Ns, R, p, tw); break;
-      }
-    }
-    __syncthreads();
-    float2* t = in;
-    in = out;
-    out = t;
-    Ns *= R;
-  }
-  return in;
-}
-
 template <int FMT>
 __global__ void __launch_bounds__(kFftThreads) fft_fwd_kernel(FftFwdJob job0, FftFwdJob job1, int njobs,
                                                               RadixPlan rp, int T,
                                                               const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
-  float2* smem = reinterpret_cast<float2*>(smem_f4);
-  const int p = rp.p;
-  const int P = p | 1;
   int b = blockIdx.x;
-  const FftFwdJob& job = (njobs > 1 && b >= job0.nblocks) ? job1 : job0;
-  if (njobs > 1 && b >= job0.nblocks) b -= job0.nblocks;
-  const long long per_plane = (long long)job.rows * job.cols;
-  const long long ntubes = 2 * per_plane;
-  const long long t0 = (long long)b * T;
-  if (t0 >= ntubes) return;
-  const int Tb = (int)min((long long)T, ntubes - t0);
-  float2* buf0 = smem;
-  float2* buf1 = smem + T * P;
-  long long* tube_off = reinterpret_cast<long long*>(smem + 2 * T * P);
-
-  // Contiguous load of Tb tubes (Tb * p complex) into padded rows.
-  const float2* src = job.in + t0 * p;
-  const int n = Tb * p;
-  if ((p & 1) == 0) {
-    const float4* src4 = reinterpret_cast<const float4*>(src);
-    for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-      const float4 v = __ldg(src4 + i);
-      const int e = 2 * i;
-      const int tube = e / p;
-      const int k = e - tube * p;
-      buf0[tube * P + k] = make_float2(v.x, v.y);
-      buf0[tube * P + k + 1] = make_float2(v.z, v.w);
-    }
-  } else {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int tube = i / p;
-      const int k = i - tube * p;
-      buf0[tube * P + k] = __ldg(src + i);
-    }
-  }
-  // Output offset of frequency 0 of every tube (one 64-bit division per tube).
-  const long long ld = job.ld;
-  const long long plane_f_stride = (long long)job.rows * ld;  // one (plane, part, f) slab
-  constexpr int NPARTS = FMT == FMT_BF16X3 ? 4 : (FMT == FMT_BF16 ? 2 : 1);
-  for (int tube = threadIdx.x; tube < Tb; tube += blockDim.x) {
-    const long long t = t0 + tube;
-    const long long plane = t / per_plane;
-    const long long rem = t - plane * per_plane;
-    const long long row = rem / job.cols;
-    const long long col = rem - row * job.cols;
-    tube_off[tube] = plane * NPARTS * p * plane_f_stride + row * ld + col;
-  }
-  __syncthreads();
-  const float2* X = run_stages<false>(buf0, buf1, Tb, P, rp, tw);
-
-  // Frequency-major store: for a fixed f, consecutive tubes are consecutive columns.
-  const long long part = (long long)p * plane_f_stride;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int f = i / Tb;
-    const int tube = i - f * Tb;
-    const float2 v = X[tube * P + f];
-    const long long o = tube_off[tube] + (long long)f * plane_f_stride;
-    if (FMT == FMT_C32) {
-      reinterpret_cast<float2*>(job.out)[o] = v;
-    } else if (FMT == FMT_BF16X3) {
-      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
-      __nv_bfloat16 rh, rl, ih, il;
-      split_bf16(v.x, rh, rl);
-      split_bf16(v.y, ih, il);
-      out[o] = rh;
-      out[o + part] = rl;
-      out[o + 2 * part] = ih;
-      out[o + 3 * part] = il;
-    } else {
-      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
-      out[o] = __float2bfloat16_rn(v.x);
-      out[o + part] = __float2bfloat16_rn(v.y);
-    }
-  }
+  const bool second = njobs > 1 && b >= job0.nblocks;
+  if (second) b -= job0.nblocks;
+  generic_fwd_body<FMT>(second ? job1 : job0, b, rp, T, tw, reinterpret_cast<float2*>(smem_f4));
 }
 
 __global__ void __launch_bounds__(kFftThreads) fft_inv_kernel(FftInvJob job0, FftInvJob job1, int njobs,
                                                               RadixPlan rp, int T,
                                                               const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
-  float2* smem = reinterpret_cast<float2*>(smem_f4);
-  const int p = rp.p;
-  const int P = p | 1;
   int b = blockIdx.x;
-  const FftInvJob& job = (njobs > 1 && b >= job0.nblocks) ? job1 : job0;
-  if (njobs > 1 && b >= job0.nblocks) b -= job0.nblocks;
-  const long long per_plane = (long long)job.rows * job.cols;
-  const long long ntubes = 2 * per_plane;
-  const long long t0 = (long long)b * T;
-  if (t0 >= ntubes) return;
-  const int Tb = (int)min((long long)T, ntubes - t0);
-  float2* buf0 = smem;
-  float2* buf1 = smem + T * P;
-  const int n = Tb * p;
-
-  // Frequency-major gather: spectra in[plane][f][row][col].
-  long long* tube_off = reinterpret_cast<long long*>(smem + 2 * T * P);
-  for (int tube = threadIdx.x; tube < Tb; tube += blockDim.x) {
-    const long long t = t0 + tube;
-    const long long plane = t / per_plane;
-    tube_off[tube] = plane * p * per_plane + (t - plane * per_plane);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int f = i / Tb;
-    const int tube = i - f * Tb;
-    buf0[tube * P + f] = __ldg(job.in + tube_off[tube] + (long long)f * per_plane);
-  }
-  __syncthreads();
-  const float2* X = run_stages<true>(buf0, buf1, Tb, P, rp, tw);
-
-  const float scale = 1.0f / (float)p;
-  float2* dst = job.out + t0 * p;
-  if ((p & 1) == 0) {
-    float4* dst4 = reinterpret_cast<float4*>(dst);
-    for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-      const int e = 2 * i;
-      const int tube = e / p;
-      const int k = e - tube * p;
-      const float2 a = X[tube * P + k];
-      const float2 c = X[tube * P + k + 1];
-      dst4[i] = make_float4(a.x * scale, a.y * scale, c.x * scale, c.y * scale);
-    }
-  } else {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int tube = i / p;
-      const int k = i - tube * p;
-      const float2 a = X[tube * P + k];
-      dst[i] = make_float2(a.x * scale, a.y * scale);
-    }
-  }
+  const bool second = njobs > 1 && b >= job0.nblocks;
+  if (second) b -= job0.nblocks;
+  generic_inv_body(second ? job1 : job0, b, rp, T, tw, reinterpret_cast<float2*>(smem_f4));
 }
 
 __global__ void twiddle_kernel(float2* tw, int p) {
@@ -282,6 +84,12 @@ RadixPlan make_radix_plan(int p) {
     while (q % r == 0) push(r);
   if (q > 1) push(q);
   return rp;
+}
+
+size_t fft_smem_bytes_for(int p) {
+  const size_t fixed = fft_fixed_smem(p);
+  if (fixed) return fixed;
+  return fft_smem_bytes(p, fft_tubes_per_block(p));
 }
 
 int fft_tubes_per_block(int p) {

@@ -106,24 +106,20 @@ __device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const
   }
 }
 
+// Forward transform of the b-th run of T = tubes_for(P) tubes of one tensor.
 template <int P, int FMT>
-__global__ void __launch_bounds__(kThreads) fft_fwd_fixed(FftFwdJob job0, FftFwdJob job1, int njobs,
-                                                          const float2* __restrict__ tw) {
+__device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b, const float2* __restrict__ tw,
+                                               float2* smem) {
   constexpr int T = tubes_for(P);
   constexpr int PP = P | 1;
   constexpr int NPARTS = FMT == FMT_BF16X3 ? 4 : (FMT == FMT_BF16 ? 2 : 1);
-  extern __shared__ float4 smem_f4[];
-  float2* buf0 = reinterpret_cast<float2*>(smem_f4);
+  float2* buf0 = smem;
   float2* buf1 = buf0 + T * PP;
   long long* tube_off = reinterpret_cast<long long*>(buf1 + T * PP);
 
-  int b = blockIdx.x;
-  const bool second = njobs > 1 && b >= job0.nblocks;
-  const FftFwdJob& job = second ? job1 : job0;
-  if (second) b -= job0.nblocks;
   const long long per_plane = (long long)job.rows * job.cols;
   const long long ntubes = 2 * per_plane;
-  const long long t0 = (long long)b * T;
+  const long long t0 = b * T;
   if (t0 >= ntubes) return;
   const int Tb = (int)min((long long)T, ntubes - t0);
 
@@ -215,23 +211,19 @@ __global__ void __launch_bounds__(kThreads) fft_fwd_fixed(FftFwdJob job0, FftFwd
   }
 }
 
+// Inverse transform (scale 1/P) of the b-th run of T = tubes_for(P) tubes.
 template <int P>
-__global__ void __launch_bounds__(kThreads) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
-                                                          const float2* __restrict__ tw) {
+__device__ __forceinline__ void fixed_inv_body(const FftInvJob& job, long long b, const float2* __restrict__ tw,
+                                               float2* smem) {
   constexpr int T = tubes_for(P);
   constexpr int PP = P | 1;
-  extern __shared__ float4 smem_f4[];
-  float2* buf0 = reinterpret_cast<float2*>(smem_f4);
+  float2* buf0 = smem;
   float2* buf1 = buf0 + T * PP;
   long long* tube_off = reinterpret_cast<long long*>(buf1 + T * PP);
 
-  int b = blockIdx.x;
-  const bool second = njobs > 1 && b >= job0.nblocks;
-  const FftInvJob& job = second ? job1 : job0;
-  if (second) b -= job0.nblocks;
   const long long per_plane = (long long)job.rows * job.cols;
   const long long ntubes = 2 * per_plane;
-  const long long t0 = (long long)b * T;
+  const long long t0 = b * T;
   if (t0 >= ntubes) return;
   const int Tb = (int)min((long long)T, ntubes - t0);
 
@@ -284,6 +276,100 @@ __global__ void __launch_bounds__(kThreads) fft_inv_fixed(FftInvJob job0, FftInv
 }
 
 template <int P, int FMT>
+__global__ void __launch_bounds__(kThreads) fft_fwd_fixed(FftFwdJob job0, FftFwdJob job1, int njobs,
+                                                          const float2* __restrict__ tw) {
+  extern __shared__ float4 smem_f4[];
+  int b = blockIdx.x;
+  const bool second = njobs > 1 && b >= job0.nblocks;
+  if (second) b -= job0.nblocks;
+  fixed_fwd_body<P, FMT>(second ? job1 : job0, b, tw, reinterpret_cast<float2*>(smem_f4));
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
+                                                          const float2* __restrict__ tw) {
+  extern __shared__ float4 smem_f4[];
+  int b = blockIdx.x;
+  const bool second = njobs > 1 && b >= job0.nblocks;
+  if (second) b -= job0.nblocks;
+  fixed_inv_body<P>(second ? job1 : job0, b, tw, reinterpret_cast<float2*>(smem_f4));
+}
+
+// ---------------------------------------------------------------------------
+// Grouped transforms for batches of products with mixed (rows, cols, p): one
+// launch covers every tensor of the batch; each CTA finds its job by binary
+// search over the jobs' first block and runs the body specialised for that
+// job's p (or the runtime-radix body).  Tensor pointers come from a per-call
+// device table ptrs[3 * product + {0: A, 1: B, 2: C}].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_job(const FftGroupJob* __restrict__ jobs, int njobs, long long b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].block_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(kThreads) fft_fwd_grouped(const FftGroupJob* __restrict__ jobs, int njobs,
+                                                            const float2* const* __restrict__ ptrs, char* ws,
+                                                            const float2* __restrict__ tw_all) {
+  extern __shared__ float4 smem_f4[];
+  float2* smem = reinterpret_cast<float2*>(smem_f4);
+  const long long b = blockIdx.x;
+  const FftGroupJob& J = jobs[find_job(jobs, njobs, b)];
+  FftFwdJob job;
+  job.in = ptrs[3 * J.prod + J.which];
+  job.out = ws + J.spec_off;
+  job.rows = J.rows;
+  job.cols = J.cols;
+  job.ld = J.ld;
+  job.nblocks = 0;
+  const long long lb = b - J.block_begin;
+  const float2* tw = tw_all + J.tw_off;
+  switch (J.p) {
+    case 8: fixed_fwd_body<8, FMT>(job, lb, tw, smem); break;
+    case 12: fixed_fwd_body<12, FMT>(job, lb, tw, smem); break;
+    case 16: fixed_fwd_body<16, FMT>(job, lb, tw, smem); break;
+    case 31: fixed_fwd_body<31, FMT>(job, lb, tw, smem); break;
+    case 32: fixed_fwd_body<32, FMT>(job, lb, tw, smem); break;
+    case 64: fixed_fwd_body<64, FMT>(job, lb, tw, smem); break;
+    case 100: fixed_fwd_body<100, FMT>(job, lb, tw, smem); break;
+    case 128: fixed_fwd_body<128, FMT>(job, lb, tw, smem); break;
+    default: generic_fwd_body<FMT>(job, lb, J.rp, J.T, tw, smem); break;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) fft_inv_grouped(const FftGroupJob* __restrict__ jobs, int njobs,
+                                                            const float2* const* __restrict__ ptrs, char* ws,
+                                                            const float2* __restrict__ tw_all) {
+  extern __shared__ float4 smem_f4[];
+  float2* smem = reinterpret_cast<float2*>(smem_f4);
+  const long long b = blockIdx.x;
+  const FftGroupJob& J = jobs[find_job(jobs, njobs, b)];
+  FftInvJob job;
+  job.in = reinterpret_cast<const float2*>(ws + J.spec_off);
+  job.out = const_cast<float2*>(ptrs[3 * J.prod + J.which]);
+  job.rows = J.rows;
+  job.cols = J.cols;
+  job.nblocks = 0;
+  const long long lb = b - J.block_begin;
+  const float2* tw = tw_all + J.tw_off;
+  switch (J.p) {
+    case 8: fixed_inv_body<8>(job, lb, tw, smem); break;
+    case 12: fixed_inv_body<12>(job, lb, tw, smem); break;
+    case 16: fixed_inv_body<16>(job, lb, tw, smem); break;
+    case 31: fixed_inv_body<31>(job, lb, tw, smem); break;
+    case 32: fixed_inv_body<32>(job, lb, tw, smem); break;
+    case 64: fixed_inv_body<64>(job, lb, tw, smem); break;
+    case 100: fixed_inv_body<100>(job, lb, tw, smem); break;
+    case 128: fixed_inv_body<128>(job, lb, tw, smem); break;
+    default: generic_inv_body(job, lb, J.rp, J.T, tw, smem); break;
+  }
+}
+
+template <int P, int FMT>
 cudaError_t fwd_launch(const FftFwdJob* jobs, int njobs, const float2* tw, cudaStream_t st) {
   constexpr size_t smem = smem_for<P>();
   cudaError_t e = cudaFuncSetAttribute(fft_fwd_fixed<P, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -318,6 +404,56 @@ cudaError_t inv_launch(const FftInvJob* jobs, int njobs, const float2* tw, cudaS
 }
 
 }  // namespace
+
+size_t fft_fixed_smem(int p) {
+  switch (p) {
+    case 8: return smem_for<8>();
+    case 12: return smem_for<12>();
+    case 16: return smem_for<16>();
+    case 31: return smem_for<31>();
+    case 32: return smem_for<32>();
+    case 64: return smem_for<64>();
+    case 100: return smem_for<100>();
+    case 128: return smem_for<128>();
+    default: return 0;
+  }
+}
+
+cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, int njobs, long long nblocks, int fmt,
+                                   const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
+                                   cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  switch (fmt) {
+    case FMT_C32:
+      e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_C32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) fft_fwd_grouped<FMT_C32><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, njobs, d_ptrs, ws, d_tw);
+      break;
+    case FMT_BF16X3:
+      e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) fft_fwd_grouped<FMT_BF16X3><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, njobs, d_ptrs, ws, d_tw);
+      break;
+    case FMT_BF16:
+      e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) fft_fwd_grouped<FMT_BF16><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, njobs, d_ptrs, ws, d_tw);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, int njobs, long long nblocks,
+                                   const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
+                                   cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fft_inv_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fft_inv_grouped<<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, njobs, d_ptrs, ws, d_tw);
+  return cudaGetLastError();
+}
 
 int fft_fixed_tubes(int p) {
   switch (p) {

@@ -1,0 +1,363 @@
+// Per-frequency products of Algorithm 5.1 Step 2 for a batch of products with
+// uneven (m, n, s, p): one persistent tcgen05 launch (split-BF16, forward).
+//
+// All tiles of all products form one index space; product g owns
+// [tile_begin_g, tile_begin_g + tiles_m * tiles_n * 2 * p_g), ordered
+// (frequency, output half, row tile, column tile).  CTA i (one per SM) takes
+// tiles i, i + grid, i + 2 grid, ...  Roles as in the single-product kernel:
+// warp 0 issues TMA, warp 1 issues tcgen05.mma, warps 2-5 drain TMEM.  Here
+// the TMA producer runs straight on from one tile's K loop into the next
+// tile's (the 6-stage ring never drains between tiles) and TMEM holds two
+// accumulator pairs, so the epilogue of one tile overlaps the MMAs of the
+// next.  Each product has its own two tensor maps, kept in device memory and
+// acquired for the async proxy before use.  All waits are bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "qtp_internal.h"
+#include "qtp_tc_common.cuh"
+
+namespace qtp {
+
+namespace {
+
+using namespace tcdev;
+
+constexpr int GBM = kGroupTcBM;          // 128 rows
+constexpr int GBN = kGroupTcBN;          // 128 complex columns
+constexpr int GBK = 16;                  // K per stage
+constexpr int GSTAGES = 6;
+constexpr int G_A_TILE = GBM * GBK * 2;  // 4 KB per bf16 part
+constexpr int G_B_TILE = GBK * GBN * 2;  // 4 KB per bf16 part
+constexpr int kGThreads = 192;
+constexpr uint32_t G_TMEM_COLS = 512;    // 2 buffers x (re, im) x 128 columns
+
+// Operand roles of the forward product per (output half h, K half kh): A and B
+// planes, whether B is read at frequency -f, and which of the four real
+// products (ar.br, ai.bi, ar.bi, ai.br) is subtracted.  Filled on the host.
+struct GViews {
+  int a_plane[2][2];
+  int b_plane[2][2];
+  int b_fneg[2][2];
+  uint32_t negmask[2][2];
+};
+
+struct GTile {
+  int g, f, h, mt, nt;
+};
+
+__device__ __forceinline__ GTile decode_tile(const GroupProblem* __restrict__ probs, int nprobs, long long t) {
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  const GroupProblem& P = probs[lo];
+  long long local = t - P.tile_begin;
+  GTile r;
+  r.g = lo;
+  r.nt = (int)(local % P.tiles_n);
+  local /= P.tiles_n;
+  r.mt = (int)(local % P.tiles_m);
+  local /= P.tiles_m;
+  r.h = (int)(local & 1);
+  r.f = (int)(local >> 1);
+  return r;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kGThreads, 1)
+    gemm_tc_grouped_kernel(const GroupProblem* __restrict__ probs, int nprobs, long long total_tiles, char* ws,
+                           int* err, const GViews V) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ int abort_flag;
+
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t sA = base;
+  const uint32_t sB = base + GSTAGES * NP * G_A_TILE;
+  const uint32_t bars = sB + GSTAGES * NP * G_B_TILE;
+  const uint32_t full = bars, empty = bars + 8 * GSTAGES;
+  const uint32_t acc_full = bars + 16 * GSTAGES;      // 2 barriers
+  const uint32_t acc_empty = acc_full + 16;           // 2 barriers
+  const uint32_t mma_done = acc_empty + 16;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GSTAGES; ++s) {
+      mbar_init(full + 8 * s, 1);
+      mbar_init(empty + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full + 8 * b, 1);
+      mbar_init(acc_empty + 8 * b, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(mma_done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
+                 "r"(G_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      long long it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+        const GTile T = decode_tile(probs, nprobs, t);
+        const GroupProblem& P = probs[T.g];
+        const CUtensorMap* tmA = reinterpret_cast<const CUtensorMap*>(P.tmA);
+        const CUtensorMap* tmB = reinterpret_cast<const CUtensorMap*>(P.tmB);
+        tensormap_acquire(tmA);
+        tensormap_acquire(tmB);
+        const int nkb = (P.K + GBK - 1) / GBK;
+        for (int kk = 0; kk < 2 * nkb; ++kk, ++it) {
+          const int kh = kk / nkb;
+          const int k0 = (kk - kh * nkb) * GBK;
+          const int s = (int)(it % GSTAGES);
+          const uint32_t ph = (uint32_t)(it / GSTAGES) & 1u;
+          if (!mbar_wait(empty + 8 * s, ph ^ 1u)) {
+            atomicExch(err, QTP_DEVERR_TIMEOUT_EMPTY);
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          if (*(volatile int*)&abort_flag) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full + 8 * s, (uint32_t)(NP * (G_A_TILE + G_B_TILE)));
+          const int ga = T.f;
+          const int gb = V.b_fneg[T.h][kh] ? (P.p - T.f) % P.p : T.f;
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const uint32_t ta = sA + (uint32_t)(s * NP + q) * G_A_TILE;
+            const uint32_t tb = sB + (uint32_t)(s * NP + q) * G_B_TILE;
+            tma_load_4d(ta, tmA, full + 8 * s, k0, T.mt * GBM, ga, V.a_plane[T.h][kh] * NP + q);
+            tma_load_4d(tb, tmB, full + 8 * s, T.nt * GBN, k0, gb, V.b_plane[T.h][kh] * NP + q);
+            tma_load_4d(tb + 128u * GBK, tmB, full + 8 * s, T.nt * GBN + 64, k0, gb, V.b_plane[T.h][kh] * NP + q);
+          }
+        }
+      }
+      if (!ok) {  // never leave with copies in flight
+        const long long first = it - GSTAGES < 0 ? 0 : it - GSTAGES;
+        for (long long j = first; j < it; ++j) mbar_wait(full + 8 * (int)(j % GSTAGES), (uint32_t)(j / GSTAGES) & 1u);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(false, true, GBN);
+      long long it = 0;
+      int lt = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++lt) {
+        const GTile T = decode_tile(probs, nprobs, t);
+        const int K = probs[T.g].K;
+        const int nkb = (K + GBK - 1) / GBK;
+        const int buf = lt & 1;
+        const uint32_t uph = (uint32_t)(lt >> 1) & 1u;
+        if (!mbar_wait(acc_empty + 8 * buf, uph ^ 1u)) {
+          atomicExch(err, QTP_DEVERR_TIMEOUT_ACC);
+          atomicExch(&abort_flag, 1);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t d_re = tmem + (uint32_t)(buf * 2 * GBN);
+        const uint32_t d_im = d_re + (uint32_t)GBN;
+        uint32_t acc_re = 0, acc_im = 0;
+        for (int kk = 0; kk < 2 * nkb; ++kk, ++it) {
+          const int kh = kk / nkb;
+          const int s = (int)(it % GSTAGES);
+          const uint32_t ph = (uint32_t)(it / GSTAGES) & 1u;
+          if (!mbar_wait(full + 8 * s, ph)) {
+            atomicExch(err, QTP_DEVERR_TIMEOUT_FULL);
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t neg = V.negmask[T.h][kh];
+          const uint32_t ta = sA + (uint32_t)(s * NP) * G_A_TILE;
+          const uint32_t tb = sB + (uint32_t)(s * NP) * G_B_TILE;
+          const int RE = 0, IM = NP / 2;
+#pragma unroll
+          for (int prod = 0; prod < 4; ++prod) {
+            const int xa = (prod == 0 || prod == 2) ? RE : IM;
+            const int yb = (prod == 0 || prod == 3) ? RE : IM;
+            const bool to_re = prod < 2;
+            const uint32_t id = idesc | (((neg >> prod) & 1u) ? kNegA : 0u);
+            const uint32_t d = to_re ? d_re : d_im;
+            uint32_t& acc = to_re ? acc_re : acc_im;
+            const uint64_t a_hi = part_desc<false, GBK>(ta + (uint32_t)xa * G_A_TILE, 0);
+            const uint64_t b_hi = part_desc<true, GBK>(tb + (uint32_t)yb * G_B_TILE, 0);
+            mma_bf16(d, a_hi, b_hi, id, acc);
+            acc = 1;
+            if (NP == 4) {
+              const uint64_t a_lo = part_desc<false, GBK>(ta + (uint32_t)(xa + 1) * G_A_TILE, 0);
+              const uint64_t b_lo = part_desc<true, GBK>(tb + (uint32_t)(yb + 1) * G_B_TILE, 0);
+              mma_bf16(d, a_hi, b_lo, id, 1);
+              mma_bf16(d, a_lo, b_hi, id, 1);
+            }
+          }
+          mma_commit(empty + 8 * s);
+        }
+        if (!ok) break;
+        mma_commit(acc_full + 8 * buf);
+      }
+      if (!ok) {
+        mma_commit(mma_done);
+        mbar_wait(mma_done, 0);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    int lt = 0;
+    for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
+      const GTile T = decode_tile(probs, nprobs, t);
+      const GroupProblem& P = probs[T.g];
+      const int buf = lt & 1;
+      const uint32_t uph = (uint32_t)(lt >> 1) & 1u;
+      if (!mbar_wait(acc_full + 8 * buf, uph)) {
+        if (lane == 0) {
+          atomicExch(err, QTP_DEVERR_TIMEOUT_ACC);
+          atomicExch(&abort_flag, 1);
+        }
+        break;
+      }
+      fence_after();
+      const int row = T.mt * GBM + q * 32 + lane;
+      float2* out = reinterpret_cast<float2*>(ws + P.out_off) + (long long)T.h * P.p * P.M * P.N +
+                    (long long)T.f * P.M * P.N;
+      const uint32_t tb = tmem + (uint32_t)(buf * 2 * GBN) + lane_off;
+#pragma unroll 1
+      for (int c0 = 0; c0 < GBN; c0 += 32) {
+        uint32_t re[32], im[32];
+        tmem_ld32(tb + (uint32_t)c0, re);
+        tmem_ld32(tb + (uint32_t)(GBN + c0), im);
+        if (row < P.M) {
+          float2* o = out + (long long)row * P.N;
+          const int col0 = T.nt * GBN + c0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j < P.N) o[col0 + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty + 8 * buf);
+      if (*(volatile int*)&abort_flag) break;
+    }
+    fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G_TMEM_COLS) : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+}  // namespace
+
+// Spectra tensor [plane][part][f][rows][ld] (bf16) as a 4-D tensor map for
+// the grouped kernel: box (16, 128) with the 32-byte swizzle for the K-major A
+// operand, (64, 16) with the 128-byte swizzle for the MN-major B operand.
+bool encode_group_map(void* tm, const void* base, int rows, int cols, int ld, int p, int nparts, bool mn_major,
+                      char* msg, size_t msglen) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) {
+    snprintf(msg, msglen, "cuTensorMapEncodeTiled unavailable");
+    return false;
+  }
+  cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)p, (cuuint64_t)(2 * nparts)};
+  cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * rows, (cuuint64_t)ld * 2 * rows * p};
+  cuuint32_t box[4] = {mn_major ? 64u : (cuuint32_t)GBK, mn_major ? (cuuint32_t)GBK : (cuuint32_t)GBM, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(tm), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base),
+                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   mn_major ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    snprintf(msg, msglen, "cuTensorMapEncodeTiled failed (%d) rows=%d cols=%d ld=%d", (int)r, rows, cols, ld);
+    return false;
+  }
+  return true;
+}
+
+cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, int nparts,
+                                   char* ws, int* d_err, int num_ctas, cudaStream_t st) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const int np = nparts == 4 ? 4 : 2;
+  const size_t smem = (size_t)GSTAGES * np * (G_A_TILE + G_B_TILE) + 1024 + 256;
+  const int grid = (int)(total_tiles < num_ctas ? total_tiles : num_ctas);
+  // Forward product (Thm 5.1): C1 = A1 B1 - A2 conj(B2(-f)), C2 = A1 B2 + A2 conj(B1(-f)).
+  // (tau ar + i tau ai)(br + i sb bi): re += tau ar.br - tau sb ai.bi, im += tau sb ar.bi + tau ai.br
+  GViews V;
+  const int a_plane[2][2] = {{0, 1}, {0, 1}};
+  const int b_plane[2][2] = {{0, 1}, {1, 0}};
+  const int b_conj[2][2] = {{0, 1}, {0, 1}};
+  const float sign[2][2] = {{1.f, -1.f}, {1.f, 1.f}};
+  for (int h = 0; h < 2; ++h)
+    for (int kh = 0; kh < 2; ++kh) {
+      V.a_plane[h][kh] = a_plane[h][kh];
+      V.b_plane[h][kh] = b_plane[h][kh];
+      V.b_fneg[h][kh] = b_conj[h][kh];  // the conjugated B operand is the one read at -f
+      const float tau = sign[h][kh];
+      const float sb = b_conj[h][kh] ? -1.f : 1.f;
+      const float c[4] = {tau, -tau * sb, tau * sb, tau};
+      uint32_t mask = 0;
+      for (int q = 0; q < 4; ++q)
+        if (c[q] < 0) mask |= 1u << q;
+      V.negmask[h][kh] = mask;
+    }
+  cudaError_t e;
+  if (np == 4) {
+    e = cudaFuncSetAttribute(gemm_tc_grouped_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gemm_tc_grouped_kernel<4><<<grid, kGThreads, smem, st>>>(d_probs, nprobs, total_tiles, ws, d_err, V);
+  } else {
+    e = cudaFuncSetAttribute(gemm_tc_grouped_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gemm_tc_grouped_kernel<2><<<grid, kGThreads, smem, st>>>(d_probs, nprobs, total_tiles, ws, d_err, V);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace qtp

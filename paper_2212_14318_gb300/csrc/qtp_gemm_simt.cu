@@ -24,13 +24,10 @@ constexpr int BN = 128;
 constexpr int BK = 8;
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmProblem pr) {
+// One BM x BN complex output tile (frequency f, output half h, origin m0, n0).
+__device__ __forceinline__ void simt_tile(const GemmProblem& pr, int f, int h, int m0, int n0) {
   __shared__ __align__(16) float2 As[BK][BM];
   __shared__ __align__(16) float2 Bs[BK][BN];
-  const int f = blockIdx.z >> 1;
-  const int h = blockIdx.z & 1;
-  const int m0 = blockIdx.y * BM;
-  const int n0 = blockIdx.x * BN;
   const int tx = threadIdx.x & 15;
   const int ty = threadIdx.x >> 4;
   const int p = pr.p;
@@ -119,7 +116,63 @@ __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmProblem pr) {
   }
 }
 
+__global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmProblem pr) {
+  simt_tile(pr, blockIdx.z >> 1, blockIdx.z & 1, blockIdx.y * BM, blockIdx.x * BN);
+}
+
+// Batched forward products: one CTA per tile of the global tile space (see
+// GroupProblem); the CTA rebuilds its product's operand views from the
+// workspace offsets: C1 = A1 B1 - A2 conj(B2(-f)), C2 = A1 B2 + A2 conj(B1(-f)).
+__global__ void __launch_bounds__(kThreads) gemm_simt_grouped_kernel(const GroupProblem* __restrict__ probs,
+                                                                     int nprobs, char* ws) {
+  const long long t = blockIdx.x;
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  const GroupProblem& P = probs[lo];
+  long long local = t - P.tile_begin;
+  const int nt = (int)(local % P.tiles_n);
+  local /= P.tiles_n;
+  const int mt = (int)(local % P.tiles_m);
+  local /= P.tiles_m;
+  const int h = (int)(local & 1);
+  const int f = (int)(local >> 1);
+  const long long m = P.M, n = P.K, s = P.N, p = P.p;
+  const float2* A = reinterpret_cast<const float2*>(ws + P.sa_off);
+  const float2* B = reinterpret_cast<const float2*>(ws + P.sb_off);
+  GemmProblem pr;
+  pr.M = P.M; pr.N = P.N; pr.K = P.K; pr.p = P.p;
+  for (int hh = 0; hh < 2; ++hh)
+    for (int kh = 0; kh < 2; ++kh) {
+      CView a;
+      a.base = A + kh * p * m * n;
+      a.fstride = m * n; a.rstride = n; a.kstride = 1; a.fneg = 0; a.conj = 0;
+      pr.a[hh][kh] = a;
+      CView b;
+      const int plane = (hh == kh) ? 0 : 1;  // h0: B1, B2(-f); h1: B2, B1(-f)
+      b.base = B + plane * p * n * s;
+      b.fstride = n * s; b.rstride = 1; b.kstride = s; b.fneg = kh; b.conj = kh;
+      pr.b[hh][kh] = b;
+      pr.sign[hh][kh] = (hh == 0 && kh == 1) ? -1.f : 1.f;
+    }
+  pr.out = reinterpret_cast<float2*>(ws + P.out_off);
+  pr.out_hstride = p * m * s;
+  pr.out_fstride = m * s;
+  pr.out_rstride = s;
+  simt_tile(pr, f, h, mt * BM, nt * BN);
+}
+
 }  // namespace
+
+cudaError_t launch_gemm_simt_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, char* ws,
+                                     cudaStream_t st) {
+  if (total_tiles <= 0) return cudaSuccess;
+  if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  gemm_simt_grouped_kernel<<<(unsigned)total_tiles, kThreads, 0, st>>>(d_probs, nprobs, ws);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_simt(const GemmProblem& pr, cudaStream_t st) {
   if (pr.M <= 0 || pr.N <= 0 || pr.p <= 0) return cudaSuccess;

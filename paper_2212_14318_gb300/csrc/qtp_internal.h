@@ -54,6 +54,27 @@ struct FftInvJob {
 };
 
 int fft_tubes_per_block(int p);
+size_t fft_smem_bytes_for(int p);  // dynamic shared memory of one FFT CTA for tube length p
+
+// Grouped (batched) tube FFTs: one job per tensor of each product.
+struct FftGroupJob {
+  long long block_begin;  // first global CTA of this job
+  long long spec_off;     // byte offset of this tensor's spectra in the workspace
+  int prod;               // product index into the per-call pointer table
+  int which;              // 0 = A, 1 = B (forward input), 2 = C (inverse output)
+  int rows, cols, ld, p;
+  int T;                  // tubes per CTA for this p
+  int tw_off;             // first entry of this p's twiddle table
+  RadixPlan rp;           // for tube lengths without a compile-time kernel
+};
+
+cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, int njobs, long long nblocks, int fmt,
+                                   const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
+                                   cudaStream_t st);
+cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, int njobs, long long nblocks,
+                                   const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
+                                   cudaStream_t st);
+size_t fft_fixed_smem(int p);
 
 // Compile-time specialisations (qtp_fft_fixed.cu) for the common tube lengths:
 // tubes per CTA, or 0 when p has none; the launches return
@@ -125,7 +146,43 @@ struct TcProblem {
   const void* b_base[2]; int b_rows[2], b_cols[2], b_ld[2];
 };
 
+// Grouped (batched) per-frequency products, forward only: product g reads its
+// spectra at workspace offsets and writes C_hat at out_off.  Tiles of all
+// products form one index space; product g owns tiles
+// [tile_begin, tile_begin + tiles_m * tiles_n * 2 * p), ordered (f, h, mt, nt)
+// with nt fastest.
+struct GroupProblem {
+  long long tile_begin;
+  long long sa_off, sb_off, out_off;  // byte offsets in the workspace
+  const void* tmA;                    // tensor maps (device memory), tensor-core path only
+  const void* tmB;
+  int M, N, K, p;
+  int tiles_m, tiles_n;
+  int lda, ldb;                       // spectra row strides (elements)
+};
+
+cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, int nparts,
+                                   char* ws, int* d_err, int num_ctas, cudaStream_t st);
+cudaError_t launch_gemm_simt_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, char* ws,
+                                     cudaStream_t st);
+// Tile shapes of the grouped kernels (rows x complex columns).
+constexpr int kGroupTcBM = 128, kGroupTcBN = 128;
+constexpr int kGroupSimtBM = 64, kGroupSimtBN = 128;
+// Tensor map of a spectra tensor for the grouped tensor-core kernel (K-major A
+// or MN-major B), written to host memory at *tm (128 bytes).
+bool encode_group_map(void* tm, const void* base, int rows, int cols, int ld, int p, int nparts, bool mn_major,
+                      char* msg, size_t msglen);
+
 bool tc_supported();
+
+// Shared host helpers (qtp_api.cu): thread-local error message, spectra layout.
+qtp_status set_error(qtp_status st, const char* fmt, ...);
+void clear_error();
+int spec_format_of(int precision);
+long long spec_ld_of(int fmt, long long cols);
+size_t spec_bytes_of(int fmt, long long p, long long rows, long long cols);
+size_t c32_bytes_of(long long p, long long rows, long long cols);
+
 cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, char* msg, size_t msglen);
 
 }  // namespace qtp

@@ -39,6 +39,13 @@ SIGNATURES = {
     "qtp_plan_set_tracing": (_i, [_vp, _i]),
     "qtp_plan_stage_times": (_i, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "qtp_forward_noalloc": (_i, [_i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "qtp_batch_plan_create": (_i, [ctypes.POINTER(_vp), _vp, _i, _i, ctypes.c_uint]),
+    "qtp_batch_plan_destroy": (_i, [_vp]),
+    "qtp_batch_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
+    "qtp_forward_batched": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "qtp_batch_plan_set_tracing": (_i, [_vp, _i]),
+    "qtp_batch_stage_times": (_i, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "qtp_batch_plan_sync": (_i, [_vp, _vp]),
     "qtp_last_error": (ctypes.c_char_p, []),
     "qtp_version": (_i, []),
 }
@@ -188,6 +195,83 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().qtp_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("s", ctypes.c_int), ("p", ctypes.c_int)]
+
+
+BATCH_NO_GRAPH = 1
+
+
+class BatchPlan:
+    """A qtp_batch_plan: many independent products C_i = A_i * B_i of uneven shapes."""
+
+    def __init__(self, shapes, precision: str = "bf16x3", graph: bool = True):
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {list(PRECISIONS)}")
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        self.precision = precision
+        arr = (Shape * len(self.shapes))(*[Shape(*sh) for sh in self.shapes])
+        h = ctypes.c_void_p()
+        _check(lib().qtp_batch_plan_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(self.shapes),
+                                           PRECISIONS[precision], 0 if graph else BATCH_NO_GRAPH),
+               "qtp_batch_plan_create")
+        self._h = h
+        self._ws = None
+
+    def workspace_size(self) -> int:
+        v = ctypes.c_size_t()
+        _check(lib().qtp_batch_workspace_size(self._h, ctypes.byref(v)), "qtp_batch_workspace_size")
+        return int(v.value)
+
+    def forward(self, As, Bs, Cs=None, workspace=None, stream=None):
+        import torch
+        n = len(self.shapes)
+        if len(As) != n or len(Bs) != n:
+            raise ValueError("one A and one B per product")
+        if Cs is None:
+            Cs = [torch.empty((2, m, s, p, 2), dtype=torch.float32, device=As[0].device)
+                  for (m, _, s, p) in self.shapes]
+        for i, (m, k, s, p) in enumerate(self.shapes):
+            _check_tensor(As[i], (2, m, k, p, 2), f"A[{i}]")
+            _check_tensor(Bs[i], (2, k, s, p, 2), f"B[{i}]")
+            _check_tensor(Cs[i], (2, m, s, p, 2), f"C[{i}]")
+        pa = (ctypes.c_void_p * n)(*[t.data_ptr() for t in As])
+        pb = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Bs])
+        pc = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Cs])
+        if workspace is None:
+            need = self.workspace_size()
+            if self._ws is None or self._ws.numel() < need:
+                self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=As[0].device)
+            workspace = self._ws
+        _check(lib().qtp_forward_batched(self._h, ctypes.cast(pa, ctypes.c_void_p), ctypes.cast(pb, ctypes.c_void_p),
+                                         ctypes.cast(pc, ctypes.c_void_p), _ptr(workspace),
+                                         workspace.numel() * workspace.element_size(), _stream(stream)),
+               "qtp_forward_batched")
+        return Cs
+
+    def set_tracing(self, enable: bool = True):
+        _check(lib().qtp_batch_plan_set_tracing(self._h, 1 if enable else 0), "qtp_batch_plan_set_tracing")
+
+    def stage_times(self):
+        buf = (ctypes.c_float * 3)()
+        _check(lib().qtp_batch_stage_times(self._h, buf), "qtp_batch_stage_times")
+        return [float(x) for x in buf]
+
+    def sync(self, stream=None):
+        _check(lib().qtp_batch_plan_sync(self._h, _stream(stream)), "qtp_batch_plan_sync")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().qtp_batch_plan_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -93,3 +93,16 @@ def sample_columns(s: int, count: int, seed: int = SEED_SAMPLE):
     """Distinct random lateral column indices t for sampled checks of C(:, t, :)."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(s, size=min(count, s), replace=False))
+
+
+def batch_tensors(shapes, seed: int = SEED_A, device="cuda"):
+    """N(0,1) inputs (A_i, B_i) for a batch, drawn on the device by torch's
+    seeded generator (the batch holds tens of GB); plane layout per tensor."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    As, Bs = [], []
+    for (m, n, s, p) in shapes:
+        As.append(torch.randn((2, m, n, p, 2), generator=g, device=device, dtype=torch.float32))
+        Bs.append(torch.randn((2, n, s, p, 2), generator=g, device=device, dtype=torch.float32))
+    return As, Bs
