@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--workload", default="video", choices=["video", "precision", "small", "diff", "batch"])
+    ap.add_argument("--batch-count", type=int, default=4096, help="products in the batch workload")
     return ap.parse_args()
 
 
@@ -398,7 +399,7 @@ def run_batch(args):
     import oracle as Q
     from paper_2212_14318_gb300 import qtp, synth
     dev = torch.device("cuda", 0)
-    shapes = synth.batch_shapes()
+    shapes = synth.batch_shapes(args.batch_count)
     As, Bs = synth.batch_tensors(shapes)
     flops = sum(effective_flops(*sh) for sh in shapes)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -434,7 +435,7 @@ def run_batch(args):
     def sampled_err(Cs):
         rng = np.random.default_rng(7)
         num = den = 0.0
-        for i in rng.choice(len(shapes), 256, replace=False):
+        for i in rng.choice(len(shapes), min(256, len(shapes)), replace=False):
             m, n, s, p = shapes[i]
             ii, tt, kk = rng.integers(0, m), rng.integers(0, s), rng.integers(0, p)
             a = As[i][:, ii:ii + 1].cpu().numpy().astype(np.float64)

@@ -26,6 +26,8 @@ LIB = os.path.join(LIBDIR, "libqtp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
           "-I" + os.path.join(ROOT, "include")]
+# Extra nvcc flags for tuning builds (e.g. "-DQTP_FFT_ELEMS=2304"); part of the build hash.
+CFLAGS += os.environ.get("QTP_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:

@@ -37,6 +37,9 @@ struct qtp_batch_plan {
   float2* d_tw = nullptr;
   FftGroupJob* d_fwd = nullptr;
   FftGroupJob* d_inv = nullptr;
+  int* d_fwd_job = nullptr;   // job index of every CTA of the grouped FFTs
+  int* d_inv_job = nullptr;
+  int* d_prob_tile = nullptr; // product of every tile of the grouped FP32 products
   GroupProblem* d_probs = nullptr;
   void* d_tmaps = nullptr;  // 2 x 128 B per product (tensor-core path)
   const float2** d_ptrs = nullptr;
@@ -88,6 +91,9 @@ void free_plan(qtp_batch_plan* b) {
   cudaFree(b->d_tw);
   cudaFree(b->d_fwd);
   cudaFree(b->d_inv);
+  cudaFree(b->d_fwd_job);
+  cudaFree(b->d_inv_job);
+  cudaFree(b->d_prob_tile);
   cudaFree(b->d_probs);
   cudaFree(b->d_tmaps);
   cudaFree(b->d_ptrs);
@@ -95,23 +101,31 @@ void free_plan(qtp_batch_plan* b) {
   delete b;
 }
 
+// Trace event i on st.  While st is capturing a graph, the record must be an
+// external event-record node, or the host could not wait on it later.
+void trace(qtp_batch_plan* b, int i, cudaStream_t st, bool capturing) {
+  if (!b->tracing) return;
+  if (capturing) cudaEventRecordWithFlags(b->ev[i], st, cudaEventRecordExternal);
+  else cudaEventRecord(b->ev[i], st);
+}
+
 // The three grouped launches of one forward call, on stream st.
-qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st) {
-  if (b->tracing) cudaEventRecord(b->ev[0], st);
-  BP_CUDA(launch_fft_fwd_grouped(b->d_fwd, b->n_fwd, b->fwd_blocks, b->fmt, b->d_ptrs, ws, b->d_tw, b->fft_smem, st),
+qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing) {
+  trace(b, 0, st, capturing);
+  BP_CUDA(launch_fft_fwd_grouped(b->d_fwd, b->d_fwd_job, b->fwd_blocks, b->fmt, b->d_ptrs, ws, b->d_tw, b->fft_smem, st),
           "batched forward FFT");
-  if (b->tracing) cudaEventRecord(b->ev[1], st);
+  trace(b, 1, st, capturing);
   if (b->precision == QTP_PREC_FP32) {
-    BP_CUDA(launch_gemm_simt_grouped(b->d_probs, b->n_probs, b->total_tiles, ws, st), "batched products (fp32)");
+    BP_CUDA(launch_gemm_simt_grouped(b->d_probs, b->d_prob_tile, b->total_tiles, ws, st), "batched products (fp32)");
   } else {
     BP_CUDA(launch_gemm_tc_grouped(b->d_probs, b->n_probs, b->total_tiles, b->fmt == FMT_BF16X3 ? 4 : 2, ws,
                                    b->d_err, b->num_sms, st),
             "batched products (tensor cores)");
   }
-  if (b->tracing) cudaEventRecord(b->ev[2], st);
-  BP_CUDA(launch_fft_inv_grouped(b->d_inv, b->n_inv, b->inv_blocks, b->d_ptrs, ws, b->d_tw, b->fft_smem, st),
+  trace(b, 2, st, capturing);
+  BP_CUDA(launch_fft_inv_grouped(b->d_inv, b->d_inv_job, b->inv_blocks, b->d_ptrs, ws, b->d_tw, b->fft_smem, st),
           "batched inverse FFT");
-  if (b->tracing) cudaEventRecord(b->ev[3], st);
+  trace(b, 3, st, capturing);
   return QTP_OK;
 }
 
@@ -289,6 +303,30 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
     e = launch_twiddles(b->d_tw + kv.second, kv.first, 0);
     if (e != cudaSuccess) break;
   }
+  // direct lookup tables: CTA -> job, tile -> product
+  std::vector<int> fwd_job((size_t)fb), inv_job((size_t)ib), prob_tile;
+  for (size_t j = 0; j < fwd.size(); ++j) {
+    const long long end = j + 1 < fwd.size() ? fwd[j + 1].block_begin : fb;
+    for (long long k = fwd[j].block_begin; k < end; ++k) fwd_job[(size_t)k] = (int)j;
+  }
+  for (size_t j = 0; j < inv.size(); ++j) {
+    const long long end = j + 1 < inv.size() ? inv[j + 1].block_begin : ib;
+    for (long long k = inv[j].block_begin; k < end; ++k) inv_job[(size_t)k] = (int)j;
+  }
+  if (!tc) {
+    prob_tile.resize((size_t)tiles);
+    for (int g = 0; g < b->n_probs; ++g) {
+      const long long end = g + 1 < b->n_probs ? b->h_probs[g + 1].tile_begin : tiles;
+      for (long long k = b->h_probs[g].tile_begin; k < end; ++k) prob_tile[(size_t)k] = g;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_fwd_job, sizeof(int) * fwd_job.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_inv_job, sizeof(int) * inv_job.size());
+  if (e == cudaSuccess && !tc) e = cudaMalloc(&b->d_prob_tile, sizeof(int) * prob_tile.size());
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_fwd_job, fwd_job.data(), sizeof(int) * fwd_job.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_inv_job, inv_job.data(), sizeof(int) * inv_job.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tc)
+    e = cudaMemcpy(b->d_prob_tile, prob_tile.data(), sizeof(int) * prob_tile.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_fwd, fwd.data(), sizeof(FftGroupJob) * fwd.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_inv, inv.data(), sizeof(FftGroupJob) * inv.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
@@ -357,7 +395,7 @@ qtp_status qtp_forward_batched(qtp_batch_plan* b, const float* const* A, const f
     BP_CUDA(cudaStreamSynchronize(b->cap), "tensor-map upload");
   }
   if (b->flags & QTP_BATCH_NO_GRAPH) {
-    qtp_status r = enqueue(b, ws, b->cap);
+    qtp_status r = enqueue(b, ws, b->cap, false);
     if (r != QTP_OK) return r;
   } else {
     if (!b->graph || b->graph_ws != ws || b->graph_tracing != b->tracing) {
@@ -367,7 +405,7 @@ qtp_status qtp_forward_batched(qtp_batch_plan* b, const float* const* A, const f
       }
       cudaGraph_t g = nullptr;
       BP_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-      qtp_status r = enqueue(b, ws, b->cap);
+      qtp_status r = enqueue(b, ws, b->cap, true);
       cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
       if (r != QTP_OK) {
         if (g) cudaGraphDestroy(g);

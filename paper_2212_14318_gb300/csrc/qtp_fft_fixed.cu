@@ -36,11 +36,15 @@ __host__ __device__ constexpr Radices radices_of(int p) {
   return rl;
 }
 
-// Tubes per CTA: about 4.5 K complex per buffer, a multiple of 32 tubes.
+// Tubes per CTA: about QTP_FFT_ELEMS complex per buffer (2304: ~34 KB per CTA,
+// six resident CTAs per SM; measured faster than 4608), a multiple of 32 tubes.
+#ifndef QTP_FFT_ELEMS
+#define QTP_FFT_ELEMS 2304
+#endif
 __host__ __device__ constexpr int tubes_for(int p) {
-  int t = 4608 / (p | 1);
+  int t = QTP_FFT_ELEMS / (p | 1);
   if (t > 512) t = 512;
-  if (t >= 32) t = t / 32 * 32;
+  t = t >= 32 ? t / 32 * 32 : t / 2 * 2;  // even: tube pairs never straddle a CTA
   return t < 2 ? 2 : t;
 }
 
@@ -50,7 +54,10 @@ constexpr size_t smem_for() {
 }
 
 // Radix-R Stockham butterfly j of one tube, Ns = length already transformed.
-template <int R, int NS, int P, bool INV>
+// Element k of the tube is read at in[k * IES] and written at out[k * OES]:
+// stride 1 in the tube-major layout (tube t at t * (P | 1)) and stride T in
+// the frequency-major layout (tube t at t, element k at k * T + t).
+template <int R, int NS, int P, bool INV, int IES, int OES>
 __device__ __forceinline__ void bfly(const float2* __restrict__ in, float2* __restrict__ out, int j,
                                      const float2* __restrict__ tw) {
   constexpr int stride = P / R;
@@ -61,12 +68,12 @@ __device__ __forceinline__ void bfly(const float2* __restrict__ in, float2* __re
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      v[r] = in[j + r * stride];
+      v[r] = in[(j + r * stride) * IES];
       if (NS > 1 && r > 0) v[r] = cmul(v[r], twid<INV>(tw, r * k * twstep));
     }
     Dft<R, INV>::run(v, tw, P);
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[base + r * NS] = v[r];
+    for (int r = 0; r < R; ++r) out[(base + r * NS) * OES] = v[r];
   } else {
     // prime radix > 8: direct DFT of length R from shared memory
 #pragma unroll 1
@@ -74,18 +81,20 @@ __device__ __forceinline__ void bfly(const float2* __restrict__ in, float2* __re
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 1
       for (int r = 0; r < R; ++r) {
-        float2 x = in[j + r * stride];
+        float2 x = in[(j + r * stride) * IES];
         if (NS > 1 && r > 0) x = cmul(x, twid<INV>(tw, r * k * twstep));
         const int e = ((r * u) % R) * stride;
         acc = cadd(acc, cmul(x, twid<INV>(tw, e)));
       }
-      out[base + u * NS] = acc;
+      out[(base + u * NS) * OES] = acc;
     }
   }
 }
 
-// Stages ST.. of the plan over the CTA's tubes; returns the buffer holding the result.
-template <int P, int ST, int NS, bool INV>
+// Stages ST.. of the plan over the CTA's tubes; returns the buffer holding the
+// result.  The first stage reads the frequency-major layout when IN_FM, the
+// last stage writes it when OUT_FM; all other accesses are tube-major.
+template <int P, int ST, int NS, bool INV, bool IN_FM, bool OUT_FM>
 __device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const float2* __restrict__ tw) {
   constexpr Radices RL = radices_of(P);
   if constexpr (ST == RL.n) {
@@ -95,14 +104,19 @@ __device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const
     constexpr int NB = P / R;
     constexpr int T = tubes_for(P);
     constexpr int PP = P | 1;
-    // tube-fastest: consecutive threads take consecutive tubes (odd stride PP: no bank conflicts)
+    constexpr bool FMI = IN_FM && ST == 0;
+    constexpr bool FMO = OUT_FM && ST == RL.n - 1;
+    // tube-fastest: consecutive threads take consecutive tubes, so both layouts
+    // are free of bank conflicts (odd stride PP, or unit stride)
     for (int idx = threadIdx.x; idx < T * NB; idx += kThreads) {
       const int j = idx / T;
       const int tube = idx - j * T;
-      if (tube < Tb) bfly<R, NS, P, INV>(in + tube * PP, out + tube * PP, j, tw);
+      if (tube < Tb)
+        bfly<R, NS, P, INV, FMI ? T : 1, FMO ? T : 1>(in + (FMI ? tube : tube * PP), out + (FMO ? tube : tube * PP), j,
+                                                       tw);
     }
     __syncthreads();
-    return stages<P, ST + 1, NS * R, INV>(out, in, Tb, tw);
+    return stages<P, ST + 1, NS * R, INV, IN_FM, OUT_FM>(out, in, Tb, tw);
   }
 }
 
@@ -150,7 +164,7 @@ __device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b
     tube_off[tube] = plane * NPARTS * P * slab + row * ld + (rem - row * job.cols);
   }
   __syncthreads();
-  const float2* X = stages<P, 0, 1, false>(buf0, buf1, Tb, tw);
+  const float2* X = stages<P, 0, 1, false, false, true>(buf0, buf1, Tb, tw);  // frequency-major result
 
   const long long part = (long long)P * slab;
   if ((job.cols & 1) == 0) {
@@ -160,8 +174,9 @@ __device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b
       const int f = i / TH;
       const int tube = 2 * (i - f * TH);
       if (tube >= Tb) continue;
-      const float2 v0 = X[tube * PP + f];
-      const float2 v1 = X[(tube + 1) * PP + f];
+      const float4 v01 = *reinterpret_cast<const float4*>(X + f * T + tube);
+      const float2 v0 = make_float2(v01.x, v01.y);
+      const float2 v1 = make_float2(v01.z, v01.w);
       const long long o = tube_off[tube] + (long long)f * slab;
       if constexpr (FMT == FMT_C32) {
         *reinterpret_cast<float4*>(reinterpret_cast<float2*>(job.out) + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
@@ -189,7 +204,7 @@ __device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b
       const int f = i / T;
       const int tube = i - f * T;
       if (tube >= Tb) continue;
-      const float2 v = X[tube * PP + f];
+      const float2 v = X[f * T + tube];
       const long long o = tube_off[tube] + (long long)f * slab;
       if constexpr (FMT == FMT_C32) {
         reinterpret_cast<float2*>(job.out)[o] = v;
@@ -240,20 +255,19 @@ __device__ __forceinline__ void fixed_inv_body(const FftInvJob& job, long long b
       const int f = i / TH;
       const int tube = 2 * (i - f * TH);
       if (tube >= Tb) continue;
-      const float4 v = __ldg(reinterpret_cast<const float4*>(job.in + tube_off[tube] + (long long)f * per_plane));
-      buf0[tube * PP + f] = make_float2(v.x, v.y);
-      buf0[(tube + 1) * PP + f] = make_float2(v.z, v.w);
+      *reinterpret_cast<float4*>(buf0 + f * T + tube) =
+          __ldg(reinterpret_cast<const float4*>(job.in + tube_off[tube] + (long long)f * per_plane));
     }
   } else {
     for (int i = threadIdx.x; i < T * P; i += kThreads) {
       const int f = i / T;
       const int tube = i - f * T;
       if (tube >= Tb) continue;
-      buf0[tube * PP + f] = __ldg(job.in + tube_off[tube] + (long long)f * per_plane);
+      buf0[f * T + tube] = __ldg(job.in + tube_off[tube] + (long long)f * per_plane);
     }
   }
   __syncthreads();
-  const float2* X = stages<P, 0, 1, true>(buf0, buf1, Tb, tw);
+  const float2* X = stages<P, 0, 1, true, true, false>(buf0, buf1, Tb, tw);  // frequency-major input
 
   const float scale = 1.0f / (float)P;
   float2* dst = job.out + t0 * P;
@@ -298,27 +312,20 @@ __global__ void __launch_bounds__(kThreads) fft_inv_fixed(FftInvJob job0, FftInv
 // ---------------------------------------------------------------------------
 // Grouped transforms for batches of products with mixed (rows, cols, p): one
 // launch covers every tensor of the batch; each CTA finds its job by binary
-// search over the jobs' first block and runs the body specialised for that
-// job's p (or the runtime-radix body).  Tensor pointers come from a per-call
+// (one table load: job_of_block) and runs the body specialised for that job's
+// p (or the runtime-radix body).  Tensor pointers come from a per-call
 // device table ptrs[3 * product + {0: A, 1: B, 2: C}].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_job(const FftGroupJob* __restrict__ jobs, int njobs, long long b) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].block_begin <= b) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 template <int FMT>
-__global__ void __launch_bounds__(kThreads) fft_fwd_grouped(const FftGroupJob* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(kThreads) fft_fwd_grouped(const FftGroupJob* __restrict__ jobs,
+                                                            const int* __restrict__ job_of_block,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
   extern __shared__ float4 smem_f4[];
   float2* smem = reinterpret_cast<float2*>(smem_f4);
   const long long b = blockIdx.x;
-  const FftGroupJob& J = jobs[find_job(jobs, njobs, b)];
+  const FftGroupJob& J = jobs[__ldg(job_of_block + b)];
   FftFwdJob job;
   job.in = ptrs[3 * J.prod + J.which];
   job.out = ws + J.spec_off;
@@ -341,13 +348,14 @@ __global__ void __launch_bounds__(kThreads) fft_fwd_grouped(const FftGroupJob* _
   }
 }
 
-__global__ void __launch_bounds__(kThreads) fft_inv_grouped(const FftGroupJob* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(kThreads) fft_inv_grouped(const FftGroupJob* __restrict__ jobs,
+                                                            const int* __restrict__ job_of_block,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
   extern __shared__ float4 smem_f4[];
   float2* smem = reinterpret_cast<float2*>(smem_f4);
   const long long b = blockIdx.x;
-  const FftGroupJob& J = jobs[find_job(jobs, njobs, b)];
+  const FftGroupJob& J = jobs[__ldg(job_of_block + b)];
   FftInvJob job;
   job.in = reinterpret_cast<const float2*>(ws + J.spec_off);
   job.out = const_cast<float2*>(ptrs[3 * J.prod + J.which]);
@@ -419,7 +427,7 @@ size_t fft_fixed_smem(int p) {
   }
 }
 
-cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, int njobs, long long nblocks, int fmt,
+cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks, int fmt,
                                    const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
                                    cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
@@ -428,15 +436,15 @@ cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, int njobs, long lo
   switch (fmt) {
     case FMT_C32:
       e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_C32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) fft_fwd_grouped<FMT_C32><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, njobs, d_ptrs, ws, d_tw);
+      if (e == cudaSuccess) fft_fwd_grouped<FMT_C32><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, d_ptrs, ws, d_tw);
       break;
     case FMT_BF16X3:
       e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) fft_fwd_grouped<FMT_BF16X3><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, njobs, d_ptrs, ws, d_tw);
+      if (e == cudaSuccess) fft_fwd_grouped<FMT_BF16X3><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, d_ptrs, ws, d_tw);
       break;
     case FMT_BF16:
       e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) fft_fwd_grouped<FMT_BF16><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, njobs, d_ptrs, ws, d_tw);
+      if (e == cudaSuccess) fft_fwd_grouped<FMT_BF16><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, d_ptrs, ws, d_tw);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -444,14 +452,14 @@ cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, int njobs, long lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, int njobs, long long nblocks,
+cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks,
                                    const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
                                    cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
   if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fft_inv_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fft_inv_grouped<<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, njobs, d_ptrs, ws, d_tw);
+  fft_inv_grouped<<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, d_ptrs, ws, d_tw);
   return cudaGetLastError();
 }
 

@@ -48,16 +48,14 @@ struct GTile {
   int g, f, h, mt, nt;
 };
 
-__device__ __forceinline__ GTile decode_tile(const GroupProblem* __restrict__ probs, int nprobs, long long t) {
-  int lo = 0, hi = nprobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
-  }
-  const GroupProblem& P = probs[lo];
+// Tile t of the global index space.  A CTA visits increasing t, so its
+// product cursor g only moves forward (a step or two per tile at most).
+__device__ __forceinline__ GTile decode_tile(const GroupProblem* __restrict__ probs, int nprobs, long long t, int& g) {
+  while (g + 1 < nprobs && probs[g + 1].tile_begin <= t) ++g;
+  const GroupProblem& P = probs[g];
   long long local = t - P.tile_begin;
   GTile r;
-  r.g = lo;
+  r.g = g;
   r.nt = (int)(local % P.tiles_n);
   local /= P.tiles_n;
   r.mt = (int)(local % P.tiles_m);
@@ -115,9 +113,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       long long it = 0;
+      int cur = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const GTile T = decode_tile(probs, nprobs, t);
+        const GTile T = decode_tile(probs, nprobs, t, cur);
         const GroupProblem& P = probs[T.g];
         const CUtensorMap* tmA = reinterpret_cast<const CUtensorMap*>(P.tmA);
         const CUtensorMap* tmB = reinterpret_cast<const CUtensorMap*>(P.tmB);
@@ -162,10 +161,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = make_idesc(false, true, GBN);
       long long it = 0;
-      int lt = 0;
+      int lt = 0, cur = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++lt) {
-        const GTile T = decode_tile(probs, nprobs, t);
+        const GTile T = decode_tile(probs, nprobs, t, cur);
         const int K = probs[T.g].K;
         const int nkb = (K + GBK - 1) / GBK;
         const int buf = lt & 1;
@@ -228,9 +227,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    int lt = 0;
+    int lt = 0, cur = 0;
     for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
-      const GTile T = decode_tile(probs, nprobs, t);
+      const GTile T = decode_tile(probs, nprobs, t, cur);
       const GroupProblem& P = probs[T.g];
       const int buf = lt & 1;
       const uint32_t uph = (uint32_t)(lt >> 1) & 1u;

@@ -124,14 +124,9 @@ __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmProblem pr) {
 // GroupProblem); the CTA rebuilds its product's operand views from the
 // workspace offsets: C1 = A1 B1 - A2 conj(B2(-f)), C2 = A1 B2 + A2 conj(B1(-f)).
 __global__ void __launch_bounds__(kThreads) gemm_simt_grouped_kernel(const GroupProblem* __restrict__ probs,
-                                                                     int nprobs, char* ws) {
+                                                                     const int* __restrict__ prob_of_tile, char* ws) {
   const long long t = blockIdx.x;
-  int lo = 0, hi = nprobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
-  }
-  const GroupProblem& P = probs[lo];
+  const GroupProblem& P = probs[__ldg(prob_of_tile + t)];
   long long local = t - P.tile_begin;
   const int nt = (int)(local % P.tiles_n);
   local /= P.tiles_n;
@@ -166,11 +161,11 @@ __global__ void __launch_bounds__(kThreads) gemm_simt_grouped_kernel(const Group
 
 }  // namespace
 
-cudaError_t launch_gemm_simt_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, char* ws,
-                                     cudaStream_t st) {
+cudaError_t launch_gemm_simt_grouped(const GroupProblem* d_probs, const int* d_prob_of_tile, long long total_tiles,
+                                     char* ws, cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;
   if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  gemm_simt_grouped_kernel<<<(unsigned)total_tiles, kThreads, 0, st>>>(d_probs, nprobs, ws);
+  gemm_simt_grouped_kernel<<<(unsigned)total_tiles, kThreads, 0, st>>>(d_probs, d_prob_of_tile, ws);
   return cudaGetLastError();
 }
 

@@ -68,10 +68,10 @@ struct FftGroupJob {
   RadixPlan rp;           // for tube lengths without a compile-time kernel
 };
 
-cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, int njobs, long long nblocks, int fmt,
+cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks, int fmt,
                                    const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
                                    cudaStream_t st);
-cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, int njobs, long long nblocks,
+cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks,
                                    const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
                                    cudaStream_t st);
 size_t fft_fixed_smem(int p);
@@ -163,8 +163,8 @@ struct GroupProblem {
 
 cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, int nparts,
                                    char* ws, int* d_err, int num_ctas, cudaStream_t st);
-cudaError_t launch_gemm_simt_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, char* ws,
-                                     cudaStream_t st);
+cudaError_t launch_gemm_simt_grouped(const GroupProblem* d_probs, const int* d_prob_of_tile, long long total_tiles,
+                                     char* ws, cudaStream_t st);
 // Tile shapes of the grouped kernels (rows x complex columns).
 constexpr int kGroupTcBM = 128, kGroupTcBN = 128;
 constexpr int kGroupSimtBM = 64, kGroupSimtBN = 128;

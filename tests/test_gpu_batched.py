@@ -98,3 +98,19 @@ def test_batch_workload_4096_products_each_checked():
     assert worst <= 1e-4, worst
     del As, Bs, Cs
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_stage_tracing(graph):
+    from paper_2212_14318_gb300 import qtp
+    shapes = MIXED[:4]
+    As = [to_dev(synth.quat_normal(m, n, p, 70 + i)) for i, (m, n, s, p) in enumerate(shapes)]
+    Bs = [to_dev(synth.quat_normal(n, s, p, 80 + i)) for i, (m, n, s, p) in enumerate(shapes)]
+    plan = qtp.BatchPlan(shapes, "bf16x3", graph=graph)
+    plan.set_tracing(True)
+    plan.forward(As, Bs)
+    t = plan.stage_times()
+    assert len(t) == 3 and all(x > 0 for x in t)
+    plan.set_tracing(False)
+    plan.forward(As, Bs)
+    plan.sync()
