@@ -76,14 +76,28 @@ typedef enum { QTP_PREC_FP32 = 0, QTP_PREC_BF16X3 = 1, QTP_PREC_BF16 = 2 } qtp_p
 
 typedef struct qtp_plan qtp_plan;
 
+/* Plan flags. */
+#define QTP_PLAN_AUTOTUNE 1u  /* time the tensor-core tile shapes for this shape at plan creation */
+
 /* Create a plan for C = A * B with A in Q^{m x n x p}, B in Q^{n x s x p}.
  * Requires 1 <= m, n, s <= 2^20, 1 <= p <= 4096 and m*n*p, n*s*p, m*s*p
  * each below 2^31 complex entries per plane.  Allocates the twiddle table
  * w^e = exp(-2 pi i e / p), e in [0, p) (eq. DFT, generated in FP64 and
- * rounded to FP32) and synchronises the current device.  flags must be 0. */
+ * rounded to FP32) and synchronises the current device.  flags: 0 or
+ * QTP_PLAN_AUTOTUNE.  With QTP_PLAN_AUTOTUNE (BF16 precisions) the plan
+ * times, for the forward and both backward product kinds, every tensor-core
+ * tile shape that keeps the split-BF16 accuracy bound for that kind's
+ * reduction length on scratch spectra it allocates and frees, and keeps the
+ * fastest; choices are cached per (device, shape, precision) in the process
+ * and appended to the file named by the environment variable
+ * QTP_AUTOTUNE_CACHE, if set, which later processes read. */
 QTP_API qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p,
                            int precision, unsigned flags);
 QTP_API qtp_status qtp_plan_destroy(qtp_plan* plan);
+
+/* Tile shapes the plan uses for its (forward, dA, dB) products: 0 = built-in
+ * rule, 1 = 256 wide, 2 = 128 wide, 3 = 128 wide with split accumulators. */
+QTP_API qtp_status qtp_plan_get_tiles(const qtp_plan* plan, int* tiles3);
 
 /* Bytes of device workspace qtp_forward needs: the spectra of A and B in the
  * GEMM operand format of the plan's precision plus the FP32 spectrum of C. */

@@ -4,7 +4,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "qtp_internal.h"
 
@@ -138,6 +143,84 @@ TcView tcv(int tensor, int plane, int fneg, int conj) {
   return v;
 }
 
+// Tensor-core problems of the three product kinds (forward, dA, dB) over
+// bf16 spectra: which planes, frequencies, conjugations and signs feed each
+// (output half, K half).  See run_products_fwd / run_products_bwd.
+TcProblem tc_fwd(const qtp_plan* pl, const void* sa, const void* sb, float2* sc) {
+  const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
+  TcProblem pr;
+  memset(&pr, 0, sizeof(pr));
+  pr.kind = TC_FWD;
+  pr.tile = pl->tile[0];
+  pr.M = m; pr.N = s; pr.K = n; pr.p = p;
+  pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
+  pr.a_base[0] = sa; pr.a_rows[0] = m; pr.a_cols[0] = n; pr.a_ld[0] = (int)spec_ld(FMT_BF16, n);
+  pr.b_base[0] = sb; pr.b_rows[0] = n; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
+  for (int h = 0; h < 2; ++h) {
+    pr.a[h][0] = tcv(0, 0, 0, 0);
+    pr.a[h][1] = tcv(0, 1, 0, 0);
+  }
+  pr.b[0][0] = tcv(0, 0, 0, 0); pr.sign[0][0] = 1.f;
+  pr.b[0][1] = tcv(0, 1, 1, 1); pr.sign[0][1] = -1.f;
+  pr.b[1][0] = tcv(0, 1, 0, 0); pr.sign[1][0] = 1.f;
+  pr.b[1][1] = tcv(0, 0, 1, 1); pr.sign[1][1] = 1.f;
+  pr.out = sc;
+  pr.out_hstride = (long long)p * m * s;
+  pr.out_fstride = (long long)m * s;
+  pr.out_rstride = s;
+  return pr;
+}
+
+TcProblem tc_bwd_a(const qtp_plan* pl, const void* sb, const void* sg, float2* sda) {
+  const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
+  TcProblem pr;
+  memset(&pr, 0, sizeof(pr));
+  pr.kind = TC_BWD_A;
+  pr.tile = pl->tile[1];
+  pr.M = m; pr.N = n; pr.K = s; pr.p = p;
+  pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
+  pr.a_base[0] = sg; pr.a_rows[0] = m; pr.a_cols[0] = s; pr.a_ld[0] = (int)spec_ld(FMT_BF16, s);
+  pr.b_base[0] = sb; pr.b_rows[0] = n; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
+  for (int h = 0; h < 2; ++h) {
+    pr.a[h][0] = tcv(0, 0, 0, 0);
+    pr.a[h][1] = tcv(0, 1, 0, 0);
+  }
+  pr.b[0][0] = tcv(0, 0, 0, 1); pr.sign[0][0] = 1.f;
+  pr.b[0][1] = tcv(0, 1, 0, 1); pr.sign[0][1] = 1.f;
+  pr.b[1][0] = tcv(0, 1, 1, 0); pr.sign[1][0] = -1.f;
+  pr.b[1][1] = tcv(0, 0, 1, 0); pr.sign[1][1] = 1.f;
+  pr.out = sda;
+  pr.out_hstride = (long long)p * m * n;
+  pr.out_fstride = (long long)m * n;
+  pr.out_rstride = n;
+  return pr;
+}
+
+TcProblem tc_bwd_b(const qtp_plan* pl, const void* sa, const void* sg, float2* sdb) {
+  const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
+  TcProblem pr;
+  memset(&pr, 0, sizeof(pr));
+  pr.kind = TC_BWD_B;
+  pr.tile = pl->tile[2];
+  pr.M = n; pr.N = s; pr.K = m; pr.p = p;
+  pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
+  pr.a_base[0] = sa; pr.a_rows[0] = m; pr.a_cols[0] = n; pr.a_ld[0] = (int)spec_ld(FMT_BF16, n);
+  pr.b_base[0] = sg; pr.b_rows[0] = m; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
+  for (int h = 0; h < 2; ++h) {
+    pr.a[h][0] = tcv(0, 0, 0, 1);
+    pr.a[h][1] = tcv(0, 1, 1, 0);
+  }
+  pr.b[0][0] = tcv(0, 0, 0, 0); pr.sign[0][0] = 1.f;
+  pr.b[0][1] = tcv(0, 1, 1, 1); pr.sign[0][1] = 1.f;
+  pr.b[1][0] = tcv(0, 1, 0, 0); pr.sign[1][0] = 1.f;
+  pr.b[1][1] = tcv(0, 0, 1, 1); pr.sign[1][1] = -1.f;
+  pr.out = sdb;
+  pr.out_hstride = (long long)p * n * s;
+  pr.out_fstride = (long long)n * s;
+  pr.out_rstride = s;
+  return pr;
+}
+
 // Step 2 of Alg. 5.1 for the forward product: out half 0 = C1, half 1 = C2.
 //   C1_f = A1_f B1_f - A2_f conj(B2_{-f}),   C2_f = A1_f B2_f + A2_f conj(B1_{-f})
 qtp_status run_products_fwd(const qtp_plan* pl, const void* sa, const void* sb, float2* sc, cudaStream_t st) {
@@ -164,25 +247,7 @@ qtp_status run_products_fwd(const qtp_plan* pl, const void* sa, const void* sb, 
     QTP_CUDA(launch_gemm_simt(pr, st), "products (fp32)");
     return QTP_OK;
   }
-  TcProblem pr;
-  memset(&pr, 0, sizeof(pr));
-  pr.kind = TC_FWD;
-  pr.M = m; pr.N = s; pr.K = n; pr.p = p;
-  pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
-  pr.a_base[0] = sa; pr.a_rows[0] = m; pr.a_cols[0] = n; pr.a_ld[0] = (int)spec_ld(FMT_BF16, n);
-  pr.b_base[0] = sb; pr.b_rows[0] = n; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
-  for (int h = 0; h < 2; ++h) {
-    pr.a[h][0] = tcv(0, 0, 0, 0);
-    pr.a[h][1] = tcv(0, 1, 0, 0);
-  }
-  pr.b[0][0] = tcv(0, 0, 0, 0); pr.sign[0][0] = 1.f;
-  pr.b[0][1] = tcv(0, 1, 1, 1); pr.sign[0][1] = -1.f;
-  pr.b[1][0] = tcv(0, 1, 0, 0); pr.sign[1][0] = 1.f;
-  pr.b[1][1] = tcv(0, 0, 1, 1); pr.sign[1][1] = 1.f;
-  pr.out = sc;
-  pr.out_hstride = (long long)p * m * s;
-  pr.out_fstride = (long long)m * s;
-  pr.out_rstride = s;
+  const TcProblem pr = tc_fwd(pl, sa, sb, sc);
   char msg[256] = "";
   cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg));
   if (e != cudaSuccess) return fail(QTP_ERR_CUDA, "products (tensor cores): %s %s", cudaGetErrorString(e), msg);
@@ -244,51 +309,138 @@ qtp_status run_products_bwd(const qtp_plan* pl, const void* sa, const void* sb, 
   }
   char msg[256] = "";
   if (sda) {
-    TcProblem pr;
-    memset(&pr, 0, sizeof(pr));
-    pr.kind = TC_BWD_A;
-    pr.M = m; pr.N = n; pr.K = s; pr.p = p;
-    pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
-    pr.a_base[0] = sg; pr.a_rows[0] = m; pr.a_cols[0] = s; pr.a_ld[0] = (int)spec_ld(FMT_BF16, s);
-    pr.b_base[0] = sb; pr.b_rows[0] = n; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
-    for (int h = 0; h < 2; ++h) {
-      pr.a[h][0] = tcv(0, 0, 0, 0);
-      pr.a[h][1] = tcv(0, 1, 0, 0);
-    }
-    pr.b[0][0] = tcv(0, 0, 0, 1); pr.sign[0][0] = 1.f;
-    pr.b[0][1] = tcv(0, 1, 0, 1); pr.sign[0][1] = 1.f;
-    pr.b[1][0] = tcv(0, 1, 1, 0); pr.sign[1][0] = -1.f;
-    pr.b[1][1] = tcv(0, 0, 1, 0); pr.sign[1][1] = 1.f;
-    pr.out = sda;
-    pr.out_hstride = (long long)p * m * n;
-    pr.out_fstride = (long long)m * n;
-    pr.out_rstride = n;
+    const TcProblem pr = tc_bwd_a(pl, sb, sg, sda);
     cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg));
     if (e != cudaSuccess) return fail(QTP_ERR_CUDA, "backward products dA: %s %s", cudaGetErrorString(e), msg);
   }
   if (sdb) {
-    TcProblem pr;
-    memset(&pr, 0, sizeof(pr));
-    pr.kind = TC_BWD_B;
-    pr.M = n; pr.N = s; pr.K = m; pr.p = p;
-    pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
-    pr.a_base[0] = sa; pr.a_rows[0] = m; pr.a_cols[0] = n; pr.a_ld[0] = (int)spec_ld(FMT_BF16, n);
-    pr.b_base[0] = sg; pr.b_rows[0] = m; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
-    for (int h = 0; h < 2; ++h) {
-      pr.a[h][0] = tcv(0, 0, 0, 1);
-      pr.a[h][1] = tcv(0, 1, 1, 0);
-    }
-    pr.b[0][0] = tcv(0, 0, 0, 0); pr.sign[0][0] = 1.f;
-    pr.b[0][1] = tcv(0, 1, 1, 1); pr.sign[0][1] = 1.f;
-    pr.b[1][0] = tcv(0, 1, 0, 0); pr.sign[1][0] = 1.f;
-    pr.b[1][1] = tcv(0, 0, 1, 1); pr.sign[1][1] = -1.f;
-    pr.out = sdb;
-    pr.out_hstride = (long long)p * n * s;
-    pr.out_fstride = (long long)n * s;
-    pr.out_rstride = s;
+    const TcProblem pr = tc_bwd_b(pl, sa, sg, sdb);
     cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg));
     if (e != cudaSuccess) return fail(QTP_ERR_CUDA, "backward products dB: %s %s", cudaGetErrorString(e), msg);
   }
+  return QTP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Autotuner (QTP_PLAN_AUTOTUNE): for each product kind, time the tensor-core
+// tile candidates that keep the split-BF16 accuracy bound for that kind's
+// reduction length K (128-wide with split accumulators always; 256- and
+// 128-wide single accumulators only for K <= 384) on scratch spectra and keep
+// the fastest.  Results are cached per (device, shape, precision) for the
+// process and, when QTP_AUTOTUNE_CACHE names a file, across processes.
+// ----------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::string, std::array<int, 3>> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+std::string tune_key(const qtp_plan* pl) {
+  cudaDeviceProp prop;
+  std::string dev = "dev";
+  if (cudaGetDeviceProperties(&prop, pl->device) == cudaSuccess) dev = prop.name;
+  for (char& c : dev)
+    if (c == ' ') c = '_';
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d", dev.c_str(), pl->m, pl->n, pl->s, pl->p, pl->precision);
+  return buf;
+}
+
+void tune_cache_load() {
+  if (g_tune_file_loaded) return;
+  g_tune_file_loaded = true;
+  const char* path = getenv("QTP_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[256];
+  int a, b, c;
+  while (fscanf(f, "%255s %d %d %d", key, &a, &b, &c) == 4) g_tune_cache[key] = {a, b, c};
+  fclose(f);
+}
+
+void tune_cache_store(const std::string& key, const std::array<int, 3>& t) {
+  g_tune_cache[key] = t;
+  const char* path = getenv("QTP_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d\n", key.c_str(), t[0], t[1], t[2]);
+  fclose(f);
+}
+
+// Mean time (ms) of `reps` launches of one tensor-core problem, after a warm-up.
+float time_tc(const TcProblem& pr, int* d_err, cudaEvent_t e0, cudaEvent_t e1, int reps) {
+  char msg[256];
+  if (launch_gemm_tc(pr, d_err, 0, msg, sizeof(msg)) != cudaSuccess) return 1e30f;
+  cudaEventRecord(e0, 0);
+  for (int i = 0; i < reps; ++i) launch_gemm_tc(pr, d_err, 0, msg, sizeof(msg));
+  cudaEventRecord(e1, 0);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms / reps;
+}
+
+qtp_status autotune(qtp_plan* pl) {
+  if (pl->precision == QTP_PREC_FP32) return QTP_OK;  // one FP32 kernel: nothing to choose
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_cache_load();
+  const std::string key = tune_key(pl);
+  auto hit = g_tune_cache.find(key);
+  if (hit != g_tune_cache.end()) {
+    for (int k = 0; k < 3; ++k) pl->tile[k] = hit->second[k];
+    return QTP_OK;
+  }
+  const int fmt = spec_format(pl->precision);
+  const size_t bA = spec_bytes(fmt, pl->p, pl->m, pl->n), bB = spec_bytes(fmt, pl->p, pl->n, pl->s),
+               bG = spec_bytes(fmt, pl->p, pl->m, pl->s);
+  const size_t bOut = c32_bytes(pl->p, std::max(pl->m, pl->n), std::max(pl->s, pl->n));
+  char* scratch = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&scratch, bA + bB + bG + bOut);
+  if (e == cudaSuccess) e = cudaMemset(scratch, 0, bA + bB + bG);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaFree(scratch);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return cuda_fail(e, "autotune scratch");
+  }
+  char* sa = scratch;
+  char* sb = sa + bA;
+  char* sg = sb + bB;
+  float2* out = (float2*)(sg + bG);
+  std::array<int, 3> best = {TILE_AUTO, TILE_AUTO, TILE_AUTO};
+  for (int kind = 0; kind < 3; ++kind) {
+    TcProblem pr = kind == 0 ? tc_fwd(pl, sa, sb, out) : kind == 1 ? tc_bwd_a(pl, sb, sg, out) : tc_bwd_b(pl, sa, sg, out);
+    std::vector<int> cands = {TILE_128_SPLIT};
+    if (pr.nparts == 2 || pr.K <= 384) {
+      cands.push_back(TILE_128);
+      if (pr.N > 128) cands.push_back(TILE_256);
+    }
+    float best_ms = 1e30f;
+    for (int c : cands) {
+      pr.tile = c;
+      const float ms = time_tc(pr, pl->d_err, e0, e1, 3);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best[kind] = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  int v = 0;
+  cudaMemcpy(&v, pl->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (v != 0) {
+    cudaMemset(pl->d_err, 0, sizeof(int));
+    return fail(QTP_ERR_TIMEOUT, "autotune: a device-side wait gave up (code %d)", v);
+  }
+  for (int k = 0; k < 3; ++k) pl->tile[k] = best[k];
+  tune_cache_store(key, best);
   return QTP_OK;
 }
 
@@ -359,7 +511,7 @@ qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int preci
   const long long lim = 1LL << 31;
   if ((long long)m * n * p >= lim || (long long)n * s * p >= lim || (long long)m * s * p >= lim)
     return fail(QTP_ERR_INVALID_ARG, "a tensor plane exceeds 2^31 complex entries");
-  if (flags != 0) return fail(QTP_ERR_INVALID_ARG, "flags must be 0");
+  if (flags & ~QTP_PLAN_AUTOTUNE) return fail(QTP_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
   if (precision != QTP_PREC_FP32 && precision != QTP_PREC_BF16X3 && precision != QTP_PREC_BF16)
     return fail(QTP_ERR_INVALID_ARG, "unknown precision %d", precision);
   if (precision != QTP_PREC_FP32 && !tc_supported())
@@ -383,7 +535,25 @@ qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int preci
     delete pl;
     return cuda_fail(e, "plan creation");
   }
+  pl->flags = flags;
+  if (flags & QTP_PLAN_AUTOTUNE) {
+    qtp_status r = autotune(pl);
+    if (r != QTP_OK) {
+      cudaFree(pl->d_tw);
+      cudaFree(pl->d_err);
+      delete pl;
+      return r;
+    }
+  }
   *out = pl;
+  return QTP_OK;
+}
+
+qtp_status qtp_plan_get_tiles(const qtp_plan* pl, int* tiles3) {
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if (!tiles3) return fail(QTP_ERR_INVALID_ARG, "tiles3 is NULL");
+  for (int k = 0; k < 3; ++k) tiles3[k] = pl->tile[k];
   return QTP_OK;
 }
 

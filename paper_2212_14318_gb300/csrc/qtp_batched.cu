@@ -251,8 +251,13 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
     P.N = q.s;
     P.K = q.n;
     P.p = q.p;
+    // tile width: 64 columns when that covers s in one tile (half the MMA work
+    // over padding at the same tile count), else 128 (more, narrower tiles
+    // measured slower: per-tile cost dominates)
+    const int bn = tc && q.s <= 64 ? 64 : BNt;
+    P.bn = bn;
     P.tiles_m = (q.m + BMt - 1) / BMt;
-    P.tiles_n = (q.s + BNt - 1) / BNt;
+    P.tiles_n = (q.s + bn - 1) / bn;
     P.lda = (int)spec_ld_of(fmt, q.n);
     P.ldb = (int)spec_ld_of(fmt, q.s);
     tiles += (long long)P.tiles_m * P.tiles_n * 2 * q.p;

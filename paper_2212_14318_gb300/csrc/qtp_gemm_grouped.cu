@@ -3,7 +3,9 @@
 //
 // All tiles of all products form one index space; product g owns
 // [tile_begin_g, tile_begin_g + tiles_m * tiles_n * 2 * p_g), ordered
-// (frequency, output half, row tile, column tile).  CTA i (one per SM) takes
+// (frequency, output half, row tile, column tile).  Each product has its own
+// tile width (64 or 128 complex columns, the MMA's N): narrow products do not
+// pay for 128-wide MMAs over padding.  CTA i (one per SM) takes
 // tiles i, i + grid, i + 2 grid, ...  Roles as in the single-product kernel:
 // warp 0 issues TMA, warp 1 issues tcgen05.mma, warps 2-5 drain TMEM.  Here
 // the TMA producer runs straight on from one tile's K loop into the next
@@ -138,7 +140,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
             ok = false;
             break;
           }
-          mbar_expect_tx(full + 8 * s, (uint32_t)(NP * (G_A_TILE + G_B_TILE)));
+          const int nb64 = P.bn / 64;  // 64-column boxes of B in this product's tiles
+          mbar_expect_tx(full + 8 * s, (uint32_t)(NP * (G_A_TILE + nb64 * (G_B_TILE / 2))));
           const int ga = T.f;
           const int gb = V.b_fneg[T.h][kh] ? (P.p - T.f) % P.p : T.f;
 #pragma unroll
@@ -146,8 +149,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
             const uint32_t ta = sA + (uint32_t)(s * NP + q) * G_A_TILE;
             const uint32_t tb = sB + (uint32_t)(s * NP + q) * G_B_TILE;
             tma_load_4d(ta, tmA, full + 8 * s, k0, T.mt * GBM, ga, V.a_plane[T.h][kh] * NP + q);
-            tma_load_4d(tb, tmB, full + 8 * s, T.nt * GBN, k0, gb, V.b_plane[T.h][kh] * NP + q);
-            tma_load_4d(tb + 128u * GBK, tmB, full + 8 * s, T.nt * GBN + 64, k0, gb, V.b_plane[T.h][kh] * NP + q);
+            tma_load_4d(tb, tmB, full + 8 * s, T.nt * P.bn, k0, gb, V.b_plane[T.h][kh] * NP + q);
+            if (nb64 == 2)
+              tma_load_4d(tb + 128u * GBK, tmB, full + 8 * s, T.nt * P.bn + 64, k0, gb, V.b_plane[T.h][kh] * NP + q);
           }
         }
       }
@@ -159,13 +163,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(false, true, GBN);
+      const uint32_t idesc128 = make_idesc(false, true, 128);
+      const uint32_t idesc64 = make_idesc(false, true, 64);
       long long it = 0;
       int lt = 0, cur = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++lt) {
         const GTile T = decode_tile(probs, nprobs, t, cur);
         const int K = probs[T.g].K;
+        const uint32_t idesc = probs[T.g].bn == 64 ? idesc64 : idesc128;
         const int nkb = (K + GBK - 1) / GBK;
         const int buf = lt & 1;
         const uint32_t uph = (uint32_t)(lt >> 1) & 1u;
@@ -242,17 +248,18 @@ __global__ void __launch_bounds__(kGThreads, 1)
       }
       fence_after();
       const int row = T.mt * GBM + q * 32 + lane;
+      const int bn = P.bn;
       float2* out = reinterpret_cast<float2*>(ws + P.out_off) + (long long)T.h * P.p * P.M * P.N +
                     (long long)T.f * P.M * P.N;
       const uint32_t tb = tmem + (uint32_t)(buf * 2 * GBN) + lane_off;
 #pragma unroll 1
-      for (int c0 = 0; c0 < GBN; c0 += 32) {
+      for (int c0 = 0; c0 < bn; c0 += 32) {
         uint32_t re[32], im[32];
         tmem_ld32(tb + (uint32_t)c0, re);
         tmem_ld32(tb + (uint32_t)(GBN + c0), im);
         if (row < P.M) {
           float2* o = out + (long long)row * P.N;
-          const int col0 = T.nt * GBN + c0;
+          const int col0 = T.nt * bn + c0;
 #pragma unroll
           for (int j = 0; j < 32; ++j)
             if (col0 + j < P.N) o[col0 + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));

@@ -378,6 +378,12 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
   int bn = pr.N > 160 ? 256 : 128;
   bool split = pr.nparts == 4 && pr.K > 384;
   if (split) bn = 128;
+  switch (pr.tile) {  // a tuned choice (autotuner) replaces the heuristic
+    case TILE_256: bn = 256; split = false; break;
+    case TILE_128: bn = 128; split = false; break;
+    case TILE_128_SPLIT: bn = 128; split = pr.nparts == 4; break;
+    default: break;
+  }
   if (const char* env = getenv("QTP_TC_TILE")) {
     if (!strcmp(env, "256")) { bn = 256; split = false; }
     else if (!strcmp(env, "128")) { bn = 128; split = false; }

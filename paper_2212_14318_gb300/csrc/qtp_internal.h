@@ -132,8 +132,13 @@ enum TcKind : int {
   TC_BWD_B = 2,   // A MN-major (A[f][i][j], m = j, k = i), B MN-major (G[f][i][c])
 };
 
+// Tensor-core tile choice: 0 = heuristic (256 wide for N > 160; split
+// accumulators for K > 384), else one of these.
+enum TcTile : int { TILE_AUTO = 0, TILE_256 = 1, TILE_128 = 2, TILE_128_SPLIT = 3 };
+
 struct TcProblem {
   int kind;
+  int tile;            // TcTile
   int M, N, K, p;
   int nparts;          // 4 (bf16x3) or 2 (bf16)
   TcView a[2][2];
@@ -159,6 +164,7 @@ struct GroupProblem {
   int M, N, K, p;
   int tiles_m, tiles_n;
   int lda, ldb;                       // spectra row strides (elements)
+  int bn;                             // tile width (complex columns): 64 or 128 (tensor-core path)
 };
 
 cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, int nparts,
@@ -190,6 +196,8 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
 struct qtp_plan {
   int m, n, s, p;
   int precision;
+  unsigned flags;
+  int tile[3];       // TcTile per product kind (forward, dA, dB); TILE_AUTO unless tuned
   int device;
   float2* d_tw;      // w^e = exp(-2 pi i e / p), e in [0, p)
   int* d_err;        // device error word written by bounded waits

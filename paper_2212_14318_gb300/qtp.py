@@ -21,6 +21,7 @@ QTP_OK = 0
 STATUS_NAMES = {0: "QTP_OK", 1: "QTP_ERR_INVALID_ARG", 2: "QTP_ERR_UNSUPPORTED", 3: "QTP_ERR_WORKSPACE",
                 4: "QTP_ERR_CUDA", 5: "QTP_ERR_TIMEOUT", 6: "QTP_ERR_INTERNAL"}
 PRECISIONS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+PLAN_AUTOTUNE = 1
 
 # Every function the C header declares, with (restype, argtypes).
 _vp = ctypes.c_void_p
@@ -29,6 +30,7 @@ _sz = ctypes.c_size_t
 SIGNATURES = {
     "qtp_plan_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, ctypes.c_uint]),
     "qtp_plan_destroy": (_i, [_vp]),
+    "qtp_plan_get_tiles": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "qtp_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "qtp_backward_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "qtp_forward": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -109,13 +111,14 @@ def _check_tensor(t, shape, name):
 class Plan:
     """A qtp_plan for C = A * B with A in Q^{m x n x p}, B in Q^{n x s x p}."""
 
-    def __init__(self, m: int, n: int, s: int, p: int, precision: str = "bf16x3"):
+    def __init__(self, m: int, n: int, s: int, p: int, precision: str = "bf16x3", autotune: bool = False):
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {list(PRECISIONS)}")
         self.m, self.n, self.s, self.p = m, n, s, p
         self.precision = precision
         h = ctypes.c_void_p()
-        _check(lib().qtp_plan_create(ctypes.byref(h), m, n, s, p, PRECISIONS[precision], 0), "qtp_plan_create")
+        _check(lib().qtp_plan_create(ctypes.byref(h), m, n, s, p, PRECISIONS[precision],
+                                     PLAN_AUTOTUNE if autotune else 0), "qtp_plan_create")
         self._h = h
         self._ws = None
         self._bws = None
@@ -179,6 +182,12 @@ class Plan:
         _check(lib().qtp_backward(self._h, _ptr(dC), _ptr(A), _ptr(B), _ptr(dA), _ptr(dB), _ptr(ws),
                                   ws.numel() * ws.element_size(), _stream(stream)), "qtp_backward")
         return dA, dB
+
+    def tiles(self):
+        """Tensor-core tile choice per product kind (forward, dA, dB); see qtp_plan_get_tiles."""
+        buf = (ctypes.c_int * 3)()
+        _check(lib().qtp_plan_get_tiles(self._h, buf), "qtp_plan_get_tiles")
+        return [int(x) for x in buf]
 
     def set_tracing(self, enable: bool = True):
         _check(lib().qtp_plan_set_tracing(self._h, 1 if enable else 0), "qtp_plan_set_tracing")

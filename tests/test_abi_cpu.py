@@ -53,7 +53,7 @@ def test_plan_rejects_bad_shapes(lib, dims, status):
 
 def test_plan_rejects_bad_flags_and_precision(lib):
     h = ctypes.c_void_p()
-    assert lib.qtp_plan_create(ctypes.byref(h), 4, 4, 4, 4, 0, 1) == 1
+    assert lib.qtp_plan_create(ctypes.byref(h), 4, 4, 4, 4, 0, 4) == 1   # unknown flag bit
     assert lib.qtp_plan_create(ctypes.byref(h), 4, 4, 4, 4, 7, 0) == 1
     assert lib.qtp_plan_create(None, 4, 4, 4, 4, 0, 0) == 1
 

@@ -1,0 +1,39 @@
+"""Autotuned tile choice (QTP_PLAN_AUTOTUNE): valid, accurate, cached."""
+import os
+
+import pytest
+
+import oracle as Q
+from paper_2212_14318_gb300 import synth
+from tests._gpu import assert_close, to_dev, to_host
+from tests._qlayout import planes_to_comp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("m,n,s,p", [(200, 96, 200, 8), (40, 500, 60, 4)])
+def test_autotuned_plan_is_accurate_and_respects_the_accuracy_rule(m, n, s, p, tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("QTP_AUTOTUNE_CACHE", str(cache))
+    from paper_2212_14318_gb300 import qtp
+    A = synth.quat_normal(m, n, p, 3)
+    B = synth.quat_normal(n, s, p, 4)
+    plan = qtp.Plan(m, n, s, p, "bf16x3", autotune=True)
+    tiles = plan.tiles()
+    assert all(t in (1, 2, 3) for t in tiles), tiles
+    # long reductions (K = n for the forward product) must use split accumulators
+    if n > 384:
+        assert tiles[0] == 3
+    C = to_host(plan.forward(to_dev(A), to_dev(B)))
+    plan.sync()
+    assert_close(C, Q.tprod_def(planes_to_comp(A), planes_to_comp(B)), 1e-5, 1e-4, "autotuned")
+    G = synth.quat_normal(m, s, p, 5)
+    dA, dB = plan.backward(to_dev(G), to_dev(A), to_dev(B))
+    Aq, Bq, Gq = planes_to_comp(A), planes_to_comp(B), planes_to_comp(G)
+    assert_close(to_host(dA), Q.tprod_def(Gq, Q.conj_transpose(Bq)), 1e-5, 1e-4, "autotuned dA")
+    assert_close(to_host(dB), Q.tprod_def(Q.conj_transpose(Aq), Gq), 1e-5, 1e-4, "autotuned dB")
+    # a second plan of the same shape reuses the choice
+    assert qtp.Plan(m, n, s, p, "bf16x3", autotune=True).tiles() == tiles
+    if os.path.exists(cache):
+        lines = cache.read_text().split("\n")
+        assert any(f":{m}:{n}:{s}:{p}:1 " in ln for ln in lines)
