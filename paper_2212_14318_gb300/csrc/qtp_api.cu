@@ -115,8 +115,8 @@ qtp_status check_host_ptr(const void* ptr, const char* name) {
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-int nblocks_for(long long rows, long long cols, int p) {
-  const long long T = fft_tubes_per_block(p);
+int nblocks_for(long long rows, long long cols, int p, bool inv) {
+  const long long T = fft_tubes_per_block(p, inv);
   return (int)((2 * rows * cols + T - 1) / T);
 }
 
@@ -456,11 +456,11 @@ qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, floa
   jobs[0].in = (const float2*)A;
   jobs[0].out = ws + L.sa;
   jobs[0].rows = pl->m; jobs[0].cols = pl->n; jobs[0].ld = (int)spec_ld(fmt, pl->n);
-  jobs[0].nblocks = nblocks_for(pl->m, pl->n, pl->p);
+  jobs[0].nblocks = nblocks_for(pl->m, pl->n, pl->p, false);
   jobs[1].in = (const float2*)B;
   jobs[1].out = ws + L.sb;
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
-  jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p);
+  jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p, false);
   trace(pl, 0, st);
   QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "forward tube FFT");
   trace(pl, 1, st);
@@ -471,7 +471,7 @@ qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, floa
   ij.in = (const float2*)(ws + L.sc);
   ij.out = (float2*)C;
   ij.rows = pl->m; ij.cols = pl->s;
-  ij.nblocks = nblocks_for(pl->m, pl->s, pl->p);
+  ij.nblocks = nblocks_for(pl->m, pl->s, pl->p, true);
   QTP_CUDA(launch_fft_inv(&ij, 1, pl->rp, pl->d_tw, st), "inverse tube FFT");
   trace(pl, 3, st);
   return QTP_OK;
@@ -657,18 +657,18 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
   jobs[0].in = (const float2*)A;
   jobs[0].out = ws + L.sa;
   jobs[0].rows = pl->m; jobs[0].cols = pl->n; jobs[0].ld = (int)spec_ld(fmt, pl->n);
-  jobs[0].nblocks = nblocks_for(pl->m, pl->n, pl->p);
+  jobs[0].nblocks = nblocks_for(pl->m, pl->n, pl->p, false);
   jobs[1].in = (const float2*)B;
   jobs[1].out = ws + L.sb;
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
-  jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p);
+  jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p, false);
   trace(pl, 0, st);
   QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "backward FFT of A, B");
   FftFwdJob gj;
   gj.in = (const float2*)dC;
   gj.out = ws + L.sg;
   gj.rows = pl->m; gj.cols = pl->s; gj.ld = (int)spec_ld(fmt, pl->s);
-  gj.nblocks = nblocks_for(pl->m, pl->s, pl->p);
+  gj.nblocks = nblocks_for(pl->m, pl->s, pl->p, false);
   QTP_CUDA(launch_fft_fwd(&gj, 1, fmt, pl->rp, pl->d_tw, st), "backward FFT of dC");
   trace(pl, 1, st);
   // Step 2.
@@ -683,14 +683,14 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
     ij[nj].in = (const float2*)(ws + L.sda);
     ij[nj].out = (float2*)dA;
     ij[nj].rows = pl->m; ij[nj].cols = pl->n;
-    ij[nj].nblocks = nblocks_for(pl->m, pl->n, pl->p);
+    ij[nj].nblocks = nblocks_for(pl->m, pl->n, pl->p, true);
     ++nj;
   }
   if (dB) {
     ij[nj].in = (const float2*)(ws + L.sdb);
     ij[nj].out = (float2*)dB;
     ij[nj].rows = pl->n; ij[nj].cols = pl->s;
-    ij[nj].nblocks = nblocks_for(pl->n, pl->s, pl->p);
+    ij[nj].nblocks = nblocks_for(pl->n, pl->s, pl->p, true);
     ++nj;
   }
   QTP_CUDA(launch_fft_inv(ij, nj, pl->rp, pl->d_tw, st), "backward inverse FFT");

@@ -46,7 +46,7 @@ struct qtp_batch_plan {
   int* d_err = nullptr;
   int n_fwd = 0, n_inv = 0, n_probs = 0;
   long long fwd_blocks = 0, inv_blocks = 0, total_tiles = 0;
-  size_t fft_smem = 0;
+  size_t fwd_smem = 0, inv_smem = 0;
   // host copies needed to encode tensor maps
   std::vector<GroupProblem> h_probs;
   std::vector<int> prod_of_prob;  // product index of each GroupProblem
@@ -112,7 +112,7 @@ void trace(qtp_batch_plan* b, int i, cudaStream_t st, bool capturing) {
 // The three grouped launches of one forward call, on stream st.
 qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing) {
   trace(b, 0, st, capturing);
-  BP_CUDA(launch_fft_fwd_grouped(b->d_fwd, b->d_fwd_job, b->fwd_blocks, b->fmt, b->d_ptrs, ws, b->d_tw, b->fft_smem, st),
+  BP_CUDA(launch_fft_fwd_grouped(b->d_fwd, b->d_fwd_job, b->fwd_blocks, b->fmt, b->d_ptrs, ws, b->d_tw, b->fwd_smem, st),
           "batched forward FFT");
   trace(b, 1, st, capturing);
   if (b->precision == QTP_PREC_FP32) {
@@ -123,7 +123,7 @@ qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing)
             "batched products (tensor cores)");
   }
   trace(b, 2, st, capturing);
-  BP_CUDA(launch_fft_inv_grouped(b->d_inv, b->d_inv_job, b->inv_blocks, b->d_ptrs, ws, b->d_tw, b->fft_smem, st),
+  BP_CUDA(launch_fft_inv_grouped(b->d_inv, b->d_inv_job, b->inv_blocks, b->d_ptrs, ws, b->d_tw, b->inv_smem, st),
           "batched inverse FFT");
   trace(b, 3, st, capturing);
   return QTP_OK;
@@ -209,11 +209,12 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   std::vector<FftGroupJob> fwd, inv;
   size_t off = 0;
   long long fb = 0, ib = 0, tiles = 0;
-  size_t smem = 0;
+  size_t fsmem = 0, ismem = 0;
   for (int idx : order) {
     const qtp_shape& q = shapes[idx];
-    const int T = fft_tubes_per_block(q.p);
-    smem = std::max(smem, fft_smem_bytes_for(q.p));
+    const int Tf = fft_tubes_per_block(q.p, false), Ti = fft_tubes_per_block(q.p, true);
+    fsmem = std::max(fsmem, fft_smem_bytes_for(q.p, false));
+    ismem = std::max(ismem, fft_smem_bytes_for(q.p, true));
     const RadixPlan rp = make_radix_plan(q.p);
     const size_t sa = off;
     off += spec_bytes_of(fmt, q.p, q.m, q.n);
@@ -222,6 +223,7 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
     const size_t sc = off;
     off += c32_bytes_of(q.p, q.m, q.s);
     auto job = [&](int which, int rows, int cols, size_t spec, long long& counter) {
+      const int T = which == 2 ? Ti : Tf;
       FftGroupJob j;
       memset(&j, 0, sizeof(j));
       j.block_begin = counter;
@@ -275,7 +277,8 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   b->fwd_blocks = fb;
   b->inv_blocks = ib;
   b->total_tiles = tiles;
-  b->fft_smem = smem;
+  b->fwd_smem = fsmem;
+  b->inv_smem = ismem;
 
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);

@@ -86,14 +86,14 @@ RadixPlan make_radix_plan(int p) {
   return rp;
 }
 
-size_t fft_smem_bytes_for(int p) {
-  const size_t fixed = fft_fixed_smem(p);
+size_t fft_smem_bytes_for(int p, bool inv) {
+  const size_t fixed = fft_fixed_smem(p, inv);
   if (fixed) return fixed;
-  return fft_smem_bytes(p, fft_tubes_per_block(p));
+  return fft_smem_bytes(p, fft_tubes_per_block(p, inv));
 }
 
-int fft_tubes_per_block(int p) {
-  const int fixed = fft_fixed_tubes(p);
+int fft_tubes_per_block(int p, bool inv) {
+  const int fixed = fft_fixed_tubes(p, inv);
   if (fixed) return fixed;
   int T = kFftElemsPerBuf / (p | 1);
   if (T > kFftMaxTubes) T = kFftMaxTubes;
@@ -108,7 +108,7 @@ cudaError_t launch_twiddles(float2* tw, int p, cudaStream_t st) {
 template <int FMT>
 static cudaError_t launch_fwd_fmt(const FftFwdJob* jobs, int njobs, const RadixPlan& rp, const float2* tw,
                                   cudaStream_t st) {
-  const int T = fft_tubes_per_block(rp.p);
+  const int T = fft_tubes_per_block(rp.p, false);
   const size_t smem = fft_smem_bytes(rp.p, T);
   cudaError_t e = cudaFuncSetAttribute(fft_fwd_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -121,7 +121,7 @@ static cudaError_t launch_fwd_fmt(const FftFwdJob* jobs, int njobs, const RadixP
 
 cudaError_t launch_fft_fwd(const FftFwdJob* jobs, int njobs, int fmt, const RadixPlan& rp, const float2* tw,
                            cudaStream_t st) {
-  if (fft_fixed_tubes(rp.p)) return launch_fft_fwd_fixed(jobs, njobs, fmt, rp.p, tw, st);
+  if (fft_fixed_tubes(rp.p, false)) return launch_fft_fwd_fixed(jobs, njobs, fmt, rp.p, tw, st);
   switch (fmt) {
     case FMT_C32: return launch_fwd_fmt<FMT_C32>(jobs, njobs, rp, tw, st);
     case FMT_BF16X3: return launch_fwd_fmt<FMT_BF16X3>(jobs, njobs, rp, tw, st);
@@ -132,8 +132,8 @@ cudaError_t launch_fft_fwd(const FftFwdJob* jobs, int njobs, int fmt, const Radi
 
 cudaError_t launch_fft_inv(const FftInvJob* jobs, int njobs, const RadixPlan& rp, const float2* tw,
                            cudaStream_t st) {
-  if (fft_fixed_tubes(rp.p)) return launch_fft_inv_fixed(jobs, njobs, rp.p, tw, st);
-  const int T = fft_tubes_per_block(rp.p);
+  if (fft_fixed_tubes(rp.p, true)) return launch_fft_inv_fixed(jobs, njobs, rp.p, tw, st);
+  const int T = fft_tubes_per_block(rp.p, true);
   const size_t smem = fft_smem_bytes(rp.p, T);
   cudaError_t e = cudaFuncSetAttribute(fft_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -37,20 +37,25 @@ __host__ __device__ constexpr Radices radices_of(int p) {
 }
 
 // Tubes per CTA: about QTP_FFT_ELEMS complex per buffer (2304: ~34 KB per CTA,
-// six resident CTAs per SM; measured faster than 4608), a multiple of 32 tubes.
+// up to six resident CTAs per SM; measured faster than 4608), even so that tube
+// pairs never straddle a CTA, a multiple of 32 from 32 up.  The forward
+// transform keeps at least 32 tubes (its frequency-major store writes runs of
+// T tubes; shorter runs measured slower at p = 128); the inverse, whose stores
+// are contiguous tubes, takes the smaller count for occupancy.
 #ifndef QTP_FFT_ELEMS
 #define QTP_FFT_ELEMS 2304
 #endif
-__host__ __device__ constexpr int tubes_for(int p) {
+__host__ __device__ constexpr int tubes_for(int p, bool inv) {
   int t = QTP_FFT_ELEMS / (p | 1);
   if (t > 512) t = 512;
-  t = t >= 32 ? t / 32 * 32 : t / 2 * 2;  // even: tube pairs never straddle a CTA
+  if (!inv && t < 32 && p <= 128) t = 32;
+  t = t >= 32 ? t / 32 * 32 : t / 2 * 2;
   return t < 2 ? 2 : t;
 }
 
-template <int P>
+template <int P, bool INV>
 constexpr size_t smem_for() {
-  return (size_t)2 * tubes_for(P) * (P | 1) * sizeof(float2) + (size_t)tubes_for(P) * sizeof(long long);
+  return (size_t)2 * tubes_for(P, INV) * (P | 1) * sizeof(float2) + (size_t)tubes_for(P, INV) * sizeof(long long);
 }
 
 // Radix-R Stockham butterfly j of one tube, Ns = length already transformed.
@@ -102,7 +107,7 @@ __device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const
   } else {
     constexpr int R = RL.r[ST];
     constexpr int NB = P / R;
-    constexpr int T = tubes_for(P);
+    constexpr int T = tubes_for(P, INV);
     constexpr int PP = P | 1;
     constexpr bool FMI = IN_FM && ST == 0;
     constexpr bool FMO = OUT_FM && ST == RL.n - 1;
@@ -124,7 +129,7 @@ __device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const
 template <int P, int FMT>
 __device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b, const float2* __restrict__ tw,
                                                float2* smem) {
-  constexpr int T = tubes_for(P);
+  constexpr int T = tubes_for(P, false);
   constexpr int PP = P | 1;
   constexpr int NPARTS = FMT == FMT_BF16X3 ? 4 : (FMT == FMT_BF16 ? 2 : 1);
   float2* buf0 = smem;
@@ -230,7 +235,7 @@ __device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b
 template <int P>
 __device__ __forceinline__ void fixed_inv_body(const FftInvJob& job, long long b, const float2* __restrict__ tw,
                                                float2* smem) {
-  constexpr int T = tubes_for(P);
+  constexpr int T = tubes_for(P, true);
   constexpr int PP = P | 1;
   float2* buf0 = smem;
   float2* buf1 = buf0 + T * PP;
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(kThreads) fft_inv_grouped(const FftGroupJob* _
 
 template <int P, int FMT>
 cudaError_t fwd_launch(const FftFwdJob* jobs, int njobs, const float2* tw, cudaStream_t st) {
-  constexpr size_t smem = smem_for<P>();
+  constexpr size_t smem = smem_for<P, false>();
   cudaError_t e = cudaFuncSetAttribute(fft_fwd_fixed<P, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
@@ -401,7 +406,7 @@ cudaError_t fwd_fmt(const FftFwdJob* jobs, int njobs, int fmt, const float2* tw,
 
 template <int P>
 cudaError_t inv_launch(const FftInvJob* jobs, int njobs, const float2* tw, cudaStream_t st) {
-  constexpr size_t smem = smem_for<P>();
+  constexpr size_t smem = smem_for<P, true>();
   cudaError_t e = cudaFuncSetAttribute(fft_inv_fixed<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
@@ -413,18 +418,15 @@ cudaError_t inv_launch(const FftInvJob* jobs, int njobs, const float2* tw, cudaS
 
 }  // namespace
 
-size_t fft_fixed_smem(int p) {
+size_t fft_fixed_smem(int p, bool inv) {
+#define QTP_SMEM_CASE(P) \
+  case P: return inv ? smem_for<P, true>() : smem_for<P, false>();
   switch (p) {
-    case 8: return smem_for<8>();
-    case 12: return smem_for<12>();
-    case 16: return smem_for<16>();
-    case 31: return smem_for<31>();
-    case 32: return smem_for<32>();
-    case 64: return smem_for<64>();
-    case 100: return smem_for<100>();
-    case 128: return smem_for<128>();
+    QTP_SMEM_CASE(8) QTP_SMEM_CASE(12) QTP_SMEM_CASE(16) QTP_SMEM_CASE(31)
+    QTP_SMEM_CASE(32) QTP_SMEM_CASE(64) QTP_SMEM_CASE(100) QTP_SMEM_CASE(128)
     default: return 0;
   }
+#undef QTP_SMEM_CASE
 }
 
 cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks, int fmt,
@@ -463,16 +465,9 @@ cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_o
   return cudaGetLastError();
 }
 
-int fft_fixed_tubes(int p) {
+int fft_fixed_tubes(int p, bool inv) {
   switch (p) {
-    case 8: return tubes_for(8);
-    case 12: return tubes_for(12);
-    case 16: return tubes_for(16);
-    case 31: return tubes_for(31);
-    case 32: return tubes_for(32);
-    case 64: return tubes_for(64);
-    case 100: return tubes_for(100);
-    case 128: return tubes_for(128);
+    case 8: case 12: case 16: case 31: case 32: case 64: case 100: case 128: return tubes_for(p, inv);
     default: return 0;
   }
 }

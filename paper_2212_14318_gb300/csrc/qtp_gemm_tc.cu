@@ -98,9 +98,23 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   const int lane = threadIdx.x & 31;
   const int nt = blockIdx.x;
   const int mt = blockIdx.y;
-  const int f = blockIdx.z >> 1;
-  const int h = blockIdx.z & 1;
   const int p = args.p;
+  // Frequencies in pairs (0, p/2 alone; then q, p - q adjacent): the tiles of f
+  // and -f read the same B spectra (B(f) and B(-f)), so running them together
+  // keeps those in L2.
+  const int fi = blockIdx.z >> 1;
+  const int h = blockIdx.z & 1;
+  int f;
+  {
+    const int single = (p & 1) ? 1 : 2;  // frequencies paired with themselves
+    if (fi < single) {
+      f = fi == 0 ? 0 : p / 2;
+    } else {
+      const int j = fi - single;
+      const int q = 1 + (j >> 1);
+      f = (j & 1) ? p - q : q;
+    }
+  }
   const int nkb = (args.K + BK - 1) / BK;
   const int total = 2 * nkb;
 
@@ -177,7 +191,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(A_MN, B_MN, BN);
+      // MMA width: this tile's valid columns rounded up to 16 (<= BN)
+      int nw = args.N - nt * BN;
+      nw = nw > BN ? BN : ((nw + 15) & ~15);
+      const uint32_t idesc = make_idesc(A_MN, B_MN, nw);
       const uint32_t d_re = tmem;
       const uint32_t d_im = tmem + (uint32_t)BN;
       const uint32_t c_re = SPLIT ? tmem + 2u * BN : d_re;  // correction accumulators

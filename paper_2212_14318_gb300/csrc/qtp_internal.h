@@ -53,8 +53,8 @@ struct FftInvJob {
   int nblocks;
 };
 
-int fft_tubes_per_block(int p);
-size_t fft_smem_bytes_for(int p);  // dynamic shared memory of one FFT CTA for tube length p
+int fft_tubes_per_block(int p, bool inv);  // tubes per CTA of the forward / inverse transform
+size_t fft_smem_bytes_for(int p, bool inv);  // dynamic shared memory of one such CTA
 
 // Grouped (batched) tube FFTs: one job per tensor of each product.
 struct FftGroupJob {
@@ -74,12 +74,12 @@ cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_o
 cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks,
                                    const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
                                    cudaStream_t st);
-size_t fft_fixed_smem(int p);
+size_t fft_fixed_smem(int p, bool inv);
 
 // Compile-time specialisations (qtp_fft_fixed.cu) for the common tube lengths:
 // tubes per CTA, or 0 when p has none; the launches return
 // cudaErrorNotSupported for other p.
-int fft_fixed_tubes(int p);
+int fft_fixed_tubes(int p, bool inv);
 cudaError_t launch_fft_fwd_fixed(const FftFwdJob* jobs, int njobs, int fmt, int p, const float2* tw,
                                  cudaStream_t st);
 cudaError_t launch_fft_inv_fixed(const FftInvJob* jobs, int njobs, int p, const float2* tw, cudaStream_t st);
