@@ -500,13 +500,14 @@ def run_batch(args):
         "dtype": {"bf16x3": "bf16x3+f32", "bf16": "bf16+f32", "fp32": "f32"}[args.precision],
         "data": "synthetic (seeded)",
         "config": {"workload": f"batch: {len(shapes)} products, m,n,s log-uniform [16,256], "
-                               "p in {8,12,16,31,32,64,100,128}, N(0,1), one grouped launch per stage, CUDA graph",
+                               "p in {8,12,16,31,32,64,100,128}, N(0,1), transforms one launch per tube length, "
+                               "products one persistent launch, CUDA graph",
                    "precision": args.precision, "l2": "inputs larger than L2; 256 MB flush before every step"},
         "rel_err": rel, "roofline": roof, "stages": stages, "fp32_path": fp32,
         "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(sum(a.numel() * 4 for a in As) + sum(b.numel() * 4 for b in Bs)),
                 "d2h_bytes_per_step": int(sum(c.numel() * 4 for c in dC))},
-        "gpu_launches": 3 * args.steps, "clocks": clocks,
+        "gpu_launches": (2 * len({q[3] for q in shapes}) + 1) * args.steps, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 

@@ -2,10 +2,11 @@
 // independent products C_i = A_i * B_i of uneven (m, n, s, p), each by
 // Algorithm 5.1, in three grouped launches replayed from a CUDA graph.
 //
-//   1. fft_fwd_grouped  - every tube of every A_i and B_i (Step 1)
+//   1. fft_fwd_grouped  - every tube of every A_i and B_i (Step 1): one
+//                         launch per distinct tube length p
 //   2. products         - all frequencies of all products (Step 2): one
 //                         persistent tcgen05 launch, or one FP32 launch
-//   3. fft_inv_grouped  - every tube of every C_i (Step 3)
+//   3. fft_inv_grouped  - every tube of every C_i (Step 3), one launch per p
 //
 // The plan buckets the products by tube length p, then by size, so that CTAs
 // working at the same time share a kernel specialisation and their
@@ -23,6 +24,13 @@
 #include "qtp_internal.h"
 
 using namespace qtp;
+
+// The CTAs of one tube length in a grouped transform: one launch.
+struct FftRange {
+  int p;
+  long long block0, nblocks;
+  size_t smem;
+};
 
 struct qtp_batch_plan {
   int count = 0;
@@ -46,7 +54,7 @@ struct qtp_batch_plan {
   int* d_err = nullptr;
   int n_fwd = 0, n_inv = 0, n_probs = 0;
   long long fwd_blocks = 0, inv_blocks = 0, total_tiles = 0;
-  size_t fwd_smem = 0, inv_smem = 0;
+  std::vector<FftRange> fwd_ranges, inv_ranges;
   // host copies needed to encode tensor maps
   std::vector<GroupProblem> h_probs;
   std::vector<int> prod_of_prob;  // product index of each GroupProblem
@@ -112,8 +120,10 @@ void trace(qtp_batch_plan* b, int i, cudaStream_t st, bool capturing) {
 // The three grouped launches of one forward call, on stream st.
 qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing) {
   trace(b, 0, st, capturing);
-  BP_CUDA(launch_fft_fwd_grouped(b->d_fwd, b->d_fwd_job, b->fwd_blocks, b->fmt, b->d_ptrs, ws, b->d_tw, b->fwd_smem, st),
-          "batched forward FFT");
+  for (const FftRange& r : b->fwd_ranges)
+    BP_CUDA(launch_fft_fwd_grouped(b->d_fwd, b->d_fwd_job, r.block0, r.nblocks, r.p, b->fmt, b->d_ptrs, ws, b->d_tw,
+                                   r.smem, st),
+            "batched forward FFT");
   trace(b, 1, st, capturing);
   if (b->precision == QTP_PREC_FP32) {
     BP_CUDA(launch_gemm_simt_grouped(b->d_probs, b->d_prob_tile, b->total_tiles, ws, st), "batched products (fp32)");
@@ -123,8 +133,10 @@ qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing)
             "batched products (tensor cores)");
   }
   trace(b, 2, st, capturing);
-  BP_CUDA(launch_fft_inv_grouped(b->d_inv, b->d_inv_job, b->inv_blocks, b->d_ptrs, ws, b->d_tw, b->inv_smem, st),
-          "batched inverse FFT");
+  for (const FftRange& r : b->inv_ranges)
+    BP_CUDA(launch_fft_inv_grouped(b->d_inv, b->d_inv_job, r.block0, r.nblocks, r.p, b->d_ptrs, ws, b->d_tw, r.smem,
+                                   st),
+            "batched inverse FFT");
   trace(b, 3, st, capturing);
   return QTP_OK;
 }
@@ -209,12 +221,9 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   std::vector<FftGroupJob> fwd, inv;
   size_t off = 0;
   long long fb = 0, ib = 0, tiles = 0;
-  size_t fsmem = 0, ismem = 0;
   for (int idx : order) {
     const qtp_shape& q = shapes[idx];
     const int Tf = fft_tubes_per_block(q.p, false), Ti = fft_tubes_per_block(q.p, true);
-    fsmem = std::max(fsmem, fft_smem_bytes_for(q.p, false));
-    ismem = std::max(ismem, fft_smem_bytes_for(q.p, true));
     const RadixPlan rp = make_radix_plan(q.p);
     const size_t sa = off;
     off += spec_bytes_of(fmt, q.p, q.m, q.n);
@@ -277,8 +286,20 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   b->fwd_blocks = fb;
   b->inv_blocks = ib;
   b->total_tiles = tiles;
-  b->fwd_smem = fsmem;
-  b->inv_smem = ismem;
+  // launch ranges: jobs are ordered by p, so each p's CTAs are contiguous
+  auto ranges = [](const std::vector<FftGroupJob>& jobs, long long total, bool inv) {
+    std::vector<FftRange> r;
+    for (size_t j = 0; j < jobs.size(); ++j) {
+      if (r.empty() || r.back().p != jobs[j].p) {
+        if (!r.empty()) r.back().nblocks = jobs[j].block_begin - r.back().block0;
+        r.push_back(FftRange{jobs[j].p, jobs[j].block_begin, 0, fft_smem_bytes_for(jobs[j].p, inv)});
+      }
+    }
+    if (!r.empty()) r.back().nblocks = total - r.back().block0;
+    return r;
+  };
+  b->fwd_ranges = ranges(fwd, fb, false);
+  b->inv_ranges = ranges(inv, ib, true);
 
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);

@@ -3,6 +3,8 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "qtp_internal.h"
 
 namespace qtp {
@@ -38,28 +40,84 @@ __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2&
   v3 = csub(a1, b1);
 }
 
-// Length-R DFT in registers.  Generic version: direct sum with roots of unity
-// read from the length-p table (omega_R^e = w^(e p / R)).
+// cos and sin of 2 pi k / n in double, usable as compile-time constants: the
+// angle is reduced to [-pi, pi] and summed by its Taylor series up to x^61
+// (within 1e-13 of the exact value, far below the float rounding the kernels
+// apply to it).
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+__host__ __device__ constexpr double turn_angle(int k, int n) {
+  k %= n;
+  if (2 * k > n) k -= n;
+  return kTwoPi * (double)k / (double)n;
+}
+__host__ __device__ constexpr double cos_turn(int k, int n) {
+  const double x = turn_angle(k, n);
+  double t = 1.0, sum = 1.0;
+  for (int i = 1; i <= 30; ++i) {
+    t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+    sum += t;
+  }
+  return sum;
+}
+__host__ __device__ constexpr double sin_turn(int k, int n) {
+  const double x = turn_angle(k, n);
+  double t = x, sum = x;
+  for (int i = 1; i <= 30; ++i) {
+    t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+    sum += t;
+  }
+  return sum;
+}
+
+// Calls f(integral_constant<int, I>) for I = B .. E-1, so that f's body sees
+// I as a constant expression.
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// Length-R DFT in registers, R odd: X[u] = sum_r x_r w^(r u), w = e^(-2 pi i/R)
+// (conjugate for the inverse).  Pairing r with R - r,
+//   X[u]     = A_u - i B_u,   X[R - u] = A_u + i B_u   (forward; signs of B
+//   swap for the inverse), A_u = x_0 + sum_r (x_r + x_{R-r}) cos(2 pi r u / R),
+//   B_u = sum_r (x_r - x_{R-r}) sin(2 pi r u / R),  r = 1 .. (R-1)/2,
+// a quarter of the multiplies of the plain sum, with the cosines and sines as
+// immediate constants.
 template <int R, bool INV>
 struct Dft {
-  __device__ __forceinline__ static void run(float2 (&v)[R], const float2* __restrict__ tw, int p) {
-    float2 w[R];
-    const int step = p / R;
+  static_assert(R % 2 == 1 && R >= 3, "odd radix");
+  __device__ __forceinline__ static void run(float2 (&v)[R], const float2*, int) {
+    constexpr int H = (R - 1) / 2;
+    float2 sp[H], dm[H];
+    const float2 x0 = v[0];
+    float2 dc = x0;
 #pragma unroll
-    for (int e = 0; e < R; ++e) w[e] = twid<INV>(tw, e * step);
-    float2 o[R];
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-      float2 acc = v[0];
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 t = cmul(v[r], w[(r * u) % R]);
-        acc = cadd(acc, t);
-      }
-      o[u] = acc;
+    for (int r = 1; r <= H; ++r) {
+      sp[r - 1] = cadd(v[r], v[R - r]);
+      dm[r - 1] = csub(v[r], v[R - r]);
+      dc = cadd(dc, sp[r - 1]);
     }
-#pragma unroll
-    for (int u = 0; u < R; ++u) v[u] = o[u];
+    v[0] = dc;
+    static_for<1, H + 1>([&](auto uc) {
+      constexpr int u = decltype(uc)::value;
+      float2 a = x0, bsum = make_float2(0.f, 0.f);
+      static_for<1, H + 1>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        constexpr float c = (float)cos_turn(r * u, R);
+        constexpr float sn = (float)sin_turn(r * u, R);
+        a.x = fmaf(sp[r - 1].x, c, a.x);
+        a.y = fmaf(sp[r - 1].y, c, a.y);
+        bsum.x = fmaf(dm[r - 1].x, sn, bsum.x);
+        bsum.y = fmaf(dm[r - 1].y, sn, bsum.y);
+      });
+      // -i B = (B.y, -B.x)
+      const float2 mib = make_float2(bsum.y, -bsum.x);
+      v[u] = INV ? csub(a, mib) : cadd(a, mib);
+      v[R - u] = INV ? cadd(a, mib) : csub(a, mib);
+    });
   }
 };
 

@@ -80,19 +80,73 @@ __device__ __forceinline__ void bfly(const float2* __restrict__ in, float2* __re
 #pragma unroll
     for (int r = 0; r < R; ++r) out[(base + r * NS) * OES] = v[r];
   } else {
-    // prime radix > 8: direct DFT of length R from shared memory
-#pragma unroll 1
-    for (int u = 0; u < R; ++u) {
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 1
-      for (int r = 0; r < R; ++r) {
-        float2 x = in[(j + r * stride) * IES];
-        if (NS > 1 && r > 0) x = cmul(x, twid<INV>(tw, r * k * twstep));
-        const int e = ((r * u) % R) * stride;
-        acc = cadd(acc, cmul(x, twid<INV>(tw, e)));
-      }
-      out[(base + u * NS) * OES] = acc;
+    static_assert(R < 0, "radices above 8 go through bfly_odd");
+  }
+}
+
+// Odd radix R > 8, output pairs (u, R - u) for u in group G (4 pairs per
+// group): one thread per (tube, butterfly, group) keeps the register count of
+// the radix-R DFT low and spreads its work over all threads of the CTA.  Same
+// symmetric form as Dft<R> (x_r +- x_{R-r} against compile-time cos / sin).
+constexpr int kOddPairsPerThread = 4;
+template <int R>
+__host__ __device__ constexpr int odd_groups() {
+  return ((R - 1) / 2 + kOddPairsPerThread - 1) / kOddPairsPerThread;
+}
+
+template <int R, int NS, int P, bool INV, int IES, int OES, int G>
+__device__ __forceinline__ void bfly_odd(const float2* __restrict__ in, float2* __restrict__ out, int j,
+                                         const float2* __restrict__ tw) {
+  constexpr int H = (R - 1) / 2;
+  constexpr int stride = P / R;
+  constexpr int twstep = P / (NS * R);
+  constexpr int u0 = 1 + G * kOddPairsPerThread;
+  constexpr int u1 = u0 + kOddPairsPerThread - 1 < H ? u0 + kOddPairsPerThread - 1 : H;
+  const int k = j % NS;
+  const int base = (j / NS) * NS * R + k;
+  const float2 x0 = in[j * IES];
+  float2 sp[H], dm[H];
+#pragma unroll
+  for (int r = 1; r <= H; ++r) {
+    float2 a = in[(j + r * stride) * IES];
+    float2 c = in[(j + (R - r) * stride) * IES];
+    if (NS > 1) {
+      a = cmul(a, twid<INV>(tw, r * k * twstep));
+      c = cmul(c, twid<INV>(tw, (R - r) * k * twstep));
     }
+    sp[r - 1] = cadd(a, c);
+    dm[r - 1] = csub(a, c);
+  }
+  if constexpr (G == 0) {
+    float2 dc = x0;
+#pragma unroll
+    for (int r = 0; r < H; ++r) dc = cadd(dc, sp[r]);
+    out[base * OES] = dc;
+  }
+  static_for<u0, u1 + 1>([&](auto uc) {
+    constexpr int u = decltype(uc)::value;
+    float2 a = x0, bsum = make_float2(0.f, 0.f);
+    static_for<1, H + 1>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      constexpr float c = (float)cos_turn(r * u, R);
+      constexpr float sn = (float)sin_turn(r * u, R);
+      a.x = fmaf(sp[r - 1].x, c, a.x);
+      a.y = fmaf(sp[r - 1].y, c, a.y);
+      bsum.x = fmaf(dm[r - 1].x, sn, bsum.x);
+      bsum.y = fmaf(dm[r - 1].y, sn, bsum.y);
+    });
+    const float2 mib = make_float2(bsum.y, -bsum.x);  // -i B
+    out[(base + u * NS) * OES] = INV ? csub(a, mib) : cadd(a, mib);
+    out[(base + (R - u) * NS) * OES] = INV ? cadd(a, mib) : csub(a, mib);
+  });
+}
+
+template <int R, int NS, int P, bool INV, int IES, int OES, int G = 0>
+__device__ __forceinline__ void bfly_odd_group(const float2* __restrict__ in, float2* __restrict__ out, int j, int g,
+                                               const float2* __restrict__ tw) {
+  if constexpr (G < odd_groups<R>()) {
+    if (g == G) bfly_odd<R, NS, P, INV, IES, OES, G>(in, out, j, tw);
+    else bfly_odd_group<R, NS, P, INV, IES, OES, G + 1>(in, out, j, g, tw);
   }
 }
 
@@ -113,12 +167,18 @@ __device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const
     constexpr bool FMO = OUT_FM && ST == RL.n - 1;
     // tube-fastest: consecutive threads take consecutive tubes, so both layouts
     // are free of bank conflicts (odd stride PP, or unit stride)
-    for (int idx = threadIdx.x; idx < T * NB; idx += kThreads) {
-      const int j = idx / T;
-      const int tube = idx - j * T;
-      if (tube < Tb)
-        bfly<R, NS, P, INV, FMI ? T : 1, FMO ? T : 1>(in + (FMI ? tube : tube * PP), out + (FMO ? tube : tube * PP), j,
-                                                       tw);
+    constexpr int NG = R > 8 ? odd_groups<R>() : 1;
+    for (int idx = threadIdx.x; idx < T * NB * NG; idx += kThreads) {
+      const int g = idx / (T * NB);
+      const int rest = idx - g * (T * NB);
+      const int j = rest / T;
+      const int tube = rest - j * T;
+      if (tube < Tb) {
+        const float2* ti = in + (FMI ? tube : tube * PP);
+        float2* to = out + (FMO ? tube : tube * PP);
+        if constexpr (R > 8) bfly_odd_group<R, NS, P, INV, FMI ? T : 1, FMO ? T : 1>(ti, to, j, g, tw);
+        else bfly<R, NS, P, INV, FMI ? T : 1, FMO ? T : 1>(ti, to, j, tw);
+      }
     }
     __syncthreads();
     return stages<P, ST + 1, NS * R, INV, IN_FM, OUT_FM>(out, in, Tb, tw);
@@ -315,21 +375,23 @@ __global__ void __launch_bounds__(kThreads) fft_inv_fixed(FftInvJob job0, FftInv
 }
 
 // ---------------------------------------------------------------------------
-// Grouped transforms for batches of products with mixed (rows, cols, p): one
-// launch covers every tensor of the batch; each CTA finds its job by binary
-// (one table load: job_of_block) and runs the body specialised for that job's
-// p (or the runtime-radix body).  Tensor pointers come from a per-call
-// device table ptrs[3 * product + {0: A, 1: B, 2: C}].
+// Grouped transforms for batches of products with mixed (rows, cols, p).  The
+// plan orders the jobs by tube length, so the CTAs of one p form a contiguous
+// range of the global block space; each range is one launch of the body
+// specialised for that p (P = 0: the runtime-radix body), which keeps each
+// launch at its own register count and occupancy.  A CTA finds its job with
+// one table load (job_of_block).  Tensor pointers come from a per-call device
+// table ptrs[3 * product + {0: A, 1: B, 2: C}].
 // ---------------------------------------------------------------------------
 
-template <int FMT>
+template <int P, int FMT>
 __global__ void __launch_bounds__(kThreads) fft_fwd_grouped(const FftGroupJob* __restrict__ jobs,
-                                                            const int* __restrict__ job_of_block,
+                                                            const int* __restrict__ job_of_block, long long block0,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
   extern __shared__ float4 smem_f4[];
   float2* smem = reinterpret_cast<float2*>(smem_f4);
-  const long long b = blockIdx.x;
+  const long long b = block0 + blockIdx.x;
   const FftGroupJob& J = jobs[__ldg(job_of_block + b)];
   FftFwdJob job;
   job.in = ptrs[3 * J.prod + J.which];
@@ -340,26 +402,18 @@ __global__ void __launch_bounds__(kThreads) fft_fwd_grouped(const FftGroupJob* _
   job.nblocks = 0;
   const long long lb = b - J.block_begin;
   const float2* tw = tw_all + J.tw_off;
-  switch (J.p) {
-    case 8: fixed_fwd_body<8, FMT>(job, lb, tw, smem); break;
-    case 12: fixed_fwd_body<12, FMT>(job, lb, tw, smem); break;
-    case 16: fixed_fwd_body<16, FMT>(job, lb, tw, smem); break;
-    case 31: fixed_fwd_body<31, FMT>(job, lb, tw, smem); break;
-    case 32: fixed_fwd_body<32, FMT>(job, lb, tw, smem); break;
-    case 64: fixed_fwd_body<64, FMT>(job, lb, tw, smem); break;
-    case 100: fixed_fwd_body<100, FMT>(job, lb, tw, smem); break;
-    case 128: fixed_fwd_body<128, FMT>(job, lb, tw, smem); break;
-    default: generic_fwd_body<FMT>(job, lb, J.rp, J.T, tw, smem); break;
-  }
+  if constexpr (P == 0) generic_fwd_body<FMT>(job, lb, J.rp, J.T, tw, smem);
+  else fixed_fwd_body<P, FMT>(job, lb, tw, smem);
 }
 
+template <int P>
 __global__ void __launch_bounds__(kThreads) fft_inv_grouped(const FftGroupJob* __restrict__ jobs,
-                                                            const int* __restrict__ job_of_block,
+                                                            const int* __restrict__ job_of_block, long long block0,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
   extern __shared__ float4 smem_f4[];
   float2* smem = reinterpret_cast<float2*>(smem_f4);
-  const long long b = blockIdx.x;
+  const long long b = block0 + blockIdx.x;
   const FftGroupJob& J = jobs[__ldg(job_of_block + b)];
   FftInvJob job;
   job.in = reinterpret_cast<const float2*>(ws + J.spec_off);
@@ -369,17 +423,40 @@ __global__ void __launch_bounds__(kThreads) fft_inv_grouped(const FftGroupJob* _
   job.nblocks = 0;
   const long long lb = b - J.block_begin;
   const float2* tw = tw_all + J.tw_off;
-  switch (J.p) {
-    case 8: fixed_inv_body<8>(job, lb, tw, smem); break;
-    case 12: fixed_inv_body<12>(job, lb, tw, smem); break;
-    case 16: fixed_inv_body<16>(job, lb, tw, smem); break;
-    case 31: fixed_inv_body<31>(job, lb, tw, smem); break;
-    case 32: fixed_inv_body<32>(job, lb, tw, smem); break;
-    case 64: fixed_inv_body<64>(job, lb, tw, smem); break;
-    case 100: fixed_inv_body<100>(job, lb, tw, smem); break;
-    case 128: fixed_inv_body<128>(job, lb, tw, smem); break;
-    default: generic_inv_body(job, lb, J.rp, J.T, tw, smem); break;
+  if constexpr (P == 0) generic_inv_body(job, lb, J.rp, J.T, tw, smem);
+  else fixed_inv_body<P>(job, lb, tw, smem);
+}
+
+template <int P, int FMT>
+cudaError_t fwd_grouped_launch(const FftGroupJob* d_jobs, const int* d_job_of_block, long long block0,
+                               long long nblocks, const float2* const* d_ptrs, char* ws, const float2* d_tw,
+                               size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(fft_fwd_grouped<P, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fft_fwd_grouped<P, FMT><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, block0, d_ptrs, ws, d_tw);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t fwd_grouped_fmt(const FftGroupJob* d_jobs, const int* d_job_of_block, long long block0, long long nblocks,
+                            int fmt, const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
+                            cudaStream_t st) {
+  switch (fmt) {
+    case FMT_C32: return fwd_grouped_launch<P, FMT_C32>(d_jobs, d_job_of_block, block0, nblocks, d_ptrs, ws, d_tw, smem, st);
+    case FMT_BF16X3: return fwd_grouped_launch<P, FMT_BF16X3>(d_jobs, d_job_of_block, block0, nblocks, d_ptrs, ws, d_tw, smem, st);
+    case FMT_BF16: return fwd_grouped_launch<P, FMT_BF16>(d_jobs, d_job_of_block, block0, nblocks, d_ptrs, ws, d_tw, smem, st);
+    default: return cudaErrorInvalidValue;
   }
+}
+
+template <int P>
+cudaError_t inv_grouped_launch(const FftGroupJob* d_jobs, const int* d_job_of_block, long long block0,
+                               long long nblocks, const float2* const* d_ptrs, char* ws, const float2* d_tw,
+                               size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(fft_inv_grouped<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fft_inv_grouped<P><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, block0, d_ptrs, ws, d_tw);
+  return cudaGetLastError();
 }
 
 template <int P, int FMT>
@@ -429,40 +506,34 @@ size_t fft_fixed_smem(int p, bool inv) {
 #undef QTP_SMEM_CASE
 }
 
-cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks, int fmt,
-                                   const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
-                                   cudaStream_t st) {
+cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long block0,
+                                   long long nblocks, int p, int fmt, const float2* const* d_ptrs, char* ws,
+                                   const float2* d_tw, size_t smem, cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
   if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
-  switch (fmt) {
-    case FMT_C32:
-      e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_C32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) fft_fwd_grouped<FMT_C32><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, d_ptrs, ws, d_tw);
-      break;
-    case FMT_BF16X3:
-      e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) fft_fwd_grouped<FMT_BF16X3><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, d_ptrs, ws, d_tw);
-      break;
-    case FMT_BF16:
-      e = cudaFuncSetAttribute(fft_fwd_grouped<FMT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) fft_fwd_grouped<FMT_BF16><<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, d_ptrs, ws, d_tw);
-      break;
-    default: return cudaErrorInvalidValue;
+#define QTP_FWD_GROUPED_CASE(P) \
+  case P: return fwd_grouped_fmt<P>(d_jobs, d_job_of_block, block0, nblocks, fmt, d_ptrs, ws, d_tw, smem, st);
+  switch (p) {
+    QTP_FWD_GROUPED_CASE(8) QTP_FWD_GROUPED_CASE(12) QTP_FWD_GROUPED_CASE(16) QTP_FWD_GROUPED_CASE(31)
+    QTP_FWD_GROUPED_CASE(32) QTP_FWD_GROUPED_CASE(64) QTP_FWD_GROUPED_CASE(100) QTP_FWD_GROUPED_CASE(128)
+    default: return fwd_grouped_fmt<0>(d_jobs, d_job_of_block, block0, nblocks, fmt, d_ptrs, ws, d_tw, smem, st);
   }
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+#undef QTP_FWD_GROUPED_CASE
 }
 
-cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks,
-                                   const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
-                                   cudaStream_t st) {
+cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long block0,
+                                   long long nblocks, int p, const float2* const* d_ptrs, char* ws,
+                                   const float2* d_tw, size_t smem, cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
   if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fft_inv_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  fft_inv_grouped<<<(unsigned)nblocks, kThreads, smem, st>>>(d_jobs, d_job_of_block, d_ptrs, ws, d_tw);
-  return cudaGetLastError();
+#define QTP_INV_GROUPED_CASE(P) \
+  case P: return inv_grouped_launch<P>(d_jobs, d_job_of_block, block0, nblocks, d_ptrs, ws, d_tw, smem, st);
+  switch (p) {
+    QTP_INV_GROUPED_CASE(8) QTP_INV_GROUPED_CASE(12) QTP_INV_GROUPED_CASE(16) QTP_INV_GROUPED_CASE(31)
+    QTP_INV_GROUPED_CASE(32) QTP_INV_GROUPED_CASE(64) QTP_INV_GROUPED_CASE(100) QTP_INV_GROUPED_CASE(128)
+    default: return inv_grouped_launch<0>(d_jobs, d_job_of_block, block0, nblocks, d_ptrs, ws, d_tw, smem, st);
+  }
+#undef QTP_INV_GROUPED_CASE
 }
 
 int fft_fixed_tubes(int p, bool inv) {

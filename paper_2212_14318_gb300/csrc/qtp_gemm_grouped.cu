@@ -38,13 +38,13 @@ constexpr uint32_t G_TMEM_COLS = 512;    // 2 buffers x (re, im) x 128 columns
 
 // Operand roles of the forward product per (output half h, K half kh): A and B
 // planes, whether B is read at frequency -f, and which of the four real
-// products (ar.br, ai.bi, ar.bi, ai.br) is subtracted.  Filled on the host.
+// products (ar.br, ai.bi, ar.bi, ai.br) is subtracted.  Filled on the host;
+// entry e = 2 h + kh sits in bit e (planes, fneg) or bits 4e..4e+3 (negmask),
+// so the kernel reads registers, not an indexed copy in local memory.
 struct GViews {
-  int a_plane[2][2];
-  int b_plane[2][2];
-  int b_fneg[2][2];
-  uint32_t negmask[2][2];
+  uint32_t a_plane, b_plane, b_fneg, negmask;
 };
+__device__ __forceinline__ uint32_t gv_bit(uint32_t bits, int h, int kh) { return (bits >> (2 * h + kh)) & 1u; }
 
 struct GTile {
   int g, f, h, mt, nt;
@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t sA = base;
   const uint32_t sB = base + GSTAGES * NP * G_A_TILE;
-  const uint32_t bars = sB + GSTAGES * NP * G_B_TILE;
+  const uint32_t stg_base = sB + GSTAGES * NP * G_B_TILE;  // 4 epilogue staging areas
+  const uint32_t bars = stg_base + 4 * kStgBytes;
   const uint32_t full = bars, empty = bars + 8 * GSTAGES;
   const uint32_t acc_full = bars + 16 * GSTAGES;      // 2 barriers
   const uint32_t acc_empty = acc_full + 16;           // 2 barriers
@@ -115,15 +116,29 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       long long it = 0;
-      int cur = 0;
+      int cur = 0, prev = -1;
       bool ok = true;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
         const GTile T = decode_tile(probs, nprobs, t, cur);
         const GroupProblem& P = probs[T.g];
         const CUtensorMap* tmA = reinterpret_cast<const CUtensorMap*>(P.tmA);
         const CUtensorMap* tmB = reinterpret_cast<const CUtensorMap*>(P.tmB);
-        tensormap_acquire(tmA);
-        tensormap_acquire(tmB);
+        if (T.g != prev) {  // first tile of this product on this CTA
+          tensormap_acquire(tmA);
+          tensormap_acquire(tmB);
+          prev = T.g;
+        }
+        {  // warm the descriptor cache for the next tile's product
+          const long long tn = t + gridDim.x;
+          if (tn < total_tiles) {
+            int gn = T.g;
+            while (gn + 1 < nprobs && probs[gn + 1].tile_begin <= tn) ++gn;
+            if (gn != T.g) {
+              asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(probs[gn].tmA)) : "memory");
+              asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(probs[gn].tmB)) : "memory");
+            }
+          }
+        }
         const int nkb = (P.K + GBK - 1) / GBK;
         for (int kk = 0; kk < 2 * nkb; ++kk, ++it) {
           const int kh = kk / nkb;
@@ -143,15 +158,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
           const int nb64 = P.bn / 64;  // 64-column boxes of B in this product's tiles
           mbar_expect_tx(full + 8 * s, (uint32_t)(NP * (G_A_TILE + nb64 * (G_B_TILE / 2))));
           const int ga = T.f;
-          const int gb = V.b_fneg[T.h][kh] ? (P.p - T.f) % P.p : T.f;
+          const int gb = gv_bit(V.b_fneg, T.h, kh) ? (P.p - T.f) % P.p : T.f;
+          const int pa = (int)gv_bit(V.a_plane, T.h, kh) * NP, pb = (int)gv_bit(V.b_plane, T.h, kh) * NP;
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             const uint32_t ta = sA + (uint32_t)(s * NP + q) * G_A_TILE;
             const uint32_t tb = sB + (uint32_t)(s * NP + q) * G_B_TILE;
-            tma_load_4d(ta, tmA, full + 8 * s, k0, T.mt * GBM, ga, V.a_plane[T.h][kh] * NP + q);
-            tma_load_4d(tb, tmB, full + 8 * s, T.nt * P.bn, k0, gb, V.b_plane[T.h][kh] * NP + q);
-            if (nb64 == 2)
-              tma_load_4d(tb + 128u * GBK, tmB, full + 8 * s, T.nt * P.bn + 64, k0, gb, V.b_plane[T.h][kh] * NP + q);
+            tma_load_4d(ta, tmA, full + 8 * s, k0, T.mt * GBM, ga, pa + q);
+            tma_load_4d(tb, tmB, full + 8 * s, T.nt * P.bn, k0, gb, pb + q);
+            if (nb64 == 2) tma_load_4d(tb + 128u * GBK, tmB, full + 8 * s, T.nt * P.bn + 64, k0, gb, pb + q);
           }
         }
       }
@@ -165,6 +180,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (lane == 0) {
       const uint32_t idesc128 = make_idesc(false, true, 128);
       const uint32_t idesc64 = make_idesc(false, true, 64);
+      const uint64_t da0 = part_desc<false, GBK>(sA, 0);
+      const uint64_t db0 = part_desc<true, GBK>(sB, 0);
       long long it = 0;
       int lt = 0, cur = 0;
       bool ok = true;
@@ -172,6 +189,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const GTile T = decode_tile(probs, nprobs, t, cur);
         const int K = probs[T.g].K;
         const uint32_t idesc = probs[T.g].bn == 64 ? idesc64 : idesc128;
+        const uint32_t idesc_neg = idesc | kNegA;
         const int nkb = (K + GBK - 1) / GBK;
         const int buf = lt & 1;
         const uint32_t uph = (uint32_t)(lt >> 1) & 1u;
@@ -196,25 +214,26 @@ __global__ void __launch_bounds__(kGThreads, 1)
             break;
           }
           fence_after();
-          const uint32_t neg = V.negmask[T.h][kh];
-          const uint32_t ta = sA + (uint32_t)(s * NP) * G_A_TILE;
-          const uint32_t tb = sB + (uint32_t)(s * NP) * G_B_TILE;
+          const uint32_t neg = V.negmask >> (4 * (2 * T.h + kh));
+          // stage descriptors: base descriptor advanced in its start-address field
+          const uint64_t da = da0 + (uint64_t)((uint32_t)(s * NP * G_A_TILE) >> 4);
+          const uint64_t db = db0 + (uint64_t)((uint32_t)(s * NP * G_B_TILE) >> 4);
           const int RE = 0, IM = NP / 2;
 #pragma unroll
           for (int prod = 0; prod < 4; ++prod) {
             const int xa = (prod == 0 || prod == 2) ? RE : IM;
             const int yb = (prod == 0 || prod == 3) ? RE : IM;
             const bool to_re = prod < 2;
-            const uint32_t id = idesc | (((neg >> prod) & 1u) ? kNegA : 0u);
+            const uint32_t id = ((neg >> prod) & 1u) ? idesc_neg : idesc;
             const uint32_t d = to_re ? d_re : d_im;
             uint32_t& acc = to_re ? acc_re : acc_im;
-            const uint64_t a_hi = part_desc<false, GBK>(ta + (uint32_t)xa * G_A_TILE, 0);
-            const uint64_t b_hi = part_desc<true, GBK>(tb + (uint32_t)yb * G_B_TILE, 0);
+            const uint64_t a_hi = da + (uint64_t)((uint32_t)xa * G_A_TILE >> 4);
+            const uint64_t b_hi = db + (uint64_t)((uint32_t)yb * G_B_TILE >> 4);
             mma_bf16(d, a_hi, b_hi, id, acc);
             acc = 1;
             if (NP == 4) {
-              const uint64_t a_lo = part_desc<false, GBK>(ta + (uint32_t)(xa + 1) * G_A_TILE, 0);
-              const uint64_t b_lo = part_desc<true, GBK>(tb + (uint32_t)(yb + 1) * G_B_TILE, 0);
+              const uint64_t a_lo = a_hi + (uint64_t)(G_A_TILE >> 4);
+              const uint64_t b_lo = b_hi + (uint64_t)(G_B_TILE >> 4);
               mma_bf16(d, a_hi, b_lo, id, 1);
               mma_bf16(d, a_lo, b_hi, id, 1);
             }
@@ -233,6 +252,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    float2* stg = reinterpret_cast<float2*>(smem_raw + (stg_base - smem_u32(smem_raw)) + q * kStgBytes);
     int lt = 0, cur = 0;
     for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
       const GTile T = decode_tile(probs, nprobs, t, cur);
@@ -247,7 +267,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         break;
       }
       fence_after();
-      const int row = T.mt * GBM + q * 32 + lane;
+      const int row0 = T.mt * GBM + q * 32;
       const int bn = P.bn;
       float2* out = reinterpret_cast<float2*>(ws + P.out_off) + (long long)T.h * P.p * P.M * P.N +
                     (long long)T.f * P.M * P.N;
@@ -257,13 +277,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
         uint32_t re[32], im[32];
         tmem_ld32(tb + (uint32_t)c0, re);
         tmem_ld32(tb + (uint32_t)(GBN + c0), im);
-        if (row < P.M) {
-          float2* o = out + (long long)row * P.N;
-          const int col0 = T.nt * bn + c0;
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col0 + j < P.N) o[col0 + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
-        }
+        const int col0 = T.nt * bn + c0;
+        store_chunk(stg, re, im, out + (long long)row0 * P.N + col0, P.N, P.M - row0, P.N - col0, lane);
       }
       fence_before();
       __syncwarp();
@@ -331,27 +346,28 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
                                    char* ws, int* d_err, int num_ctas, cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;
   const int np = nparts == 4 ? 4 : 2;
-  const size_t smem = (size_t)GSTAGES * np * (G_A_TILE + G_B_TILE) + 1024 + 256;
+  const size_t smem = (size_t)GSTAGES * np * (G_A_TILE + G_B_TILE) + 4 * kStgBytes + 1024 + 256;
   const int grid = (int)(total_tiles < num_ctas ? total_tiles : num_ctas);
   // Forward product (Thm 5.1): C1 = A1 B1 - A2 conj(B2(-f)), C2 = A1 B2 + A2 conj(B1(-f)).
   // (tau ar + i tau ai)(br + i sb bi): re += tau ar.br - tau sb ai.bi, im += tau sb ar.bi + tau ai.br
-  GViews V;
+  GViews V = {0u, 0u, 0u, 0u};
   const int a_plane[2][2] = {{0, 1}, {0, 1}};
   const int b_plane[2][2] = {{0, 1}, {1, 0}};
   const int b_conj[2][2] = {{0, 1}, {0, 1}};
   const float sign[2][2] = {{1.f, -1.f}, {1.f, 1.f}};
   for (int h = 0; h < 2; ++h)
     for (int kh = 0; kh < 2; ++kh) {
-      V.a_plane[h][kh] = a_plane[h][kh];
-      V.b_plane[h][kh] = b_plane[h][kh];
-      V.b_fneg[h][kh] = b_conj[h][kh];  // the conjugated B operand is the one read at -f
+      const int e = 2 * h + kh;
+      V.a_plane |= (uint32_t)a_plane[h][kh] << e;
+      V.b_plane |= (uint32_t)b_plane[h][kh] << e;
+      V.b_fneg |= (uint32_t)b_conj[h][kh] << e;  // the conjugated B operand is the one read at -f
       const float tau = sign[h][kh];
       const float sb = b_conj[h][kh] ? -1.f : 1.f;
       const float c[4] = {tau, -tau * sb, tau * sb, tau};
       uint32_t mask = 0;
       for (int q = 0; q < 4; ++q)
         if (c[q] < 0) mask |= 1u << q;
-      V.negmask[h][kh] = mask;
+      V.negmask |= mask << (4 * e);
     }
   cudaError_t e;
   if (np == 4) {

@@ -195,6 +195,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       int nw = args.N - nt * BN;
       nw = nw > BN ? BN : ((nw + 15) & ~15);
       const uint32_t idesc = make_idesc(A_MN, B_MN, nw);
+      const uint32_t idesc_neg = idesc | kNegA;
+      const uint64_t da0 = part_desc<A_MN, BK>(S.a, 0);
+      const uint64_t db0 = part_desc<B_MN, BK>(S.b, 0);
       const uint32_t d_re = tmem;
       const uint32_t d_im = tmem + (uint32_t)BN;
       const uint32_t c_re = SPLIT ? tmem + 2u * BN : d_re;  // correction accumulators
@@ -213,29 +216,33 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         }
         fence_after();
         const uint32_t neg = args.negmask[h][kh];
-        const uint32_t ta = S.a + (uint32_t)(s * NP) * A_TILE;
-        const uint32_t tb = S.b + (uint32_t)(s * NP) * B_TILE;
+        // descriptors of this stage's part tiles: the base descriptor advanced by
+        // (byte offset >> 4) in its start-address field (no carry: smem < 256 KB)
+        const uint64_t da = da0 + (uint64_t)((uint32_t)(s * NP * A_TILE) >> 4);
+        const uint64_t db = db0 + (uint64_t)((uint32_t)(s * NP * B_TILE) >> 4);
 #pragma unroll
         for (int k16 = 0; k16 < BK / 16; ++k16) {
           // part tiles: NP == 4: re_hi, re_lo, im_hi, im_lo; NP == 2: re, im
           const int RE = 0, IM = NP / 2;
+          const uint32_t ka = (uint32_t)k16 * (A_MN ? 2048u : 32u) >> 4;
+          const uint32_t kb = (uint32_t)k16 * (B_MN ? 2048u : 32u) >> 4;
 #pragma unroll
           for (int prod = 0; prod < 4; ++prod) {
             const int xa = (prod == 0 || prod == 2) ? RE : IM;  // ar, ai, ar, ai
             const int yb = (prod == 0 || prod == 3) ? RE : IM;  // br, bi, bi, br
             const bool to_re = prod < 2;
-            const uint32_t id = idesc | (((neg >> prod) & 1u) ? kNegA : 0u);
+            const uint32_t id = ((neg >> prod) & 1u) ? idesc_neg : idesc;
             const uint32_t d = to_re ? d_re : d_im;
             const uint32_t dc = to_re ? c_re : c_im;
             uint32_t& acc = to_re ? acc_re : acc_im;
             uint32_t& accc = SPLIT ? (to_re ? acc_cre : acc_cim) : acc;
-            const uint64_t a_hi = part_desc<A_MN, BK>(ta + (uint32_t)xa * A_TILE, k16);
-            const uint64_t b_hi = part_desc<B_MN, BK>(tb + (uint32_t)yb * B_TILE, k16);
+            const uint64_t a_hi = da + (uint64_t)(((uint32_t)xa * A_TILE >> 4) + ka);
+            const uint64_t b_hi = db + (uint64_t)(((uint32_t)yb * B_TILE >> 4) + kb);
             mma_bf16(d, a_hi, b_hi, id, acc);
             acc = 1;
             if (NP == 4) {
-              const uint64_t a_lo = part_desc<A_MN, BK>(ta + (uint32_t)(xa + 1) * A_TILE, k16);
-              const uint64_t b_lo = part_desc<B_MN, BK>(tb + (uint32_t)(yb + 1) * B_TILE, k16);
+              const uint64_t a_lo = a_hi + (uint64_t)(A_TILE >> 4);
+              const uint64_t b_lo = b_hi + (uint64_t)(B_TILE >> 4);
               mma_bf16(dc, a_hi, b_lo, id, accc);
               accc = 1;
               mma_bf16(dc, a_lo, b_hi, id, 1);
@@ -255,7 +262,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   } else {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int row = mt * BM + q * 32 + lane;
     bool ok = mbar_wait(S.acc_full, 0);
     if (!ok) {
       if (lane == 0) {
@@ -264,8 +270,15 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       }
     } else {
       fence_after();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // ring: async-proxy use -> generic writes
       float2* out = args.out + (long long)h * args.out_hstride + (long long)f * args.out_fstride;
       const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+      // The operand ring is idle once the accumulators are final (every TMA
+      // load was consumed and every MMA has completed): it holds the staging
+      // areas of the four epilogue warps.
+      static_assert(STAGES * NP * (A_TILE + B_TILE) >= 4 * kStgBytes, "staging areas must fit in the operand ring");
+      float2* stg = reinterpret_cast<float2*>(smem_raw + (S.a - raw) + q * kStgBytes);
+      const int row0 = mt * BM + q * 32;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t re[32], im[32];
@@ -281,14 +294,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             im[j] = __float_as_uint(__uint_as_float(im[j]) + __uint_as_float(cim[j]));
           }
         }
-        if (row < args.M) {
-          float2* o = out + (long long)row * args.out_rstride;
-          const int col0 = nt * BN + c0;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (col0 + j < args.N) o[col0 + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
-          }
-        }
+        const int col0 = nt * BN + c0;
+        store_chunk(stg, re, im, out + (long long)row0 * args.out_rstride + col0, args.out_rstride, args.M - row0,
+                    args.N - col0, lane);
       }
     }
     fence_before();

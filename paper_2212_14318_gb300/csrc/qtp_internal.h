@@ -68,12 +68,15 @@ struct FftGroupJob {
   RadixPlan rp;           // for tube lengths without a compile-time kernel
 };
 
-cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks, int fmt,
-                                   const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
-                                   cudaStream_t st);
-cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long nblocks,
-                                   const float2* const* d_ptrs, char* ws, const float2* d_tw, size_t smem,
-                                   cudaStream_t st);
+// One launch over global CTAs [block0, block0 + nblocks), all of whose jobs
+// have tube length p (any p without a compile-time kernel may share a range,
+// with smem the largest of theirs).
+cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long block0,
+                                   long long nblocks, int p, int fmt, const float2* const* d_ptrs, char* ws,
+                                   const float2* d_tw, size_t smem, cudaStream_t st);
+cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_of_block, long long block0,
+                                   long long nblocks, int p, const float2* const* d_ptrs, char* ws,
+                                   const float2* d_tw, size_t smem, cudaStream_t st);
 size_t fft_fixed_smem(int p, bool inv);
 
 // Compile-time specialisations (qtp_fft_fixed.cu) for the common tube lengths:

@@ -140,5 +140,35 @@ __device__ __forceinline__ void tensormap_acquire(const void* tm) {
                : "memory");
 }
 
+// Epilogue store of one warp's 32 x 32 complex chunk of an accumulator tile.
+// tcgen05.ld 32x32b hands lane l row l (re[j], im[j] = column j); storing that
+// directly would put the 32 lanes of every store on 32 different rows.  The
+// chunk is instead transposed through this warp's staging area stg, 16
+// columns at a time (32 rows of kStgPitch float2; the odd pitch keeps both
+// phases free of bank conflicts), and written with lane = column: each store
+// covers 128 contiguous bytes of two rows.  out points at (row0, col0) of a
+// row-major matrix with row stride ld (float2); rows_valid / cols_valid clip
+// the chunk at the matrix edge.
+constexpr int kStgPitch = 17;
+constexpr int kStgBytes = 32 * kStgPitch * 8;  // per epilogue warp
+
+__device__ __forceinline__ void store_chunk(float2* stg, const uint32_t (&re)[32], const uint32_t (&im)[32],
+                                            float2* out, long long ld, int rows_valid, int cols_valid, int lane) {
+  const int nr = rows_valid < 32 ? rows_valid : 32;
+  const int c = lane & 15, rr = lane >> 4;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      stg[lane * kStgPitch + j] = make_float2(__uint_as_float(re[16 * half + j]), __uint_as_float(im[16 * half + j]));
+    __syncwarp();
+    if (16 * half + c < cols_valid) {
+#pragma unroll 4
+      for (int r = rr; r < nr; r += 2) out[(long long)r * ld + 16 * half + c] = stg[r * kStgPitch + c];
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace tcdev
 }  // namespace qtp
