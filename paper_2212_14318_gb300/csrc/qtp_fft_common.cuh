@@ -79,51 +79,76 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
-// Length-R DFT in registers, R odd: X[u] = sum_r x_r w^(r u), w = e^(-2 pi i/R)
-// (conjugate for the inverse).  Pairing r with R - r,
+// Length-R DFT in registers: X[u] = sum_r x_r w^(r u), w = e^(-2 pi i/R)
+// (conjugate for the inverse), with every root of unity a compile-time
+// constant.  R = 2, 4, 8 have their own specialisations below.
+//
+// R odd: pairing r with R - r,
 //   X[u]     = A_u - i B_u,   X[R - u] = A_u + i B_u   (forward; signs of B
 //   swap for the inverse), A_u = x_0 + sum_r (x_r + x_{R-r}) cos(2 pi r u / R),
 //   B_u = sum_r (x_r - x_{R-r}) sin(2 pi r u / R),  r = 1 .. (R-1)/2,
-// a quarter of the multiplies of the plain sum, with the cosines and sines as
-// immediate constants.
+// a quarter of the multiplies of the plain sum.
+// R even: even/odd split, X[u] = E[u] + w^u O[u], X[u + R/2] = E[u] - w^u O[u]
+// with E, O the length-R/2 DFTs of the even and odd samples.
 template <int R, bool INV>
 struct Dft {
-  static_assert(R % 2 == 1 && R >= 3, "odd radix");
-  __device__ __forceinline__ static void run(float2 (&v)[R], const float2*, int) {
-    constexpr int H = (R - 1) / 2;
-    float2 sp[H], dm[H];
-    const float2 x0 = v[0];
-    float2 dc = x0;
+  static_assert(R >= 3, "radix");
+  __device__ __forceinline__ static void run(float2 (&v)[R], const float2* tw = nullptr, int p = 0) {
+    if constexpr (R % 2 == 1) {
+      constexpr int H = (R - 1) / 2;
+      float2 sp[H], dm[H];
+      const float2 x0 = v[0];
+      float2 dc = x0;
 #pragma unroll
-    for (int r = 1; r <= H; ++r) {
-      sp[r - 1] = cadd(v[r], v[R - r]);
-      dm[r - 1] = csub(v[r], v[R - r]);
-      dc = cadd(dc, sp[r - 1]);
-    }
-    v[0] = dc;
-    static_for<1, H + 1>([&](auto uc) {
-      constexpr int u = decltype(uc)::value;
-      float2 a = x0, bsum = make_float2(0.f, 0.f);
-      static_for<1, H + 1>([&](auto rc) {
-        constexpr int r = decltype(rc)::value;
-        constexpr float c = (float)cos_turn(r * u, R);
-        constexpr float sn = (float)sin_turn(r * u, R);
-        a.x = fmaf(sp[r - 1].x, c, a.x);
-        a.y = fmaf(sp[r - 1].y, c, a.y);
-        bsum.x = fmaf(dm[r - 1].x, sn, bsum.x);
-        bsum.y = fmaf(dm[r - 1].y, sn, bsum.y);
+      for (int r = 1; r <= H; ++r) {
+        sp[r - 1] = cadd(v[r], v[R - r]);
+        dm[r - 1] = csub(v[r], v[R - r]);
+        dc = cadd(dc, sp[r - 1]);
+      }
+      v[0] = dc;
+      static_for<1, H + 1>([&](auto uc) {
+        constexpr int u = decltype(uc)::value;
+        float2 a = x0, bsum = make_float2(0.f, 0.f);
+        static_for<1, H + 1>([&](auto rc) {
+          constexpr int r = decltype(rc)::value;
+          constexpr float c = (float)cos_turn(r * u, R);
+          constexpr float sn = (float)sin_turn(r * u, R);
+          a.x = fmaf(sp[r - 1].x, c, a.x);
+          a.y = fmaf(sp[r - 1].y, c, a.y);
+          bsum.x = fmaf(dm[r - 1].x, sn, bsum.x);
+          bsum.y = fmaf(dm[r - 1].y, sn, bsum.y);
+        });
+        // -i B = (B.y, -B.x)
+        const float2 mib = make_float2(bsum.y, -bsum.x);
+        v[u] = INV ? csub(a, mib) : cadd(a, mib);
+        v[R - u] = INV ? cadd(a, mib) : csub(a, mib);
       });
-      // -i B = (B.y, -B.x)
-      const float2 mib = make_float2(bsum.y, -bsum.x);
-      v[u] = INV ? csub(a, mib) : cadd(a, mib);
-      v[R - u] = INV ? cadd(a, mib) : csub(a, mib);
-    });
+    } else {
+      constexpr int Q = R / 2;
+      float2 e[Q], o[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        e[i] = v[2 * i];
+        o[i] = v[2 * i + 1];
+      }
+      Dft<Q, INV>::run(e);
+      Dft<Q, INV>::run(o);
+      static_for<0, Q>([&](auto uc) {
+        constexpr int u = decltype(uc)::value;
+        constexpr float c = (float)cos_turn(u, R);
+        constexpr float sn = (float)sin_turn(u, R);
+        const float2 w = make_float2(c, INV ? sn : -sn);
+        const float2 t = u == 0 ? o[u] : cmul(o[u], w);
+        v[u] = cadd(e[u], t);
+        v[u + Q] = csub(e[u], t);
+      });
+    }
   }
 };
 
 template <bool INV>
 struct Dft<2, INV> {
-  __device__ __forceinline__ static void run(float2 (&v)[2], const float2*, int) {
+  __device__ __forceinline__ static void run(float2 (&v)[2], const float2* = nullptr, int = 0) {
     float2 a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
@@ -132,7 +157,7 @@ struct Dft<2, INV> {
 
 template <bool INV>
 struct Dft<4, INV> {
-  __device__ __forceinline__ static void run(float2 (&v)[4], const float2*, int) {
+  __device__ __forceinline__ static void run(float2 (&v)[4], const float2* = nullptr, int = 0) {
     dft4<INV>(v[0], v[1], v[2], v[3]);
   }
 };
@@ -140,13 +165,14 @@ struct Dft<4, INV> {
 template <bool INV>
 struct Dft<8, INV> {
   // Even/odd split: X[u] = E[u] + omega_8^u O[u], X[u+4] = E[u] - omega_8^u O[u].
-  __device__ __forceinline__ static void run(float2 (&v)[8], const float2* __restrict__ tw, int p) {
+  __device__ __forceinline__ static void run(float2 (&v)[8], const float2* = nullptr, int = 0) {
     float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
     float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
     dft4<INV>(e0, e1, e2, e3);
     dft4<INV>(o0, o1, o2, o3);
-    const float2 w1 = twid<INV>(tw, p / 8);
-    const float2 w3 = twid<INV>(tw, 3 * p / 8);
+    constexpr float h = (float)cos_turn(1, 8);  // sqrt(1/2)
+    const float2 w1 = make_float2(h, INV ? h : -h);
+    const float2 w3 = make_float2(-h, INV ? h : -h);
     o1 = cmul(o1, w1);
     o2 = mul_w4<INV>(o2);
     o3 = cmul(o3, w3);

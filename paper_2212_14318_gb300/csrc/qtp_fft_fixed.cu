@@ -36,26 +36,101 @@ __host__ __device__ constexpr Radices radices_of(int p) {
   return rl;
 }
 
-// Tubes per CTA: about QTP_FFT_ELEMS complex per buffer (2304: ~34 KB per CTA,
-// up to six resident CTAs per SM; measured faster than 4608), even so that tube
-// pairs never straddle a CTA, a multiple of 32 from 32 up.  The forward
-// transform keeps at least 32 tubes (its frequency-major store writes runs of
-// T tubes; shorter runs measured slower at p = 128); the inverse, whose stores
-// are contiguous tubes, takes the smaller count for occupancy.
+// Two-pass transforms (see fs_fwd_body) take p = R1 R2 with both factors in
+// registers; p without such a split runs the Stockham stages below.  The
+// forward p = 100 stays on the stages (its two-pass form measured slower).
+struct Split {
+  int r1, r2;
+};
+__host__ __device__ constexpr Split split_of(int p, bool inv) {
+  switch (p) {
+    case 8: return Split{4, 2};
+    case 12: return Split{4, 3};
+    case 16: return Split{4, 4};
+    case 32: return Split{8, 4};
+    case 64: return Split{8, 8};
+    case 100: return inv ? Split{10, 10} : Split{0, 0};
+    case 128: return Split{16, 8};
+    default: return Split{0, 0};
+  }
+}
+
+// Tubes per CTA: a power of two, at most kThreads, so that in the strided
+// loops over (frequency, tube) every thread keeps one tube (or tube pair) and
+// computes its address once.
+//   Two-pass: about 4096 complex per CTA (32 KB of exchange buffer), at least
+//   32 tubes (the frequency-major stores write runs of T tubes).
+//   Stockham: about QTP_FFT_ELEMS complex per buffer (2304: ~34 KB per CTA,
+//   up to six resident CTAs per SM; measured faster than 4608); the forward
+//   transform keeps at least 32 tubes, the inverse, whose stores are
+//   contiguous tubes, takes the smaller count for occupancy.
 #ifndef QTP_FFT_ELEMS
 #define QTP_FFT_ELEMS 2304
 #endif
+// Resident CTAs per SM the transform kernels are compiled for (caps their
+// registers at 65536 / (kThreads kMinBlocks) = 85): the two-pass forward is
+// latency-bound, and three resident CTAs beat the spill-free register count
+// (video forward 80 -> 66 us).
+#ifndef QTP_FFT_MINB
+#define QTP_FFT_MINB 3
+#endif
+constexpr int kMinBlocks = QTP_FFT_MINB;
+
 __host__ __device__ constexpr int tubes_for(int p, bool inv) {
-  int t = QTP_FFT_ELEMS / (p | 1);
-  if (t > 512) t = 512;
-  if (!inv && t < 32 && p <= 128) t = 32;
-  t = t >= 32 ? t / 32 * 32 : t / 2 * 2;
-  return t < 2 ? 2 : t;
+  int lim = 0;
+  if (split_of(p, inv).r1 != 0) {
+    lim = 4096 / p;
+    if (lim < 32) lim = 32;
+  } else {
+    lim = QTP_FFT_ELEMS / (p | 1);
+    if (!inv && lim < 32 && p <= 128) lim = 32;
+  }
+  if (lim > 256) lim = 256;
+  int t = 2;
+  while (2 * t <= lim) t *= 2;
+  return t;
+}
+
+// Row pitch (complex) of the two-pass exchange buffer: T plus the even pad
+// that minimises shared-memory bank conflicts of its scalar accesses, thread
+// idx touching row (idx % A) * S + const at column idx / A (A = R2, S = 1 for
+// the forward pass-1 writes; A = F2, S = F1 for the inverse pass-2 reads).
+// Cost: per half warp, the largest number of 8-byte accesses on one bank pair.
+__host__ __device__ constexpr int fs_conflicts(int A, int S, int tp) {
+  int total = 0;
+  for (int w = 0; w < 8; ++w)
+    for (int h = 0; h < 2; ++h) {
+      int cnt[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      int mx = 0;
+      for (int l = 0; l < 16; ++l) {
+        const int idx = 32 * w + 16 * h + l;
+        const int b = ((idx % A) * S * tp + idx / A) % 16;
+        ++cnt[b];
+        if (cnt[b] > mx) mx = cnt[b];
+      }
+      total += mx;
+    }
+  return total;
+}
+__host__ __device__ constexpr int fs_pitch(int p, bool inv) {
+  const Split sp = split_of(p, inv);
+  const int T = tubes_for(p, inv);
+  const int A = sp.r2, S = inv ? sp.r1 : 1;
+  int best = T, cost = fs_conflicts(A, S, T);
+  for (int pad = 2; pad < 32; pad += 2) {
+    const int c = fs_conflicts(A, S, T + pad);
+    if (c < cost) {
+      cost = c;
+      best = T + pad;
+    }
+  }
+  return best;
 }
 
 template <int P, bool INV>
 constexpr size_t smem_for() {
-  return (size_t)2 * tubes_for(P, INV) * (P | 1) * sizeof(float2) + (size_t)tubes_for(P, INV) * sizeof(long long);
+  if constexpr (split_of(P, INV).r1 != 0) return (size_t)P * fs_pitch(P, INV) * sizeof(float2);
+  return (size_t)2 * tubes_for(P, INV) * (P | 1) * sizeof(float2);
 }
 
 // Radix-R Stockham butterfly j of one tube, Ns = length already transformed.
@@ -185,16 +260,33 @@ __device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const
   }
 }
 
-// Forward transform of the b-th run of T = tubes_for(P) tubes of one tensor.
+// ---------------------------------------------------------------------------
+// Two-pass transforms for p = R1 R2 (Cooley-Tukey with a single exchange).
+// Forward, tube sample n = R2 n1 + n2, frequency f = k1 + R1 k2, w = w_p:
+//   X[k1 + R1 k2] = sum_n2 w_R2^(n2 k2) w^(n2 k1) sum_n1 x[R2 n1 + n2] w_R1^(n1 k1)
+//   pass 1: thread (tube, n2) loads its R1 samples from HBM, DFT-R1, twiddle
+//           w^(n2 k1), writes Y[k1][n2][tube] to shared memory;
+//   pass 2: thread (tube pair, k1) reads Y[k1][.][tube pair], DFT-R2, stores
+//           frequencies k1 + R1 k2 to the frequency-major spectra.
+// Inverse, f = f1 + F1 f2, n = n1 + F2 n2 (F1 = R1, F2 = R2), conjugate roots:
+//   x[n1 + F2 n2] = 1/p sum_f1 w_F1^(n2 f1) w^(n1 f1) sum_f2 X[f1 + F1 f2] w_F2^(n1 f2)
+//   pass 1: thread (tube pair, f1) gathers X[f1 + F1 f2], DFT-F2, twiddle,
+//           writes Z[n1][f1][tube pair];
+//   pass 2: thread (tube, n1) reads Z[n1][.][tube], DFT-F1, stores the
+//           samples n1 + F2 n2.
+// Every sample crosses shared memory once; both HBM sides are coalesced
+// (pass-1 loads / pass-2 stores of runs of R2 samples per tube; frequency-
+// major runs of T / 2 tube pairs).
+// ---------------------------------------------------------------------------
+
 template <int P, int FMT>
-__device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b, const float2* __restrict__ tw,
-                                               float2* smem) {
+__device__ __forceinline__ void fs_fwd_body(const FftFwdJob& job, long long b, const float2* __restrict__ tw,
+                                            float2* smem) {
+  constexpr int R1 = split_of(P, false).r1, R2 = split_of(P, false).r2;
   constexpr int T = tubes_for(P, false);
-  constexpr int PP = P | 1;
+  constexpr int TP = fs_pitch(P, false);
   constexpr int NPARTS = FMT == FMT_BF16X3 ? 4 : (FMT == FMT_BF16 ? 2 : 1);
-  float2* buf0 = smem;
-  float2* buf1 = buf0 + T * PP;
-  long long* tube_off = reinterpret_cast<long long*>(buf1 + T * PP);
+  static_assert(R1 * R2 == P && kThreads % T == 0, "two-pass split");
 
   const long long per_plane = (long long)job.rows * job.cols;
   const long long ntubes = 2 * per_plane;
@@ -202,47 +294,241 @@ __device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b
   if (t0 >= ntubes) return;
   const int Tb = (int)min((long long)T, ntubes - t0);
 
-  // contiguous load of the CTA's tubes
+  // pass 1
   const float2* src = job.in + t0 * P;
-  if constexpr (P % 2 == 0) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    for (int i = threadIdx.x; i < Tb * (P / 2); i += kThreads) {
-      const float4 v = __ldg(s4 + i);
-      const int tube = (2 * i) / P;
-      const int k = 2 * i - tube * P;
-      buf0[tube * PP + k] = make_float2(v.x, v.y);
-      buf0[tube * PP + k + 1] = make_float2(v.z, v.w);
-    }
-  } else {
-    for (int i = threadIdx.x; i < Tb * P; i += kThreads) {
-      const int tube = i / P;
-      buf0[tube * PP + (i - tube * P)] = __ldg(src + i);
+  for (int idx = threadIdx.x; idx < T * R2; idx += kThreads) {
+    const int n2 = idx % R2;
+    const int tube = idx / R2;
+    if (tube >= Tb) continue;
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(src + tube * P + R2 * n1 + n2);
+    Dft<R1, false>::run(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      const float2 y = (k1 == 0 || n2 == 0) ? v[k1] : cmul(v[k1], twid<false>(tw, n2 * k1));
+      smem[(k1 * R2 + n2) * TP + tube] = y;
     }
   }
+  __syncthreads();
+
+  // pass 2
   const long long ld = job.ld;
   const long long slab = (long long)job.rows * ld;  // one (plane, part, f) slab
-  for (int tube = threadIdx.x; tube < Tb; tube += kThreads) {
-    const long long t = t0 + tube;
+  const long long part = (long long)P * slab;
+  auto spec_off = [&](long long t) {  // [plane][part 0][f 0][row][col] of tube t
     const long long plane = t / per_plane;
     const long long rem = t - plane * per_plane;
     const long long row = rem / job.cols;
-    tube_off[tube] = plane * NPARTS * P * slab + row * ld + (rem - row * job.cols);
+    return plane * NPARTS * P * slab + row * ld + (rem - row * job.cols);
+  };
+  if ((job.cols & 1) == 0) {
+    // tube pairs share a row: 16-byte / 4-byte stores
+    constexpr int TH = T / 2;
+    const int tube = 2 * (threadIdx.x % TH);
+    if (tube >= Tb) return;
+    const long long o0 = spec_off(t0 + tube);
+    for (int k1 = threadIdx.x / TH; k1 < R1; k1 += kThreads / TH) {
+      float2 a[R2], c[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) {
+        const float4 y = *reinterpret_cast<const float4*>(smem + (k1 * R2 + n2) * TP + tube);
+        a[n2] = make_float2(y.x, y.y);
+        c[n2] = make_float2(y.z, y.w);
+      }
+      Dft<R2, false>::run(a);
+      Dft<R2, false>::run(c);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const long long o = o0 + (long long)(k1 + R1 * k2) * slab;
+        const float2 v0 = a[k2], v1 = c[k2];
+        if constexpr (FMT == FMT_C32) {
+          *reinterpret_cast<float4*>(reinterpret_cast<float2*>(job.out) + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        } else if constexpr (FMT == FMT_BF16X3) {
+          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
+          __nv_bfloat16 rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
+          split_bf16(v0.x, rh0, rl0);
+          split_bf16(v0.y, ih0, il0);
+          split_bf16(v1.x, rh1, rl1);
+          split_bf16(v1.y, ih1, il1);
+          *reinterpret_cast<__nv_bfloat162*>(out + o) = __halves2bfloat162(rh0, rh1);
+          *reinterpret_cast<__nv_bfloat162*>(out + o + part) = __halves2bfloat162(rl0, rl1);
+          *reinterpret_cast<__nv_bfloat162*>(out + o + 2 * part) = __halves2bfloat162(ih0, ih1);
+          *reinterpret_cast<__nv_bfloat162*>(out + o + 3 * part) = __halves2bfloat162(il0, il1);
+        } else {
+          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
+          *reinterpret_cast<__nv_bfloat162*>(out + o) =
+              __halves2bfloat162(__float2bfloat16_rn(v0.x), __float2bfloat16_rn(v1.x));
+          *reinterpret_cast<__nv_bfloat162*>(out + o + part) =
+              __halves2bfloat162(__float2bfloat16_rn(v0.y), __float2bfloat16_rn(v1.y));
+        }
+      }
+    }
+  } else {
+    const int tube = threadIdx.x % T;
+    if (tube >= Tb) return;
+    const long long o0 = spec_off(t0 + tube);
+    for (int k1 = threadIdx.x / T; k1 < R1; k1 += kThreads / T) {
+      float2 a[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) a[n2] = smem[(k1 * R2 + n2) * TP + tube];
+      Dft<R2, false>::run(a);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const long long o = o0 + (long long)(k1 + R1 * k2) * slab;
+        const float2 v = a[k2];
+        if constexpr (FMT == FMT_C32) {
+          reinterpret_cast<float2*>(job.out)[o] = v;
+        } else if constexpr (FMT == FMT_BF16X3) {
+          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
+          __nv_bfloat16 rh, rl, ih, il;
+          split_bf16(v.x, rh, rl);
+          split_bf16(v.y, ih, il);
+          out[o] = rh;
+          out[o + part] = rl;
+          out[o + 2 * part] = ih;
+          out[o + 3 * part] = il;
+        } else {
+          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(job.out);
+          out[o] = __float2bfloat16_rn(v.x);
+          out[o + part] = __float2bfloat16_rn(v.y);
+        }
+      }
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void fs_inv_body(const FftInvJob& job, long long b, const float2* __restrict__ tw,
+                                            float2* smem) {
+  constexpr int F1 = split_of(P, true).r1, F2 = split_of(P, true).r2;
+  constexpr int T = tubes_for(P, true);
+  constexpr int TP = fs_pitch(P, true);
+  static_assert(F1 * F2 == P && kThreads % T == 0, "two-pass split");
+
+  const long long per_plane = (long long)job.rows * job.cols;
+  const long long ntubes = 2 * per_plane;
+  const long long t0 = b * T;
+  if (t0 >= ntubes) return;
+  const int Tb = (int)min((long long)T, ntubes - t0);
+  auto spec_off = [&](long long t) {  // [plane][f 0][row][col] of tube t
+    const long long plane = t / per_plane;
+    return plane * P * per_plane + (t - plane * per_plane);
+  };
+
+  // pass 1
+  if ((job.cols & 1) == 0) {
+    constexpr int TH = T / 2;
+    const int tube = 2 * (threadIdx.x % TH);
+    if (tube < Tb) {
+      const float2* in = job.in + spec_off(t0 + tube);
+      for (int f1 = threadIdx.x / TH; f1 < F1; f1 += kThreads / TH) {
+        float2 a[F2], c[F2];
+#pragma unroll
+        for (int f2 = 0; f2 < F2; ++f2) {
+          const float4 x = __ldg(reinterpret_cast<const float4*>(in + (long long)(f1 + F1 * f2) * per_plane));
+          a[f2] = make_float2(x.x, x.y);
+          c[f2] = make_float2(x.z, x.w);
+        }
+        Dft<F2, true>::run(a);
+        Dft<F2, true>::run(c);
+#pragma unroll
+        for (int n1 = 0; n1 < F2; ++n1) {
+          float2 za = a[n1], zc = c[n1];
+          if (n1 > 0 && f1 > 0) {
+            const float2 w = twid<true>(tw, n1 * f1);
+            za = cmul(za, w);
+            zc = cmul(zc, w);
+          }
+          *reinterpret_cast<float4*>(smem + (n1 * F1 + f1) * TP + tube) = make_float4(za.x, za.y, zc.x, zc.y);
+        }
+      }
+    }
+  } else {
+    const int tube = threadIdx.x % T;
+    if (tube < Tb) {
+      const float2* in = job.in + spec_off(t0 + tube);
+      for (int f1 = threadIdx.x / T; f1 < F1; f1 += kThreads / T) {
+        float2 a[F2];
+#pragma unroll
+        for (int f2 = 0; f2 < F2; ++f2) a[f2] = __ldg(in + (long long)(f1 + F1 * f2) * per_plane);
+        Dft<F2, true>::run(a);
+#pragma unroll
+        for (int n1 = 0; n1 < F2; ++n1)
+          smem[(n1 * F1 + f1) * TP + tube] = (n1 > 0 && f1 > 0) ? cmul(a[n1], twid<true>(tw, n1 * f1)) : a[n1];
+      }
+    }
+  }
+  __syncthreads();
+
+  // pass 2
+  const float scale = 1.0f / (float)P;
+  float2* dst = job.out + t0 * P;
+  for (int idx = threadIdx.x; idx < T * F2; idx += kThreads) {
+    const int n1 = idx % F2;
+    const int tube = idx / F2;
+    if (tube >= Tb) continue;
+    float2 v[F1];
+#pragma unroll
+    for (int f1 = 0; f1 < F1; ++f1) v[f1] = smem[(n1 * F1 + f1) * TP + tube];
+    Dft<F1, true>::run(v);
+#pragma unroll
+    for (int n2 = 0; n2 < F1; ++n2) dst[tube * P + n1 + F2 * n2] = make_float2(v[n2].x * scale, v[n2].y * scale);
+  }
+}
+
+// Forward transform of the b-th run of T = tubes_for(P) tubes of one tensor.
+template <int P, int FMT>
+__device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b, const float2* __restrict__ tw,
+                                               float2* smem) {
+  if constexpr (split_of(P, false).r1 != 0) {
+    fs_fwd_body<P, FMT>(job, b, tw, smem);
+    return;
+  }
+  constexpr int T = tubes_for(P, false);
+  constexpr int PP = P | 1;
+  constexpr int NPARTS = FMT == FMT_BF16X3 ? 4 : (FMT == FMT_BF16 ? 2 : 1);
+  static_assert(kThreads % T == 0, "a thread keeps one tube in the store loops");
+  float2* buf0 = smem;
+  float2* buf1 = buf0 + T * PP;
+
+  const long long per_plane = (long long)job.rows * job.cols;
+  const long long ntubes = 2 * per_plane;
+  const long long t0 = b * T;
+  if (t0 >= ntubes) return;
+  const int Tb = (int)min((long long)T, ntubes - t0);
+
+  // contiguous load of the CTA's tubes; consecutive lanes write consecutive
+  // elements of a tube (conflict-free with the odd tube stride PP)
+  const float2* src = job.in + t0 * P;
+  for (int i = threadIdx.x; i < Tb * P; i += kThreads) {
+    const int tube = i / P;
+    buf0[tube * PP + (i - tube * P)] = __ldg(src + i);
   }
   __syncthreads();
   const float2* X = stages<P, 0, 1, false, false, true>(buf0, buf1, Tb, tw);  // frequency-major result
 
+  const long long ld = job.ld;
+  const long long slab = (long long)job.rows * ld;  // one (plane, part, f) slab
   const long long part = (long long)P * slab;
+  // spectra offset of tube t: [plane][part 0][f 0][row][col]
+  auto spec_off = [&](long long t) {
+    const long long plane = t / per_plane;
+    const long long rem = t - plane * per_plane;
+    const long long row = rem / job.cols;
+    return plane * NPARTS * P * slab + row * ld + (rem - row * job.cols);
+  };
   if ((job.cols & 1) == 0) {
     // pairs of neighbouring tubes share a row: 16-byte / 4-byte stores
     constexpr int TH = T / 2;
-    for (int i = threadIdx.x; i < TH * P; i += kThreads) {
-      const int f = i / TH;
-      const int tube = 2 * (i - f * TH);
-      if (tube >= Tb) continue;
+    const int tube = 2 * (threadIdx.x % TH);
+    if (tube >= Tb) return;
+    const long long o0 = spec_off(t0 + tube);
+    for (int f = threadIdx.x / TH; f < P; f += kThreads / TH) {
       const float4 v01 = *reinterpret_cast<const float4*>(X + f * T + tube);
       const float2 v0 = make_float2(v01.x, v01.y);
       const float2 v1 = make_float2(v01.z, v01.w);
-      const long long o = tube_off[tube] + (long long)f * slab;
+      const long long o = o0 + (long long)f * slab;
       if constexpr (FMT == FMT_C32) {
         *reinterpret_cast<float4*>(reinterpret_cast<float2*>(job.out) + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
       } else if constexpr (FMT == FMT_BF16X3) {
@@ -265,12 +551,12 @@ __device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b
       }
     }
   } else {
-    for (int i = threadIdx.x; i < T * P; i += kThreads) {
-      const int f = i / T;
-      const int tube = i - f * T;
-      if (tube >= Tb) continue;
+    const int tube = threadIdx.x % T;
+    if (tube >= Tb) return;
+    const long long o0 = spec_off(t0 + tube);
+    for (int f = threadIdx.x / T; f < P; f += kThreads / T) {
       const float2 v = X[f * T + tube];
-      const long long o = tube_off[tube] + (long long)f * slab;
+      const long long o = o0 + (long long)f * slab;
       if constexpr (FMT == FMT_C32) {
         reinterpret_cast<float2*>(job.out)[o] = v;
       } else if constexpr (FMT == FMT_BF16X3) {
@@ -295,11 +581,15 @@ __device__ __forceinline__ void fixed_fwd_body(const FftFwdJob& job, long long b
 template <int P>
 __device__ __forceinline__ void fixed_inv_body(const FftInvJob& job, long long b, const float2* __restrict__ tw,
                                                float2* smem) {
+  if constexpr (split_of(P, true).r1 != 0) {
+    fs_inv_body<P>(job, b, tw, smem);
+    return;
+  }
   constexpr int T = tubes_for(P, true);
   constexpr int PP = P | 1;
+  static_assert(kThreads % T == 0, "a thread keeps one tube in the gather loops");
   float2* buf0 = smem;
   float2* buf1 = buf0 + T * PP;
-  long long* tube_off = reinterpret_cast<long long*>(buf1 + T * PP);
 
   const long long per_plane = (long long)job.rows * job.cols;
   const long long ntubes = 2 * per_plane;
@@ -307,55 +597,42 @@ __device__ __forceinline__ void fixed_inv_body(const FftInvJob& job, long long b
   if (t0 >= ntubes) return;
   const int Tb = (int)min((long long)T, ntubes - t0);
 
-  for (int tube = threadIdx.x; tube < Tb; tube += kThreads) {
-    const long long t = t0 + tube;
-    const long long plane = t / per_plane;
-    tube_off[tube] = plane * P * per_plane + (t - plane * per_plane);
-  }
-  __syncthreads();
   // frequency-major gather of C_hat[plane][f][row][col]
+  auto spec_off = [&](long long t) {
+    const long long plane = t / per_plane;
+    return plane * P * per_plane + (t - plane * per_plane);
+  };
   if ((job.cols & 1) == 0) {
     constexpr int TH = T / 2;
-    for (int i = threadIdx.x; i < TH * P; i += kThreads) {
-      const int f = i / TH;
-      const int tube = 2 * (i - f * TH);
-      if (tube >= Tb) continue;
-      *reinterpret_cast<float4*>(buf0 + f * T + tube) =
-          __ldg(reinterpret_cast<const float4*>(job.in + tube_off[tube] + (long long)f * per_plane));
+    const int tube = 2 * (threadIdx.x % TH);
+    if (tube < Tb) {
+      const float2* in = job.in + spec_off(t0 + tube);
+      for (int f = threadIdx.x / TH; f < P; f += kThreads / TH)
+        *reinterpret_cast<float4*>(buf0 + f * T + tube) =
+            __ldg(reinterpret_cast<const float4*>(in + (long long)f * per_plane));
     }
   } else {
-    for (int i = threadIdx.x; i < T * P; i += kThreads) {
-      const int f = i / T;
-      const int tube = i - f * T;
-      if (tube >= Tb) continue;
-      buf0[f * T + tube] = __ldg(job.in + tube_off[tube] + (long long)f * per_plane);
+    const int tube = threadIdx.x % T;
+    if (tube < Tb) {
+      const float2* in = job.in + spec_off(t0 + tube);
+      for (int f = threadIdx.x / T; f < P; f += kThreads / T) buf0[f * T + tube] = __ldg(in + (long long)f * per_plane);
     }
   }
   __syncthreads();
   const float2* X = stages<P, 0, 1, true, true, false>(buf0, buf1, Tb, tw);  // frequency-major input
 
+  // contiguous store; consecutive lanes read consecutive elements of a tube
   const float scale = 1.0f / (float)P;
   float2* dst = job.out + t0 * P;
-  if constexpr (P % 2 == 0) {
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int i = threadIdx.x; i < Tb * (P / 2); i += kThreads) {
-      const int tube = (2 * i) / P;
-      const int k = 2 * i - tube * P;
-      const float2 a = X[tube * PP + k];
-      const float2 c = X[tube * PP + k + 1];
-      d4[i] = make_float4(a.x * scale, a.y * scale, c.x * scale, c.y * scale);
-    }
-  } else {
-    for (int i = threadIdx.x; i < Tb * P; i += kThreads) {
-      const int tube = i / P;
-      const float2 a = X[tube * PP + (i - tube * P)];
-      dst[i] = make_float2(a.x * scale, a.y * scale);
-    }
+  for (int i = threadIdx.x; i < Tb * P; i += kThreads) {
+    const int tube = i / P;
+    const float2 a = X[tube * PP + (i - tube * P)];
+    dst[i] = make_float2(a.x * scale, a.y * scale);
   }
 }
 
 template <int P, int FMT>
-__global__ void __launch_bounds__(kThreads) fft_fwd_fixed(FftFwdJob job0, FftFwdJob job1, int njobs,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_fixed(FftFwdJob job0, FftFwdJob job1, int njobs,
                                                           const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
   int b = blockIdx.x;
@@ -365,7 +642,7 @@ __global__ void __launch_bounds__(kThreads) fft_fwd_fixed(FftFwdJob job0, FftFwd
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
                                                           const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
   int b = blockIdx.x;
@@ -385,7 +662,7 @@ __global__ void __launch_bounds__(kThreads) fft_inv_fixed(FftInvJob job0, FftInv
 // ---------------------------------------------------------------------------
 
 template <int P, int FMT>
-__global__ void __launch_bounds__(kThreads) fft_fwd_grouped(const FftGroupJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_grouped(const FftGroupJob* __restrict__ jobs,
                                                             const int* __restrict__ job_of_block, long long block0,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
@@ -407,7 +684,7 @@ __global__ void __launch_bounds__(kThreads) fft_fwd_grouped(const FftGroupJob* _
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads) fft_inv_grouped(const FftGroupJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) fft_inv_grouped(const FftGroupJob* __restrict__ jobs,
                                                             const int* __restrict__ job_of_block, long long block0,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
