@@ -93,9 +93,9 @@ __host__ __device__ constexpr int tubes_for(int p, bool inv) {
 
 // Row pitch (complex) of the two-pass exchange buffer: T plus the even pad
 // that minimises shared-memory bank conflicts of its scalar accesses, thread
-// idx touching row (idx % A) * S + const at column idx / A (A = R2, S = 1 for
-// the forward pass-1 writes; A = F2, S = F1 for the inverse pass-2 reads).
-// Cost: per half warp, the largest number of 8-byte accesses on one bank pair.
+// idx touching row (idx % A) + const at column idx / A (A = R2: forward
+// pass-1 writes, inverse pass-2 reads).  Cost: per half warp, the largest
+// number of 8-byte accesses on one bank pair.
 __host__ __device__ constexpr int fs_conflicts(int A, int S, int tp) {
   int total = 0;
   for (int w = 0; w < 8; ++w)
@@ -115,7 +115,7 @@ __host__ __device__ constexpr int fs_conflicts(int A, int S, int tp) {
 __host__ __device__ constexpr int fs_pitch(int p, bool inv) {
   const Split sp = split_of(p, inv);
   const int T = tubes_for(p, inv);
-  const int A = sp.r2, S = inv ? sp.r1 : 1;
+  const int A = sp.r2, S = 1;
   int best = T, cost = fs_conflicts(A, S, T);
   for (int pad = 2; pad < 32; pad += 2) {
     const int c = fs_conflicts(A, S, T + pad);
@@ -271,8 +271,8 @@ __device__ __forceinline__ float2* stages(float2* in, float2* out, int Tb, const
 // Inverse, f = f1 + F1 f2, n = n1 + F2 n2 (F1 = R1, F2 = R2), conjugate roots:
 //   x[n1 + F2 n2] = 1/p sum_f1 w_F1^(n2 f1) w^(n1 f1) sum_f2 X[f1 + F1 f2] w_F2^(n1 f2)
 //   pass 1: thread (tube pair, f1) gathers X[f1 + F1 f2], DFT-F2, twiddle,
-//           writes Z[n1][f1][tube pair];
-//   pass 2: thread (tube, n1) reads Z[n1][.][tube], DFT-F1, stores the
+//           writes Z[f1][n1][tube pair];
+//   pass 2: thread (tube, n1) reads Z[.][n1][tube], DFT-F1, stores the
 //           samples n1 + F2 n2.
 // Every sample crosses shared memory once; both HBM sides are coalesced
 // (pass-1 loads / pass-2 stores of runs of R2 samples per tube; frequency-
@@ -294,19 +294,30 @@ __device__ __forceinline__ void fs_fwd_body(const FftFwdJob& job, long long b, c
   if (t0 >= ntubes) return;
   const int Tb = (int)min((long long)T, ntubes - t0);
 
-  // pass 1
+  // pass 1: every load of the thread's NI items is issued before the first
+  // DFT, to keep more bytes in flight
+  constexpr int NI = (T * R2 + kThreads - 1) / kThreads;
   const float2* src = job.in + t0 * P;
-  for (int idx = threadIdx.x; idx < T * R2; idx += kThreads) {
+  float2 v[NI][R1];
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    const int idx = threadIdx.x + it * kThreads;
+    const int tube = idx / R2;
+    if (idx < T * R2 && tube < Tb) {
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) v[it][n1] = __ldg(src + tube * P + R2 * n1 + idx % R2);
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    const int idx = threadIdx.x + it * kThreads;
     const int n2 = idx % R2;
     const int tube = idx / R2;
-    if (tube >= Tb) continue;
-    float2 v[R1];
-#pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(src + tube * P + R2 * n1 + n2);
-    Dft<R1, false>::run(v);
+    if (idx >= T * R2 || tube >= Tb) continue;
+    Dft<R1, false>::run(v[it]);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
-      const float2 y = (k1 == 0 || n2 == 0) ? v[k1] : cmul(v[k1], twid<false>(tw, n2 * k1));
+      const float2 y = (k1 == 0 || n2 == 0) ? v[it][k1] : cmul(v[it][k1], twid<false>(tw, n2 * k1));
       smem[(k1 * R2 + n2) * TP + tube] = y;
     }
   }
@@ -440,7 +451,7 @@ __device__ __forceinline__ void fs_inv_body(const FftInvJob& job, long long b, c
             za = cmul(za, w);
             zc = cmul(zc, w);
           }
-          *reinterpret_cast<float4*>(smem + (n1 * F1 + f1) * TP + tube) = make_float4(za.x, za.y, zc.x, zc.y);
+          *reinterpret_cast<float4*>(smem + (f1 * F2 + n1) * TP + tube) = make_float4(za.x, za.y, zc.x, zc.y);
         }
       }
     }
@@ -455,7 +466,7 @@ __device__ __forceinline__ void fs_inv_body(const FftInvJob& job, long long b, c
         Dft<F2, true>::run(a);
 #pragma unroll
         for (int n1 = 0; n1 < F2; ++n1)
-          smem[(n1 * F1 + f1) * TP + tube] = (n1 > 0 && f1 > 0) ? cmul(a[n1], twid<true>(tw, n1 * f1)) : a[n1];
+          smem[(f1 * F2 + n1) * TP + tube] = (n1 > 0 && f1 > 0) ? cmul(a[n1], twid<true>(tw, n1 * f1)) : a[n1];
       }
     }
   }
@@ -470,7 +481,7 @@ __device__ __forceinline__ void fs_inv_body(const FftInvJob& job, long long b, c
     if (tube >= Tb) continue;
     float2 v[F1];
 #pragma unroll
-    for (int f1 = 0; f1 < F1; ++f1) v[f1] = smem[(n1 * F1 + f1) * TP + tube];
+    for (int f1 = 0; f1 < F1; ++f1) v[f1] = smem[(f1 * F2 + n1) * TP + tube];
     Dft<F1, true>::run(v);
 #pragma unroll
     for (int n2 = 0; n2 < F1; ++n2) dst[tube * P + n1 + F2 * n2] = make_float2(v[n2].x * scale, v[n2].y * scale);
