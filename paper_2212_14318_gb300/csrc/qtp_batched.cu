@@ -262,13 +262,20 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
     P.N = q.s;
     P.K = q.n;
     P.p = q.p;
-    // tile width: 64 columns when that covers s in one tile (half the MMA work
-    // over padding at the same tile count), else 128 (more, narrower tiles
-    // measured slower: per-tile cost dominates)
-    const int bn = tc && q.s <= 64 ? 64 : BNt;
-    P.bn = bn;
-    P.tiles_m = (q.m + BMt - 1) / BMt;
-    P.tiles_n = (q.s + bn - 1) / bn;
+    // Tensor cores: 128-row tiles, MMA width the tile's columns rounded up to
+    // 16; computing C^T = B^T A^T instead when that pads less (the larger of
+    // m and s then fills the 128 rows).
+    P.bn = BNt;
+    P.trans = 0;
+    if (tc) {
+      auto padded = [](long long rows, long long cols) {
+        return (rows + 127) / 128 * 128 * ((cols + 15) / 16 * 16);
+      };
+      P.trans = padded(q.s, q.m) < padded(q.m, q.s) ? 1 : 0;
+    }
+    const int trows = P.trans ? q.s : q.m, tcols = P.trans ? q.m : q.s;
+    P.tiles_m = (trows + BMt - 1) / BMt;
+    P.tiles_n = (tcols + BNt - 1) / BNt;
     P.lda = (int)spec_ld_of(fmt, q.n);
     P.ldb = (int)spec_ld_of(fmt, q.s);
     tiles += (long long)P.tiles_m * P.tiles_n * 2 * q.p;

@@ -3,9 +3,14 @@
 //
 // All tiles of all products form one index space; product g owns
 // [tile_begin_g, tile_begin_g + tiles_m * tiles_n * 2 * p_g), ordered
-// (frequency, output half, row tile, column tile).  Each product has its own
-// tile width (64 or 128 complex columns, the MMA's N): narrow products do not
-// pay for 128-wide MMAs over padding.  CTA i (one per SM) takes
+// (frequency, output half, row tile, column tile).  A tile is 128 rows by up
+// to 128 columns; its MMA width is the tile's valid columns rounded up to 16,
+// so narrow products do not pay for MMAs over padding.  A product with
+// trans set is computed as C^T = B^T A^T, rows over s and columns over m: the
+// larger of m and s fills the MMA's 128 rows (B's MN-major spectra are then
+// the MN-major A operand and A's K-major spectra the K-major B operand; the
+// epilogue writes C^T's rows, which are C's contiguous columns).  CTA i (one
+// per SM) takes
 // tiles i, i + grid, i + 2 grid, ...  Roles as in the single-product kernel:
 // warp 0 issues TMA, warp 1 issues tcgen05.mma, warps 2-5 drain TMEM.  Here
 // the TMA producer runs straight on from one tile's K loop into the next
@@ -33,16 +38,19 @@ constexpr int GBK = 16;                  // K per stage
 constexpr int GSTAGES = 6;
 constexpr int G_A_TILE = GBM * GBK * 2;  // 4 KB per bf16 part
 constexpr int G_B_TILE = GBK * GBN * 2;  // 4 KB per bf16 part
+static_assert(G_A_TILE == G_B_TILE, "either tile region holds either operand");
 constexpr int kGThreads = 192;
 constexpr uint32_t G_TMEM_COLS = 512;    // 2 buffers x (re, im) x 128 columns
 
 // Operand roles of the forward product per (output half h, K half kh): A and B
 // planes, whether B is read at frequency -f, and which of the four real
-// products (ar.br, ai.bi, ar.bi, ai.br) is subtracted.  Filled on the host;
-// entry e = 2 h + kh sits in bit e (planes, fneg) or bits 4e..4e+3 (negmask),
-// so the kernel reads registers, not an indexed copy in local memory.
+// MMA products (a_re.b_re, a_im.b_im, a_re.b_im, a_im.b_re, with a and b the
+// MMA's operands) is subtracted, for the plain (negmask) and the transposed
+// (negmask_t) orientation.  Filled on the host; entry e = 2 h + kh sits in bit
+// e (planes, fneg) or bits 4e..4e+3 (masks), so the kernel reads registers,
+// not an indexed copy in local memory.
 struct GViews {
-  uint32_t a_plane, b_plane, b_fneg, negmask;
+  uint32_t a_plane, b_plane, b_fneg, negmask, negmask_t;
 };
 __device__ __forceinline__ uint32_t gv_bit(uint32_t bits, int h, int kh) { return (bits >> (2 * h + kh)) & 1u; }
 
@@ -140,6 +148,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
           }
         }
         const int nkb = (P.K + GBK - 1) / GBK;
+        // MMA width of this tile, and the 64-column boxes of the MN-major operand
+        const int ncols = P.trans ? P.M : P.N;
+        const int nw = min(GBN, ncols - T.nt * GBN);
+        const int nb64 = P.trans ? 2 : (nw + 63) / 64;
+        const uint32_t tx_bytes = (uint32_t)(NP * (G_A_TILE + (P.trans ? G_B_TILE : nb64 * (G_B_TILE / 2))));
         for (int kk = 0; kk < 2 * nkb; ++kk, ++it) {
           const int kh = kk / nkb;
           const int k0 = (kk - kh * nkb) * GBK;
@@ -155,18 +168,22 @@ __global__ void __launch_bounds__(kGThreads, 1)
             ok = false;
             break;
           }
-          const int nb64 = P.bn / 64;  // 64-column boxes of B in this product's tiles
-          mbar_expect_tx(full + 8 * s, (uint32_t)(NP * (G_A_TILE + nb64 * (G_B_TILE / 2))));
+          mbar_expect_tx(full + 8 * s, tx_bytes);
           const int ga = T.f;
           const int gb = gv_bit(V.b_fneg, T.h, kh) ? (P.p - T.f) % P.p : T.f;
           const int pa = (int)gv_bit(V.a_plane, T.h, kh) * NP, pb = (int)gv_bit(V.b_plane, T.h, kh) * NP;
+          // A's spectra (K-major rows of m) and B's (MN-major columns of s)
+          // go to the MMA's A and B tiles, or the other way round when trans
+          const uint32_t tk = P.trans ? sB : sA;   // K-major tile: 128 rows of m
+          const uint32_t tm = P.trans ? sA : sB;   // MN-major tile: 64-column boxes of s
+          const int rowA = (P.trans ? T.nt : T.mt) * GBM;
+          const int colB = (P.trans ? T.mt : T.nt) * GBN;
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
-            const uint32_t ta = sA + (uint32_t)(s * NP + q) * G_A_TILE;
-            const uint32_t tb = sB + (uint32_t)(s * NP + q) * G_B_TILE;
-            tma_load_4d(ta, tmA, full + 8 * s, k0, T.mt * GBM, ga, pa + q);
-            tma_load_4d(tb, tmB, full + 8 * s, T.nt * P.bn, k0, gb, pb + q);
-            if (nb64 == 2) tma_load_4d(tb + 128u * GBK, tmB, full + 8 * s, T.nt * P.bn + 64, k0, gb, pb + q);
+            const uint32_t off = (uint32_t)(s * NP + q) * G_A_TILE;  // G_A_TILE == G_B_TILE
+            tma_load_4d(tk + off, tmA, full + 8 * s, k0, rowA, ga, pa + q);
+            tma_load_4d(tm + off, tmB, full + 8 * s, colB, k0, gb, pb + q);
+            if (nb64 == 2) tma_load_4d(tm + off + 128u * GBK, tmB, full + 8 * s, colB + 64, k0, gb, pb + q);
           }
         }
       }
@@ -178,18 +195,23 @@ __global__ void __launch_bounds__(kGThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc128 = make_idesc(false, true, 128);
-      const uint32_t idesc64 = make_idesc(false, true, 64);
-      const uint64_t da0 = part_desc<false, GBK>(sA, 0);
-      const uint64_t db0 = part_desc<true, GBK>(sB, 0);
+      // base descriptors of the A / B tiles in either orientation
+      const uint64_t da0_k = part_desc<false, GBK>(sA, 0), da0_mn = part_desc<true, GBK>(sA, 0);
+      const uint64_t db0_k = part_desc<false, GBK>(sB, 0), db0_mn = part_desc<true, GBK>(sB, 0);
       long long it = 0;
       int lt = 0, cur = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++lt) {
         const GTile T = decode_tile(probs, nprobs, t, cur);
-        const int K = probs[T.g].K;
-        const uint32_t idesc = probs[T.g].bn == 64 ? idesc64 : idesc128;
-        const uint32_t idesc_neg = idesc | kNegA;
+        const GroupProblem& P = probs[T.g];
+        const int K = P.K;
+        const bool tr = P.trans != 0;
+        const int ncols = tr ? P.M : P.N;
+        const int nw = (min(GBN, ncols - T.nt * GBN) + 15) & ~15;
+        const uint32_t idesc = make_idesc(tr, !tr, nw);
+        const uint64_t da0 = tr ? da0_mn : da0_k;
+        const uint64_t db0 = tr ? db0_k : db0_mn;
+        const uint32_t nmask = tr ? V.negmask_t : V.negmask;
         const int nkb = (K + GBK - 1) / GBK;
         const int buf = lt & 1;
         const uint32_t uph = (uint32_t)(lt >> 1) & 1u;
@@ -214,30 +236,12 @@ __global__ void __launch_bounds__(kGThreads, 1)
             break;
           }
           fence_after();
-          const uint32_t neg = V.negmask >> (4 * (2 * T.h + kh));
+          const uint32_t neg = nmask >> (4 * (2 * T.h + kh));
           // stage descriptors: base descriptor advanced in its start-address field
           const uint64_t da = da0 + (uint64_t)((uint32_t)(s * NP * G_A_TILE) >> 4);
           const uint64_t db = db0 + (uint64_t)((uint32_t)(s * NP * G_B_TILE) >> 4);
-          const int RE = 0, IM = NP / 2;
-#pragma unroll
-          for (int prod = 0; prod < 4; ++prod) {
-            const int xa = (prod == 0 || prod == 2) ? RE : IM;
-            const int yb = (prod == 0 || prod == 3) ? RE : IM;
-            const bool to_re = prod < 2;
-            const uint32_t id = ((neg >> prod) & 1u) ? idesc_neg : idesc;
-            const uint32_t d = to_re ? d_re : d_im;
-            uint32_t& acc = to_re ? acc_re : acc_im;
-            const uint64_t a_hi = da + (uint64_t)((uint32_t)xa * G_A_TILE >> 4);
-            const uint64_t b_hi = db + (uint64_t)((uint32_t)yb * G_B_TILE >> 4);
-            mma_bf16(d, a_hi, b_hi, id, acc);
-            acc = 1;
-            if (NP == 4) {
-              const uint64_t a_lo = a_hi + (uint64_t)(G_A_TILE >> 4);
-              const uint64_t b_lo = b_hi + (uint64_t)(G_B_TILE >> 4);
-              mma_bf16(d, a_hi, b_lo, id, 1);
-              mma_bf16(d, a_lo, b_hi, id, 1);
-            }
-          }
+          complex_kstep<NP, false>(da, db, (uint32_t)(G_A_TILE >> 4), (uint32_t)(G_B_TILE >> 4), idesc, neg, d_re,
+                                   d_im, d_re, d_im, acc_re, acc_im, acc_re, acc_im);
           mma_commit(empty + 8 * s);
         }
         if (!ok) break;
@@ -267,18 +271,31 @@ __global__ void __launch_bounds__(kGThreads, 1)
         break;
       }
       fence_after();
-      const int row0 = T.mt * GBM + q * 32;
-      const int bn = P.bn;
       float2* out = reinterpret_cast<float2*>(ws + P.out_off) + (long long)T.h * P.p * P.M * P.N +
                     (long long)T.f * P.M * P.N;
       const uint32_t tb = tmem + (uint32_t)(buf * 2 * GBN) + lane_off;
+      const int row0 = T.mt * GBM + q * 32;  // this warp's first accumulator row
+      const int ncols = P.trans ? P.M : P.N;
+      const int nw = min(GBN, ncols - T.nt * GBN);
 #pragma unroll 1
-      for (int c0 = 0; c0 < bn; c0 += 32) {
+      for (int c0 = 0; c0 < nw; c0 += 32) {
         uint32_t re[32], im[32];
         tmem_ld32(tb + (uint32_t)c0, re);
         tmem_ld32(tb + (uint32_t)(GBN + c0), im);
-        const int col0 = T.nt * bn + c0;
-        store_chunk(stg, re, im, out + (long long)row0 * P.N + col0, P.N, P.M - row0, P.N - col0, lane);
+        const int col0 = T.nt * GBN + c0;
+        if (P.trans) {
+          // accumulator row = column of C (index into s), column = row of C
+          // (index into m): lane-consecutive stores along C's rows
+          const int cs = row0 + lane;
+          if (cs < P.N) {
+            const int nj = min(32, P.M - col0);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nj) out[(long long)(col0 + j) * P.N + cs] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+          }
+        } else {
+          store_chunk(stg, re, im, out + (long long)row0 * P.N + col0, P.N, P.M - row0, P.N - col0, lane);
+        }
       }
       fence_before();
       __syncwarp();
@@ -350,7 +367,7 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
   const int grid = (int)(total_tiles < num_ctas ? total_tiles : num_ctas);
   // Forward product (Thm 5.1): C1 = A1 B1 - A2 conj(B2(-f)), C2 = A1 B2 + A2 conj(B1(-f)).
   // (tau ar + i tau ai)(br + i sb bi): re += tau ar.br - tau sb ai.bi, im += tau sb ar.bi + tau ai.br
-  GViews V = {0u, 0u, 0u, 0u};
+  GViews V = {0u, 0u, 0u, 0u, 0u};
   const int a_plane[2][2] = {{0, 1}, {0, 1}};
   const int b_plane[2][2] = {{0, 1}, {1, 0}};
   const int b_conj[2][2] = {{0, 1}, {0, 1}};
@@ -363,11 +380,18 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
       V.b_fneg |= (uint32_t)b_conj[h][kh] << e;  // the conjugated B operand is the one read at -f
       const float tau = sign[h][kh];
       const float sb = b_conj[h][kh] ? -1.f : 1.f;
+      // MMA products (a_re b_re, a_im b_im, a_re b_im, a_im b_re).  Plain: a = A,
+      // b = B (conjugate when sb = -1).  Transposed: a = B, b = A; the complex
+      // product commutes, so only the cross terms swap their signs.
       const float c[4] = {tau, -tau * sb, tau * sb, tau};
-      uint32_t mask = 0;
-      for (int q = 0; q < 4; ++q)
+      const float ct[4] = {tau, -tau * sb, tau, tau * sb};
+      uint32_t mask = 0, mask_t = 0;
+      for (int q = 0; q < 4; ++q) {
         if (c[q] < 0) mask |= 1u << q;
+        if (ct[q] < 0) mask_t |= 1u << q;
+      }
       V.negmask |= mask << (4 * e);
+      V.negmask_t |= mask_t << (4 * e);
     }
   cudaError_t e;
   if (np == 4) {

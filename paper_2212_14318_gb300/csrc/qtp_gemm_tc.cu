@@ -195,7 +195,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       int nw = args.N - nt * BN;
       nw = nw > BN ? BN : ((nw + 15) & ~15);
       const uint32_t idesc = make_idesc(A_MN, B_MN, nw);
-      const uint32_t idesc_neg = idesc | kNegA;
       const uint64_t da0 = part_desc<A_MN, BK>(S.a, 0);
       const uint64_t db0 = part_desc<B_MN, BK>(S.b, 0);
       const uint32_t d_re = tmem;
@@ -223,31 +222,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
 #pragma unroll
         for (int k16 = 0; k16 < BK / 16; ++k16) {
           // part tiles: NP == 4: re_hi, re_lo, im_hi, im_lo; NP == 2: re, im
-          const int RE = 0, IM = NP / 2;
           const uint32_t ka = (uint32_t)k16 * (A_MN ? 2048u : 32u) >> 4;
           const uint32_t kb = (uint32_t)k16 * (B_MN ? 2048u : 32u) >> 4;
-#pragma unroll
-          for (int prod = 0; prod < 4; ++prod) {
-            const int xa = (prod == 0 || prod == 2) ? RE : IM;  // ar, ai, ar, ai
-            const int yb = (prod == 0 || prod == 3) ? RE : IM;  // br, bi, bi, br
-            const bool to_re = prod < 2;
-            const uint32_t id = ((neg >> prod) & 1u) ? idesc_neg : idesc;
-            const uint32_t d = to_re ? d_re : d_im;
-            const uint32_t dc = to_re ? c_re : c_im;
-            uint32_t& acc = to_re ? acc_re : acc_im;
-            uint32_t& accc = SPLIT ? (to_re ? acc_cre : acc_cim) : acc;
-            const uint64_t a_hi = da + (uint64_t)(((uint32_t)xa * A_TILE >> 4) + ka);
-            const uint64_t b_hi = db + (uint64_t)(((uint32_t)yb * B_TILE >> 4) + kb);
-            mma_bf16(d, a_hi, b_hi, id, acc);
-            acc = 1;
-            if (NP == 4) {
-              const uint64_t a_lo = a_hi + (uint64_t)(A_TILE >> 4);
-              const uint64_t b_lo = b_hi + (uint64_t)(B_TILE >> 4);
-              mma_bf16(dc, a_hi, b_lo, id, accc);
-              accc = 1;
-              mma_bf16(dc, a_lo, b_hi, id, 1);
-            }
-          }
+          complex_kstep<NP, SPLIT>(da + ka, db + kb, (uint32_t)(A_TILE >> 4), (uint32_t)(B_TILE >> 4), idesc, neg,
+                                   d_re, d_im, c_re, c_im, acc_re, acc_im, acc_cre, acc_cim);
         }
         mma_commit(S.empty + 8 * s);  // frees the stage when these MMAs complete
       }

@@ -167,7 +167,8 @@ struct GroupProblem {
   int M, N, K, p;
   int tiles_m, tiles_n;
   int lda, ldb;                       // spectra row strides (elements)
-  int bn;                             // tile width (complex columns): 64 or 128 (tensor-core path)
+  int bn;                             // tile width (complex columns)
+  int trans;                          // tensor-core path: tiles of C^T = B^T A^T (rows over s, columns over m)
 };
 
 cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, int nparts,

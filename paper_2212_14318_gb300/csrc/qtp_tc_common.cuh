@@ -128,7 +128,84 @@ __host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn, int bn, 
          ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(bm >> 4) << 24);
 }
 constexpr uint32_t kNegA = 1u << 13;
+constexpr uint32_t kNegB = 1u << 14;
 
+// A-operand collector use of one tcgen05.mma: read A from shared memory and
+// keep it (FILL), or take the kept A a last time and release it (LASTUSE).
+// Used on pairs of consecutive MMAs with the same A descriptor and the same
+// instruction descriptor (different B and accumulator), which then read A from
+// shared memory once.  (Chains with .collector::a::use between them, across
+// MMAs whose instruction descriptors differ in a negate bit, gave wrong
+// results on the GB300 and are not used.)
+enum : int { kCollFill = 1, kCollLastUse = 3 };
+
+template <int COLL>
+__device__ __forceinline__ void mma_bf16_c(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  if constexpr (COLL == kCollFill) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    static_assert(COLL == kCollLastUse, "collector use");
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+
+// The MMAs of one K step of a complex product in split-BF16 (NP = 4 parts per
+// operand: re_hi, re_lo, im_hi, im_lo) or plain BF16 (NP = 2: re, im):
+//   re += s0 ar.br + s1 ai.bi,   im += s2 ar.bi + s3 ai.br,
+// each real product x.y as x_hi.y_hi (into the main accumulator) plus
+// x_hi.y_lo + x_lo.y_hi (into the correction accumulator, which is the main
+// one unless the kernel splits them).  Bit q of neg makes s_q = -1, applied by
+// negating B.  In split-BF16 the two MMAs x_hi.y_hi and x_hi.y_lo share A and
+// sign and run as a collector pair, so a K step reads each A_hi part twice
+// from shared memory instead of four times.  da, db: the descriptors of part 0
+// of the A and B tiles; a_step, b_step: descriptor increments from one part to
+// the next.  acc_*: accumulate flags (0 until the accumulator's first MMA).
+template <int NP, bool SPLIT>
+__device__ __forceinline__ void complex_kstep(uint64_t da, uint64_t db, uint32_t a_step, uint32_t b_step,
+                                              uint32_t idesc, uint32_t neg, uint32_t d_re, uint32_t d_im,
+                                              uint32_t c_re, uint32_t c_im, uint32_t& acc_re, uint32_t& acc_im,
+                                              uint32_t& acc_cre, uint32_t& acc_cim) {
+  const uint32_t s0 = (neg & 1u) ? idesc | kNegB : idesc;
+  const uint32_t s1 = (neg & 2u) ? idesc | kNegB : idesc;
+  const uint32_t s2 = (neg & 4u) ? idesc | kNegB : idesc;
+  const uint32_t s3 = (neg & 8u) ? idesc | kNegB : idesc;
+  if constexpr (NP == 4) {
+    const uint64_t ar_hi = da, ar_lo = da + a_step, ai_hi = da + 2 * a_step, ai_lo = da + 3 * a_step;
+    const uint64_t br_hi = db, br_lo = db + b_step, bi_hi = db + 2 * b_step, bi_lo = db + 3 * b_step;
+    const uint32_t f_cre = SPLIT ? acc_cre : 1u, f_cim = SPLIT ? acc_cim : 1u;
+    mma_bf16_c<kCollFill>(d_re, ar_hi, br_hi, s0, acc_re);
+    mma_bf16_c<kCollLastUse>(c_re, ar_hi, br_lo, s0, f_cre);
+    mma_bf16_c<kCollFill>(d_im, ar_hi, bi_hi, s2, acc_im);
+    mma_bf16_c<kCollLastUse>(c_im, ar_hi, bi_lo, s2, f_cim);
+    mma_bf16(c_re, ar_lo, br_hi, s0, 1u);
+    mma_bf16(c_im, ar_lo, bi_hi, s2, 1u);
+    mma_bf16_c<kCollFill>(d_re, ai_hi, bi_hi, s1, 1u);
+    mma_bf16_c<kCollLastUse>(c_re, ai_hi, bi_lo, s1, 1u);
+    mma_bf16_c<kCollFill>(d_im, ai_hi, br_hi, s3, 1u);
+    mma_bf16_c<kCollLastUse>(c_im, ai_hi, br_lo, s3, 1u);
+    mma_bf16(c_re, ai_lo, bi_hi, s1, 1u);
+    mma_bf16(c_im, ai_lo, br_hi, s3, 1u);
+    acc_cre = 1u;
+    acc_cim = 1u;
+  } else {
+    const uint64_t ar = da, ai = da + a_step, br = db, bi = db + b_step;
+    mma_bf16(d_re, ar, br, s0, acc_re);
+    mma_bf16(d_im, ar, bi, s2, acc_im);
+    mma_bf16(d_re, ai, bi, s1, 1u);
+    mma_bf16(d_im, ai, br, s3, 1u);
+  }
+  acc_re = 1u;
+  acc_im = 1u;
+}
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");

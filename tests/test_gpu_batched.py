@@ -15,7 +15,10 @@ ELEM_TOL = 1e-4
 # mixed shapes: specialised and generic tube lengths, ragged tiles, tiny and wide products
 MIXED = [(8, 8, 8, 16), (17, 9, 13, 3), (33, 65, 31, 7), (130, 40, 150, 8), (5, 3, 4, 2), (1, 1, 1, 1),
          (20, 30, 40, 12), (16, 16, 16, 31), (40, 24, 36, 64), (13, 7, 11, 100), (64, 48, 80, 128),
-         (9, 11, 10, 97), (3, 5, 7, 1), (70, 1, 70, 5), (24, 20, 28, 32), (12, 12, 12, 8)]
+         (9, 11, 10, 97), (3, 5, 7, 1), (70, 1, 70, 5), (24, 20, 28, 32), (12, 12, 12, 8),
+         # s well above m: computed as C^T = B^T A^T on the tensor cores (several
+         # row tiles over s; two column tiles over m in the second)
+         (20, 30, 200, 8), (150, 40, 300, 4), (5, 17, 260, 12)]
 
 
 def _check_all(shapes, As, Bs, Cs, what):
