@@ -8,7 +8,7 @@
 // X.Y the three tensor-core products Xhi.Yhi + Xhi.Ylo + Xlo.Yhi (the lo.lo
 // term is below FP32 rounding), accumulated in FP32 in tensor memory.  Signs
 // (from the paper's "-" in eq. TC and from conjugations) are applied with the
-// instruction descriptor's negate-A bit, so no operand is ever rewritten.
+// instruction descriptor's negate-B bit, so no operand is ever rewritten.
 //
 // For frequency f and output half h the CTA computes a 128 x BN complex tile
 // (BN = 256 for wide products, 128 otherwise)
@@ -16,12 +16,12 @@
 // with two accumulators in TMEM (real part: columns 0..BN-1, imaginary part:
 // columns BN..2BN-1).  The 256-wide MMA reads 96 B of operands per clock from
 // shared memory where two 128-wide ones read 128 B, which leaves room for the
-// TMA fills.  Operands stream through a 2-4 stage TMA -> shared memory
-// pipeline (mbarrier full/empty pairs); one thread issues tcgen05.mma, four
-// warps drain TMEM with tcgen05.ld.  K-major operands use the 64-byte swizzle
-// (32 bf16 of K per row); MN-major operands the 128-byte swizzle (64 bf16 of
-// M or N per row, 32 rows of K).  Every wait is bounded: on expiry the kernel
-// records an error code in the plan's error word and unwinds.
+// TMA fills.  Operands stream through a TMA -> shared memory ring of 16-deep
+// K steps (mbarrier full/empty pairs); one thread issues tcgen05.mma, four
+// warps drain TMEM with tcgen05.ld.  K-major operands use the 32-byte swizzle
+// (16 bf16 of K per row); MN-major operands the 128-byte swizzle (64 bf16 of
+// M or N per row).  Every wait is bounded: on expiry the kernel records an
+// error code in the plan's error word and unwinds.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdio.h>
