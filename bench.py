@@ -204,13 +204,14 @@ def kernel_source_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(stage):
-    """DRAM bytes per launch from the committed ncu record, if the sources have not changed since."""
+def recorded_traffic(stage, workload):
+    """DRAM bytes per launch from the committed ncu record, if it was taken on this workload and the
+    sources have not changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    if rec.get("source_digest") != kernel_source_digest():
+    if rec.get("source_digest") != kernel_source_digest() or rec.get("workload") != workload:
         return None
     ent = rec.get("stages", {}).get(stage)
     return None if ent is None else ent.get("dram_bytes_per_launch")
@@ -349,11 +350,11 @@ def run_ours(args):
         tc_peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         stages = {
             "fft_forward": {"ms": st[0], "bound": "hbm", "achieved": bytes_s1 / (st[0] * 1e-3) / 1e9,
-                            "peak": hbm, "unit": "GB/s", "traffic": recorded_traffic("fft_forward")},
+                            "peak": hbm, "unit": "GB/s", "traffic": recorded_traffic("fft_forward", args.workload)},
             "products": {"ms": st[1], "bound": "tensor", "achieved": alg_flops_issued / (st[1] * 1e-3) / 1e12,
-                         "peak": tc_peak, "unit": "TFLOP/s", "traffic": recorded_traffic("products")},
+                         "peak": tc_peak, "unit": "TFLOP/s", "traffic": recorded_traffic("products", args.workload)},
             "fft_inverse": {"ms": st[2], "bound": "hbm", "achieved": bytes_s3 / (st[2] * 1e-3) / 1e9,
-                            "peak": hbm, "unit": "GB/s", "traffic": recorded_traffic("fft_inverse")},
+                            "peak": hbm, "unit": "GB/s", "traffic": recorded_traffic("fft_inverse", args.workload)},
         }
         for v in stages.values():
             v["frac"] = v["achieved"] / v["peak"]
