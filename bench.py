@@ -12,7 +12,11 @@ fast-route work, 32 m n s p (Thm 5.2) + 5 p log2(p) per complex tube
 transform x 2 (mn + ns + ms) transforms.  Split-BF16 (bf16x3) products are
 the main path; the plain FP32 path on the same workload is reported beside
 it, with the relative error of both against the FP64 oracle on sampled
-entries.  For N > 1 (torchrun) every rank runs its own replica (the products
+entries.  Per-stage times (the JSON line's `stages`, and the roofline's
+kernel time) come from a separate loop of up to 200 steps with the library's
+stage events on, since events between the three launches would stop each
+from starting while the previous one drains.  For N > 1 (torchrun) every rank
+runs its own replica (the products
 are independent; no collective on the data path): weak scaling, value = total
 work of all ranks / max-over-ranks time.
 
@@ -250,15 +254,14 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     flops = effective_flops(m, n, s, p)
 
-    def timed_leg(precision, steps, warmup, trace):
+    def timed_leg(precision, steps, warmup, trace_steps):
+        """Per-step CUDA events around plan.forward (no stage events inside: they
+        would serialise the launches), then a separate traced loop of
+        trace_steps steps for the per-stage times (ms per launch)."""
         plan = qtp.Plan(m, n, s, p, precision)
-        if trace:
-            plan.set_tracing(True)
         for _ in range(warmup):
             plan.forward(A, B, C)
         plan.sync()
-        stage_ms = [0.0, 0.0, 0.0]
-        step_ms = []
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
         for i in range(steps):
@@ -266,19 +269,26 @@ def run_ours(args):
             evs[i][0].record()
             plan.forward(A, B, C)
             evs[i][1].record()
-            if trace:
-                st = plan.stage_times()
-                for j in range(3):
-                    stage_ms[j] += st[j]
         barrier()
         plan.sync()
         step_ms = [a.elapsed_time(b) for a, b in evs]
+        stage_ms = [0.0, 0.0, 0.0]
+        if trace_steps:
+            plan.set_tracing(True)
+            for _ in range(trace_steps):
+                flush.zero_()
+                plan.forward(A, B, C)
+                st = plan.stage_times()
+                for j in range(3):
+                    stage_ms[j] += st[j] / trace_steps
+            plan.set_tracing(False)
+            plan.sync()
         return plan, sum(step_ms), stage_ms
 
     # main leg (split-BF16 by default)
     sampler = ClockSampler(local)
     sampler.start()
-    plan, total_ms, stage_ms = timed_leg(args.precision, args.steps, args.warmup, trace=True)
+    plan, total_ms, stage_ms = timed_leg(args.precision, args.steps, args.warmup, trace_steps=min(args.steps, 200))
     clocks = sampler.stop()
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -308,10 +318,10 @@ def run_ours(args):
     # at most ~3 s of timed work
     est = ms_per_step * 6.0
     fp32_steps = max(3, min(args.fp32_steps, int(3000.0 / max(est, 1e-3))))
-    fp32_plan, fp32_ms, fp32_stage = timed_leg("fp32", fp32_steps, 3, trace=True)
+    fp32_plan, fp32_ms, fp32_stage = timed_leg("fp32", fp32_steps, 3, trace_steps=min(fp32_steps, 5))
     fp32 = {"ms_per_step": fp32_ms / fp32_steps,
             "value": flops / (fp32_ms / fp32_steps * 1e-3) / 1e12,
-            "products_ms": fp32_stage[1] / fp32_steps, "steps": fp32_steps}
+            "products_ms": fp32_stage[1], "steps": fp32_steps}
     if rank == 0:
         fp32_plan.forward(A, B, C)
         fp32_plan.sync()
@@ -342,7 +352,7 @@ def run_ours(args):
 
     if rank == 0:
         peaks, peak_src = load_peaks()
-        st = [x / args.steps for x in stage_ms]   # ms per launch
+        st = stage_ms   # ms per launch (traced loop)
         alg_flops_issued = (3.0 if args.precision == "bf16x3" else 1.0) * 32.0 * m * n * s * p
         bytes_s1 = 32.0 * p * (m * n + n * s)      # read 16 B + write 16 B per quaternion entry
         bytes_s3 = 32.0 * p * (m * s)

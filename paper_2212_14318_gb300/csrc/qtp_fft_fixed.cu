@@ -647,6 +647,7 @@ template <int P, int FMT>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_fixed(FftFwdJob job0, FftFwdJob job1, int njobs,
                                                           const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
+  if (threadIdx.x == 0) grid_dep_launch();  // the products may be scheduled once every CTA got here
   int b = blockIdx.x;
   const bool second = njobs > 1 && b >= job0.nblocks;
   if (second) b -= job0.nblocks;
@@ -657,6 +658,7 @@ template <int P>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
                                                           const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
+  grid_dep_wait();  // C's spectra come from the previous kernel (launched with PDL)
   int b = blockIdx.x;
   const bool second = njobs > 1 && b >= job0.nblocks;
   if (second) b -= job0.nblocks;
@@ -778,7 +780,18 @@ cudaError_t inv_launch(const FftInvJob* jobs, int njobs, const float2* tw, cudaS
   int nb = 0;
   for (int i = 0; i < njobs; ++i) nb += jobs[i].nblocks;
   if (nb == 0) return cudaSuccess;
-  fft_inv_fixed<P><<<nb, kThreads, smem, st>>>(jobs[0], njobs > 1 ? jobs[1] : jobs[0], njobs, tw);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, fft_inv_fixed<P>, jobs[0], njobs > 1 ? jobs[1] : jobs[0], njobs, tw);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&args.tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&args.tmB)) : "memory");
+    grid_dep_launch();  // the inverse transform may be scheduled once every CTA got here
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
+      grid_dep_wait();  // the spectra come from the previous kernel (launched with PDL)
       int issued = 0;
       for (int it = 0; it < total; ++it) {
         const int kh = it / nkb;
@@ -349,7 +351,20 @@ cudaError_t launch_kind(const TcArgs& args, dim3 grid, cudaStream_t st) {
       (size_t)stages_for(NP, BN, BK) * NP * (BM * BK * 2 + BK * BN * 2) + 1024 /*align*/ + 256 /*barriers*/;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kfn<<<grid, kThreads, smem, st>>>(args);
+  // programmatic dependent launch: the prologue (barriers, TMEM, tensor-map
+  // prefetch) overlaps the previous kernel's tail; the producer waits
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kfn, args);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

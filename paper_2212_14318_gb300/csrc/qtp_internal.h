@@ -16,6 +16,16 @@
 
 namespace qtp {
 
+// Programmatic dependent launch: a kernel launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization may start while the
+// previous kernel on its stream drains; every thread that reads that kernel's
+// output first executes grid_dep_wait() (griddepcontrol.wait: returns once the
+// prerequisite grid has completed and its writes are visible).  A kernel
+// calls grid_dep_launch() (griddepcontrol.launch_dependents) to let such a
+// successor be scheduled before it finishes.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Output formats of the forward tube FFT (Alg. 5.1 Step 1).
 enum SpecFormat : int {
   FMT_C32 = 0,     // complex FP32, [plane][f][row][ld]
