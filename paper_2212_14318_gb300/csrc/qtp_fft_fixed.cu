@@ -59,8 +59,9 @@ __host__ __device__ constexpr Split split_of(int p, bool inv) {
 // Tubes per CTA: a power of two, at most kThreads, so that in the strided
 // loops over (frequency, tube) every thread keeps one tube (or tube pair) and
 // computes its address once.
-//   Two-pass: about 4096 complex per CTA (32 KB of exchange buffer), at least
-//   32 tubes (the frequency-major stores write runs of T tubes).
+//   Two-pass: about QTP_FS_ELEMS = 4096 complex per CTA (32 KB of exchange
+//   buffer), at least 32 tubes (the frequency-major stores write runs of T
+//   tubes).
 //   Stockham: about QTP_FFT_ELEMS complex per buffer (2304: ~34 KB per CTA,
 //   up to six resident CTAs per SM; measured faster than 4608); the forward
 //   transform keeps at least 32 tubes, the inverse, whose stores are
@@ -68,19 +69,27 @@ __host__ __device__ constexpr Split split_of(int p, bool inv) {
 #ifndef QTP_FFT_ELEMS
 #define QTP_FFT_ELEMS 2304
 #endif
+#ifndef QTP_FS_ELEMS
+#define QTP_FS_ELEMS 4096
+#endif
 // Resident CTAs per SM the transform kernels are compiled for (caps their
-// registers at 65536 / (kThreads kMinBlocks) = 85): the two-pass forward is
-// latency-bound, and three resident CTAs beat the spill-free register count
-// (video forward 80 -> 66 us).
+// registers at 65536 / (kThreads kMinBlocks)): the two-pass transforms are
+// latency-bound.  Forward: three (85 registers; video forward 80 -> 66 us
+// against the spill-free count; four measured slower).  Inverse: four (64
+// registers; the batch's inverse transforms 9.4 -> 8.7 ms).
 #ifndef QTP_FFT_MINB
 #define QTP_FFT_MINB 3
 #endif
+#ifndef QTP_FFT_MINB_INV
+#define QTP_FFT_MINB_INV 4
+#endif
 constexpr int kMinBlocks = QTP_FFT_MINB;
+constexpr int kMinBlocksInv = QTP_FFT_MINB_INV;
 
 __host__ __device__ constexpr int tubes_for(int p, bool inv) {
   int lim = 0;
   if (split_of(p, inv).r1 != 0) {
-    lim = 4096 / p;
+    lim = QTP_FS_ELEMS / p;
     if (lim < 32) lim = 32;
   } else {
     lim = QTP_FFT_ELEMS / (p | 1);
@@ -655,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_fixed(FftFwdJob 
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
+__global__ void __launch_bounds__(kThreads, kMinBlocksInv) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
                                                           const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
   grid_dep_wait();  // C's spectra come from the previous kernel (launched with PDL)
@@ -698,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_grouped(const Ff
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) fft_inv_grouped(const FftGroupJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, kMinBlocksInv) fft_inv_grouped(const FftGroupJob* __restrict__ jobs,
                                                             const int* __restrict__ job_of_block, long long block0,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
