@@ -148,6 +148,58 @@ def cpu_baseline(Aq, Bq, budget_s=15.0):
     }
 
 
+def cpu_alg51(Aq, Bq):
+    """The paper's own method (Algorithm 5.1) in FP64 NumPy on the host cores, timed once: the
+    Table 1 parity timing.  Skipped (None) where its per-frequency products exceed 100 GFLOP."""
+    import oracle as Q
+    m, n, s, p = dims()
+    if 32.0 * m * n * s * p > 1e11:
+        return None
+    t0 = time.perf_counter()
+    Q.alg51(Aq, Bq)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "value": effective_flops(m, n, s, p) / dt / 1e12, "unit": UNIT,
+            "cores": cores_used(), "kind": "oracle Algorithm 5.1 (FP64 NumPy FFT + per-frequency matmuls)"}
+
+
+def measure_fp32_peak(dev, n=8192, reps=10):
+    """FP32 FMA throughput of this GPU, measured as cuBLAS SGEMM (TF32 off) through torch: the
+    roofline denominator of the plain FP32 path (MEASURED_PEAKS.json has none)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(n, n, device=dev)
+        b = torch.randn(n, n, device=dev)
+        c = torch.empty(n, n, device=dev)
+        for _ in range(3):
+            torch.mm(a, b, out=c)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.mm(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def reduce_max(x, world, device):
+    """Max of x over the ranks of the default process group (x itself on one rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(flops_per_rank, world, ms_per_step):
+    """Whole-job TFLOP/s: every rank's work over the slowest rank's time per step."""
+    return world * flops_per_rank / (ms_per_step * 1e-3) / 1e12
+
+
 # ----------------------------------------------------------------------------- clocks
 
 
@@ -290,12 +342,9 @@ def run_ours(args):
     sampler.start()
     plan, total_ms, stage_ms = timed_leg(args.precision, args.steps, args.warmup, trace_steps=min(args.steps, 200))
     clocks = sampler.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = reduce_max(total_ms, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * flops / (ms_per_step * 1e-3) / 1e12
+    value = job_value(flops, world, ms_per_step)
 
     # accuracy against the FP64 oracle on 32 sampled mode-1 fibres C(:, t, k)
     if rank == 0:
@@ -322,6 +371,11 @@ def run_ours(args):
     fp32 = {"ms_per_step": fp32_ms / fp32_steps,
             "value": flops / (fp32_ms / fp32_steps * 1e-3) / 1e12,
             "products_ms": fp32_stage[1], "steps": fp32_steps}
+    fp32_peak = measure_fp32_peak(dev)
+    fp32_ach = 32.0 * m * n * s * p / (fp32_stage[1] * 1e-3) / 1e12
+    fp32["roofline"] = {"bound": "fp32", "kernel": "products (gemm_simt_kernel)", "achieved": fp32_ach,
+                        "peak": fp32_peak, "unit": "TFLOP/s", "frac": fp32_ach / fp32_peak,
+                        "peak_source": "cuBLAS FP32 SGEMM (TF32 off) measured in this run"}
     if rank == 0:
         fp32_plan.forward(A, B, C)
         fp32_plan.sync()
@@ -345,10 +399,7 @@ def run_ours(args):
     e1.record()
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_ms = float(te.item())
+    e2e_ms = reduce_max(e2e_ms, world, dev)
 
     if rank == 0:
         peaks, peak_src = load_peaks()
@@ -385,7 +436,7 @@ def run_ours(args):
             "roofline": roof,
             "stages": stages,
             "fp32_path": fp32,
-            "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+            "e2e": {"value": job_value(flops, world, e2e_ms), "unit": UNIT,
                     "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(A.numel() * 4 + B.numel() * 4),
                     "d2h_bytes_per_step": int(C.numel() * 4)},
@@ -394,6 +445,9 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(Aq, Bq)
+            a51 = cpu_alg51(Aq, Bq)
+            if a51 is not None:
+                line["cpu_baseline"]["alg51_fp64"] = a51
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -140,3 +140,40 @@ def test_forward_host_buffers(precision):
     plan.forward_host(hA, hB, hC, buf)
     plan.sync()
     assert_close(hC.numpy(), _oracle(A, B), REL_TOL, ELEM_TOL, "host buffers")
+
+
+# Tube lengths beyond the compile-time set (runtime-radix transforms, one or a
+# few tubes per CTA; p up to the supported maximum 4096): sampled entries by
+# the definition (O(n p) each) and the whole result against the oracle's FP64
+# Algorithm 5.1, itself pinned to the definition on the CPU.
+LARGE_P = [(5, 6, 7, 256), (3, 4, 5, 1000), (17, 9, 13, 500), (2, 3, 2, 4096), (4, 6, 5, 2187)]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("m,n,s,p", LARGE_P)
+def test_forward_large_p(precision, m, n, s, p):
+    qtp = _qtp()
+    A, B = _inputs(m, n, s, p, seed=p + m)
+    plan = qtp.Plan(m, n, s, p, precision)
+    C = to_host(plan.forward(to_dev(A), to_dev(B)))
+    plan.sync()
+    Aq, Bq = planes_to_comp(A), planes_to_comp(B)
+    assert_close(C, Q.alg51(Aq, Bq), REL_TOL, ELEM_TOL, f"large p={p} vs Alg. 5.1 (FP64)")
+    ii, tt, kk = synth.sample_positions(m, s, p, 64)
+    ref = Q.tprod_def_entries(Aq, Bq, ii, tt, kk)
+    got = planes_to_comp(C)[:, ii, tt, kk]
+    assert np.linalg.norm(got - ref) <= REL_TOL * np.linalg.norm(ref), f"large p={p} sampled entries"
+
+
+@pytest.mark.parametrize("m,n,s,p", LARGE_P[:2])
+def test_batched_large_p(m, n, s, p):
+    qtp = _qtp()
+    shapes = [(m, n, s, p), (m + 1, n, s + 2, p), (4, 4, 4, 8)]
+    As = [synth.quat_normal(a, b, q, 70 + i) for i, (a, b, c, q) in enumerate(shapes)]
+    Bs = [synth.quat_normal(b, c, q, 80 + i) for i, (a, b, c, q) in enumerate(shapes)]
+    plan = qtp.BatchPlan(shapes, "bf16x3")
+    Cs = plan.forward([to_dev(a) for a in As], [to_dev(b) for b in Bs])
+    plan.sync()
+    for i, (a, b, c, q) in enumerate(shapes):
+        ref = Q.alg51(planes_to_comp(As[i]), planes_to_comp(Bs[i]))
+        assert_close(to_host(Cs[i]), ref, REL_TOL, ELEM_TOL, f"batched product {i} p={q}")
