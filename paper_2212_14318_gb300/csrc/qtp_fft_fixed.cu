@@ -52,6 +52,9 @@ __host__ __device__ constexpr Split split_of(int p, bool inv) {
     case 64: return Split{8, 8};
     case 100: return inv ? Split{10, 10} : Split{20, 5};
     case 128: return Split{16, 8};
+    case 256: return Split{16, 16};
+    case 512: return Split{32, 16};
+    case 1024: return Split{32, 32};
     default: return Split{0, 0};
   }
 }
@@ -61,7 +64,8 @@ __host__ __device__ constexpr Split split_of(int p, bool inv) {
 // computes its address once.
 //   Two-pass: about QTP_FS_ELEMS = 4096 complex per CTA (32 KB of exchange
 //   buffer), at least 32 tubes (the frequency-major stores write runs of T
-//   tubes).
+//   tubes) as long as the buffer stays within 64 KB (p = 256, 512, 1024:
+//   32, 16, 8 tubes).
 //   Stockham: about QTP_FFT_ELEMS complex per buffer (2304: ~34 KB per CTA,
 //   up to six resident CTAs per SM; measured faster than 4608); the forward
 //   transform keeps at least 32 tubes, the inverse, whose stores are
@@ -73,8 +77,8 @@ __host__ __device__ constexpr Split split_of(int p, bool inv) {
 #define QTP_FS_ELEMS 4096
 #endif
 // Resident CTAs per SM the transform kernels are compiled for (caps their
-// registers at 65536 / (kThreads kMinBlocks)): the two-pass transforms are
-// latency-bound.  Forward: three (85 registers; video forward 80 -> 66 us
+// registers at 65536 / (kThreads * resident CTAs)): the two-pass transforms
+// are latency-bound.  Forward: three (85 registers; video forward 80 -> 66 us
 // against the spill-free count; four measured slower).  Inverse: four (64
 // registers; the batch's inverse transforms 9.4 -> 8.7 ms).
 #ifndef QTP_FFT_MINB
@@ -83,14 +87,20 @@ __host__ __device__ constexpr Split split_of(int p, bool inv) {
 #ifndef QTP_FFT_MINB_INV
 #define QTP_FFT_MINB_INV 4
 #endif
-constexpr int kMinBlocks = QTP_FFT_MINB;
-constexpr int kMinBlocksInv = QTP_FFT_MINB_INV;
+// Tube lengths of 256 and up (64 KB CTAs, DFTs of 16 or 32 per thread) take
+// two CTAs per SM: 128 registers, no spills.
+template <int P, bool INV>
+__host__ __device__ constexpr int min_blocks() {
+  return P >= 256 ? 2 : (INV ? QTP_FFT_MINB_INV : QTP_FFT_MINB);
+}
 
 __host__ __device__ constexpr int tubes_for(int p, bool inv) {
   int lim = 0;
   if (split_of(p, inv).r1 != 0) {
+    // at least 32 tubes while the buffer stays within 64 KB (8 192 complex)
     lim = QTP_FS_ELEMS / p;
-    if (lim < 32) lim = 32;
+    const int cap = 8192 / p < 32 ? 8192 / p : 32;
+    if (lim < cap) lim = cap;
   } else {
     lim = QTP_FFT_ELEMS / (p | 1);
     if (!inv && lim < 32 && p <= 128) lim = 32;
@@ -343,7 +353,10 @@ __device__ __forceinline__ void fs_fwd_body(const FftFwdJob& job, long long b, c
     const long long row = rem / job.cols;
     return plane * NPARTS * P * slab + row * ld + (rem - row * job.cols);
   };
-  if ((job.cols & 1) == 0) {
+  // Tube pairs (4-byte bf16 pair stores) when the row has an even number of
+  // columns and two tubes' R2 values fit in registers.
+  constexpr bool kPairs = R2 <= 10;
+  if (kPairs && (job.cols & 1) == 0) {
     // tube pairs share a row: 16-byte / 4-byte stores
     constexpr int TH = T / 2;
     const int tube = 2 * (threadIdx.x % TH);
@@ -437,8 +450,9 @@ __device__ __forceinline__ void fs_inv_body(const FftInvJob& job, long long b, c
     return plane * P * per_plane + (t - plane * per_plane);
   };
 
-  // pass 1
-  if ((job.cols & 1) == 0) {
+  // pass 1 (tube pairs: 16-byte loads, when two tubes' F2 values fit in registers)
+  constexpr bool kPairs = F2 <= 10;
+  if (kPairs && (job.cols & 1) == 0) {
     constexpr int TH = T / 2;
     const int tube = 2 * (threadIdx.x % TH);
     if (tube < Tb) {
@@ -653,7 +667,7 @@ __device__ __forceinline__ void fixed_inv_body(const FftInvJob& job, long long b
 }
 
 template <int P, int FMT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_fixed(FftFwdJob job0, FftFwdJob job1, int njobs,
+__global__ void __launch_bounds__(kThreads, min_blocks<P, false>()) fft_fwd_fixed(FftFwdJob job0, FftFwdJob job1, int njobs,
                                                           const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
   if (threadIdx.x == 0) grid_dep_launch();  // the products may be scheduled once every CTA got here
@@ -664,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_fixed(FftFwdJob 
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, kMinBlocksInv) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
+__global__ void __launch_bounds__(kThreads, min_blocks<P, true>()) fft_inv_fixed(FftInvJob job0, FftInvJob job1, int njobs,
                                                           const float2* __restrict__ tw) {
   extern __shared__ float4 smem_f4[];
   grid_dep_wait();  // C's spectra come from the previous kernel (launched with PDL)
@@ -685,7 +699,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksInv) fft_inv_fixed(FftInvJ
 // ---------------------------------------------------------------------------
 
 template <int P, int FMT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_grouped(const FftGroupJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, min_blocks<P, false>()) fft_fwd_grouped(const FftGroupJob* __restrict__ jobs,
                                                             const int* __restrict__ job_of_block, long long block0,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
@@ -707,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) fft_fwd_grouped(const Ff
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, kMinBlocksInv) fft_inv_grouped(const FftGroupJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, min_blocks<P, true>()) fft_inv_grouped(const FftGroupJob* __restrict__ jobs,
                                                             const int* __restrict__ job_of_block, long long block0,
                                                             const float2* const* __restrict__ ptrs, char* ws,
                                                             const float2* __restrict__ tw_all) {
@@ -812,6 +826,7 @@ size_t fft_fixed_smem(int p, bool inv) {
   switch (p) {
     QTP_SMEM_CASE(8) QTP_SMEM_CASE(12) QTP_SMEM_CASE(16) QTP_SMEM_CASE(31)
     QTP_SMEM_CASE(32) QTP_SMEM_CASE(64) QTP_SMEM_CASE(100) QTP_SMEM_CASE(128)
+    QTP_SMEM_CASE(256) QTP_SMEM_CASE(512) QTP_SMEM_CASE(1024)
     default: return 0;
   }
 #undef QTP_SMEM_CASE
@@ -827,6 +842,7 @@ cudaError_t launch_fft_fwd_grouped(const FftGroupJob* d_jobs, const int* d_job_o
   switch (p) {
     QTP_FWD_GROUPED_CASE(8) QTP_FWD_GROUPED_CASE(12) QTP_FWD_GROUPED_CASE(16) QTP_FWD_GROUPED_CASE(31)
     QTP_FWD_GROUPED_CASE(32) QTP_FWD_GROUPED_CASE(64) QTP_FWD_GROUPED_CASE(100) QTP_FWD_GROUPED_CASE(128)
+    QTP_FWD_GROUPED_CASE(256) QTP_FWD_GROUPED_CASE(512) QTP_FWD_GROUPED_CASE(1024)
     default: return fwd_grouped_fmt<0>(d_jobs, d_job_of_block, block0, nblocks, fmt, d_ptrs, ws, d_tw, smem, st);
   }
 #undef QTP_FWD_GROUPED_CASE
@@ -842,6 +858,7 @@ cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_o
   switch (p) {
     QTP_INV_GROUPED_CASE(8) QTP_INV_GROUPED_CASE(12) QTP_INV_GROUPED_CASE(16) QTP_INV_GROUPED_CASE(31)
     QTP_INV_GROUPED_CASE(32) QTP_INV_GROUPED_CASE(64) QTP_INV_GROUPED_CASE(100) QTP_INV_GROUPED_CASE(128)
+    QTP_INV_GROUPED_CASE(256) QTP_INV_GROUPED_CASE(512) QTP_INV_GROUPED_CASE(1024)
     default: return inv_grouped_launch<0>(d_jobs, d_job_of_block, block0, nblocks, d_ptrs, ws, d_tw, smem, st);
   }
 #undef QTP_INV_GROUPED_CASE
@@ -849,7 +866,8 @@ cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_o
 
 int fft_fixed_tubes(int p, bool inv) {
   switch (p) {
-    case 8: case 12: case 16: case 31: case 32: case 64: case 100: case 128: return tubes_for(p, inv);
+    case 8: case 12: case 16: case 31: case 32: case 64: case 100: case 128: case 256: case 512: case 1024:
+      return tubes_for(p, inv);
     default: return 0;
   }
 }
@@ -865,6 +883,9 @@ cudaError_t launch_fft_fwd_fixed(const FftFwdJob* jobs, int njobs, int fmt, int 
     case 64: return fwd_fmt<64>(jobs, njobs, fmt, tw, st);
     case 100: return fwd_fmt<100>(jobs, njobs, fmt, tw, st);
     case 128: return fwd_fmt<128>(jobs, njobs, fmt, tw, st);
+    case 256: return fwd_fmt<256>(jobs, njobs, fmt, tw, st);
+    case 512: return fwd_fmt<512>(jobs, njobs, fmt, tw, st);
+    case 1024: return fwd_fmt<1024>(jobs, njobs, fmt, tw, st);
     default: return cudaErrorNotSupported;
   }
 }
@@ -879,6 +900,9 @@ cudaError_t launch_fft_inv_fixed(const FftInvJob* jobs, int njobs, int p, const 
     case 64: return inv_launch<64>(jobs, njobs, tw, st);
     case 100: return inv_launch<100>(jobs, njobs, tw, st);
     case 128: return inv_launch<128>(jobs, njobs, tw, st);
+    case 256: return inv_launch<256>(jobs, njobs, tw, st);
+    case 512: return inv_launch<512>(jobs, njobs, tw, st);
+    case 1024: return inv_launch<1024>(jobs, njobs, tw, st);
     default: return cudaErrorNotSupported;
   }
 }

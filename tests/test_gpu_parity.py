@@ -142,11 +142,13 @@ def test_forward_host_buffers(precision):
     assert_close(hC.numpy(), _oracle(A, B), REL_TOL, ELEM_TOL, "host buffers")
 
 
-# Tube lengths beyond the compile-time set (runtime-radix transforms, one or a
-# few tubes per CTA; p up to the supported maximum 4096): sampled entries by
+# Long tubes: the two-pass lengths 256, 512, 1024 (8-32 tubes per CTA) and
+# runtime-radix lengths up to the supported maximum 4096 (one to fifteen
+# tubes per CTA), odd and even column counts: sampled entries by
 # the definition (O(n p) each) and the whole result against the oracle's FP64
 # Algorithm 5.1, itself pinned to the definition on the CPU.
-LARGE_P = [(5, 6, 7, 256), (3, 4, 5, 1000), (17, 9, 13, 500), (2, 3, 2, 4096), (4, 6, 5, 2187)]
+LARGE_P = [(5, 6, 7, 256), (3, 4, 5, 1000), (17, 9, 13, 500), (2, 3, 2, 4096), (4, 6, 5, 2187),
+           (6, 5, 7, 512), (3, 4, 5, 1024), (9, 7, 40, 1024)]
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
