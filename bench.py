@@ -71,11 +71,21 @@ def effective_flops(m, n, s, p):
     return 32.0 * m * n * s * p + 10.0 * p * math.log2(p) * (m * n + n * s + m * s) if p > 1 else 32.0 * m * n * s
 
 
+def backward_flops(m, n, s, p):
+    """dA = dC * B^H and dB = A^H * dC by the same route: 2 x 32 m n s p of products, transforms of A,
+    B and dC forward and of dA, dB inverse (5 p log2 p per complex transform, 2 per quaternion tube)."""
+    fft = 10.0 * p * math.log2(p) * (2 * m * n + 2 * n * s + m * s) if p > 1 else 0.0
+    return 64.0 * m * n * s * p + fft
+
+
 def workload_desc():
     m, n, s, p = dims()
     if WORKLOAD == "video":
         return (f"colour-video T-product: A {m}x{n}x{p} pure quaternion (pixel-like, i/j/k ~ U[0,1]) * "
                 f"B {n}x{s}x{p} N(0,1), FP32 storage")
+    if WORKLOAD == "diff":
+        return (f"differentiation step: C = A * B with A {m}x{n}x{p}, B {n}x{s}x{p}, then dA = dC * B^H and "
+                f"dB = A^H * dC (hand-written backward), N(0,1) components, FP32 storage")
     return f"{WORKLOAD} T-product: A {m}x{n}x{p} * B {n}x{s}x{p}, N(0,1) components, FP32 storage"
 
 
@@ -304,7 +314,11 @@ def run_ours(args):
     B = torch.from_numpy(B_np).to(dev)
     C = torch.empty((2, m, s, p, 2), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    flops = effective_flops(m, n, s, p)
+    # the differentiation workload's step is a gradient step's T-products: forward, then the
+    # hand-written backward (dA, dB) from a resident dC
+    train = WORKLOAD == "diff"
+    flops = effective_flops(m, n, s, p) + (backward_flops(m, n, s, p) if train else 0.0)
+    dC = torch.randn((2, m, s, p, 2), dtype=torch.float32, device=dev) if train else None
 
     def timed_leg(precision, steps, warmup, trace_steps):
         """Per-step CUDA events around plan.forward (no stage events inside: they
@@ -320,18 +334,23 @@ def run_ours(args):
             flush.zero_()
             evs[i][0].record()
             plan.forward(A, B, C)
+            if train:
+                plan.backward(dC, A, B)
             evs[i][1].record()
         barrier()
         plan.sync()
         step_ms = [a.elapsed_time(b) for a, b in evs]
-        stage_ms = [0.0, 0.0, 0.0]
+        stage_ms = [0.0] * (6 if train else 3)   # forward stages, then backward stages
         if trace_steps:
             plan.set_tracing(True)
             for _ in range(trace_steps):
                 flush.zero_()
                 plan.forward(A, B, C)
                 st = plan.stage_times()
-                for j in range(3):
+                if train:
+                    plan.backward(dC, A, B)
+                    st = list(st) + list(plan.stage_times())
+                for j in range(len(stage_ms)):
                     stage_ms[j] += st[j] / trace_steps
             plan.set_tracing(False)
             plan.sync()
@@ -417,6 +436,18 @@ def run_ours(args):
             "fft_inverse": {"ms": st[2], "bound": "hbm", "achieved": bytes_s3 / (st[2] * 1e-3) / 1e9,
                             "peak": hbm, "unit": "GB/s", "traffic": recorded_traffic("fft_inverse", args.workload)},
         }
+        if train:
+            bb1 = 32.0 * p * (m * n + n * s + m * s)   # forward transforms of A, B, dC
+            bb3 = 32.0 * p * (m * n + n * s)           # inverse transforms of dA, dB
+            bw_flops = (3.0 if args.precision == "bf16x3" else 1.0) * 64.0 * m * n * s * p
+            stages.update({
+                "bwd_fft_forward": {"ms": st[3], "bound": "hbm", "achieved": bb1 / (st[3] * 1e-3) / 1e9,
+                                    "peak": hbm, "unit": "GB/s", "traffic": None},
+                "bwd_products": {"ms": st[4], "bound": "tensor", "achieved": bw_flops / (st[4] * 1e-3) / 1e12,
+                                 "peak": tc_peak, "unit": "TFLOP/s", "traffic": None},
+                "bwd_fft_inverse": {"ms": st[5], "bound": "hbm", "achieved": bb3 / (st[5] * 1e-3) / 1e9,
+                                    "peak": hbm, "unit": "GB/s", "traffic": None},
+            })
         for v in stages.values():
             v["frac"] = v["achieved"] / v["peak"]
         dom = max(stages, key=lambda k: stages[k]["ms"])
@@ -440,7 +471,7 @@ def run_ours(args):
                     "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(A.numel() * 4 + B.numel() * 4),
                     "d2h_bytes_per_step": int(C.numel() * 4)},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": (8 if train else 3) * args.steps,
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:

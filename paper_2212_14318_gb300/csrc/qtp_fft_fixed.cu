@@ -776,7 +776,8 @@ cudaError_t inv_grouped_launch(const FftGroupJob* d_jobs, const int* d_job_of_bl
 template <int P, int FMT>
 cudaError_t fwd_launch(const FftFwdJob* jobs, int njobs, const float2* tw, cudaStream_t st) {
   constexpr size_t smem = smem_for<P, false>();
-  cudaError_t e = cudaFuncSetAttribute(fft_fwd_fixed<P, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> attr_set{0};
+  cudaError_t e = ensure_smem_attr(attr_set, fft_fwd_fixed<P, FMT>, smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
   for (int i = 0; i < njobs; ++i) nb += jobs[i].nblocks;
@@ -798,7 +799,8 @@ cudaError_t fwd_fmt(const FftFwdJob* jobs, int njobs, int fmt, const float2* tw,
 template <int P>
 cudaError_t inv_launch(const FftInvJob* jobs, int njobs, const float2* tw, cudaStream_t st) {
   constexpr size_t smem = smem_for<P, true>();
-  cudaError_t e = cudaFuncSetAttribute(fft_inv_fixed<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> attr_set{0};
+  cudaError_t e = ensure_smem_attr(attr_set, fft_inv_fixed<P>, smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
   for (int i = 0; i < njobs; ++i) nb += jobs[i].nblocks;

@@ -349,7 +349,8 @@ cudaError_t launch_kind(const TcArgs& args, dim3 grid, cudaStream_t st) {
   auto kfn = gemm_tc_kernel<A_MN, B_MN, NP, BN, BK, SPLIT>;
   const size_t smem =
       (size_t)stages_for(NP, BN, BK) * NP * (BM * BK * 2 + BK * BN * 2) + 1024 /*align*/ + 256 /*barriers*/;
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> attr_set{0};
+  cudaError_t e = ensure_smem_attr(attr_set, kfn, smem);
   if (e != cudaSuccess) return e;
   // programmatic dependent launch: the prologue (barriers, TMEM, tensor-map
   // prefetch) overlaps the previous kernel's tail; the producer waits
@@ -366,6 +367,43 @@ cudaError_t launch_kind(const TcArgs& args, dim3 grid, cudaStream_t st) {
   e = cudaLaunchKernelEx(&cfg, kfn, args);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+// Tensor maps and operand roles of one tensor-core problem with tile width bn.
+bool build_args(const TcProblem& pr, bool a_mn, bool b_mn, int bn, int bk, TcArgs& args, char* msg,
+                size_t msglen) {
+  memset(&args, 0, sizeof(args));
+  if (!encode_map(&args.tmA, pr.a_base[0], pr.a_rows[0], pr.a_cols[0], pr.a_ld[0], pr.p, pr.nparts, a_mn, BM,
+                  bk, msg, msglen))
+    return false;
+  if (!encode_map(&args.tmB, pr.b_base[0], pr.b_rows[0], pr.b_cols[0], pr.b_ld[0], pr.p, pr.nparts, b_mn, bn,
+                  bk, msg, msglen))
+    return false;
+  args.M = pr.M; args.N = pr.N; args.K = pr.K; args.p = pr.p; args.nparts = pr.nparts;
+  for (int h = 0; h < 2; ++h)
+    for (int kh = 0; kh < 2; ++kh) {
+      const TcView& va = pr.a[h][kh];
+      const TcView& vb = pr.b[h][kh];
+      args.a_plane[h][kh] = va.plane;
+      args.a_fneg[h][kh] = va.fneg;
+      args.b_plane[h][kh] = vb.plane;
+      args.b_fneg[h][kh] = vb.fneg;
+      // (tau ar + i tau sa ai)(br + i sb bi):
+      //   re += tau ar.br - tau sa sb ai.bi,  im += tau sb ar.bi + tau sa ai.br
+      const float tau = pr.sign[h][kh];
+      const float sa = va.conj ? -1.f : 1.f;
+      const float sb = vb.conj ? -1.f : 1.f;
+      const float c[4] = {tau, -tau * sa * sb, tau * sb, tau * sa};
+      uint32_t mask = 0;
+      for (int q = 0; q < 4; ++q)
+        if (c[q] < 0) mask |= 1u << q;
+      args.negmask[h][kh] = mask;
+    }
+  args.out = pr.out;
+  args.out_hstride = pr.out_hstride;
+  args.out_fstride = pr.out_fstride;
+  args.out_rstride = pr.out_rstride;
+  return true;
 }
 
 }  // namespace
@@ -408,38 +446,39 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
     else if (!strcmp(env, "128s") && pr.nparts == 4) { bn = 128; split = true; }
   }
   const int bk = 16;
+  // The encoded arguments (two tensor maps and the operand roles) depend only
+  // on the problem, the tile choice and the device: repeated calls with the
+  // same spectra buffers reuse them from a small per-thread cache instead of
+  // encoding the tensor maps again.
+  struct CacheEntry {
+    bool valid;
+    int dev, bn;
+    bool split;
+    TcProblem pr;
+    TcArgs args;
+  };
+  static thread_local CacheEntry cache[4];
+  static thread_local int cache_next = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidValue;
   TcArgs args;
-  memset(&args, 0, sizeof(args));
-  if (!encode_map(&args.tmA, pr.a_base[0], pr.a_rows[0], pr.a_cols[0], pr.a_ld[0], pr.p, pr.nparts, a_mn, BM,
-                  bk, msg, msglen))
-    return cudaErrorInvalidValue;
-  if (!encode_map(&args.tmB, pr.b_base[0], pr.b_rows[0], pr.b_cols[0], pr.b_ld[0], pr.p, pr.nparts, b_mn, bn,
-                  bk, msg, msglen))
-    return cudaErrorInvalidValue;
-  args.M = pr.M; args.N = pr.N; args.K = pr.K; args.p = pr.p; args.nparts = pr.nparts;
-  for (int h = 0; h < 2; ++h)
-    for (int kh = 0; kh < 2; ++kh) {
-      const TcView& va = pr.a[h][kh];
-      const TcView& vb = pr.b[h][kh];
-      args.a_plane[h][kh] = va.plane;
-      args.a_fneg[h][kh] = va.fneg;
-      args.b_plane[h][kh] = vb.plane;
-      args.b_fneg[h][kh] = vb.fneg;
-      // (tau ar + i tau sa ai)(br + i sb bi):
-      //   re += tau ar.br - tau sa sb ai.bi,  im += tau sb ar.bi + tau sa ai.br
-      const float tau = pr.sign[h][kh];
-      const float sa = va.conj ? -1.f : 1.f;
-      const float sb = vb.conj ? -1.f : 1.f;
-      const float c[4] = {tau, -tau * sa * sb, tau * sb, tau * sa};
-      uint32_t mask = 0;
-      for (int q = 0; q < 4; ++q)
-        if (c[q] < 0) mask |= 1u << q;
-      args.negmask[h][kh] = mask;
-    }
-  args.out = pr.out;
-  args.out_hstride = pr.out_hstride;
-  args.out_fstride = pr.out_fstride;
-  args.out_rstride = pr.out_rstride;
+  const CacheEntry* hit = nullptr;
+  for (const CacheEntry& ce : cache)
+    if (ce.valid && ce.dev == dev && ce.bn == bn && ce.split == split && memcmp(&ce.pr, &pr, sizeof(pr)) == 0)
+      hit = &ce;
+  if (hit) {
+    args = hit->args;
+  } else {
+    if (!build_args(pr, a_mn, b_mn, bn, bk, args, msg, msglen)) return cudaErrorInvalidValue;
+    CacheEntry& slot = cache[cache_next];
+    cache_next = (cache_next + 1) % 4;
+    slot.valid = true;
+    slot.dev = dev;
+    slot.bn = bn;
+    slot.split = split;
+    slot.pr = pr;
+    slot.args = args;
+  }
   args.err = d_err;
   dim3 grid((pr.N + bn - 1) / bn, (pr.M + BM - 1) / BM, 2 * pr.p);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;

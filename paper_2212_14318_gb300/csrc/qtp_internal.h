@@ -1,6 +1,8 @@
 // Internal declarations of libqtp (CUDA sources only; not part of the ABI).
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,6 +17,21 @@
 #define QTP_DEVERR_TIMEOUT_ACC 3    // epilogue gave up waiting for the accumulator
 
 namespace qtp {
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per device for one
+// kernel: `mask` (a static of the kernel's launcher) holds a bit per device
+// already set.  Setting it before every launch cost host time that small
+// products see inside their step.
+template <class K>
+inline cudaError_t ensure_smem_attr(std::atomic<unsigned long long>& mask, K kernel, size_t smem) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && ((mask.load(std::memory_order_acquire) >> dev) & 1ull)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev < 64) mask.fetch_or(1ull << dev, std::memory_order_acq_rel);
+  return e;
+}
 
 // Programmatic dependent launch: a kernel launched with
 // cudaLaunchAttributeProgrammaticStreamSerialization may start while the
