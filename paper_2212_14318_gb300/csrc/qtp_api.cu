@@ -450,6 +450,17 @@ void trace(const qtp_plan* pl, int i, cudaStream_t st) {
 
 qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, float* C, char* ws,
                         cudaStream_t st) {
+  if (fused_small_eligible(pl->m, pl->n, pl->s, pl->p)) {
+    // all three steps in one CTA (qtp_fused_small.cu); traced as the products stage
+    trace(pl, 0, st);
+    trace(pl, 1, st);
+    QTP_CUDA(launch_fused_small((const float2*)A, (const float2*)B, (float2*)C, pl->m, pl->n, pl->s, pl->p,
+                                pl->d_tw, st),
+             "fused small product");
+    trace(pl, 2, st);
+    trace(pl, 3, st);
+    return QTP_OK;
+  }
   const int fmt = spec_format(pl->precision);
   const FwdLayout L = fwd_layout(pl);
   FftFwdJob jobs[2];

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "../../include/qtp.h"
 
@@ -32,6 +33,15 @@ inline cudaError_t ensure_smem_attr(std::atomic<unsigned long long>& mask, K ker
   if (e == cudaSuccess && dev < 64) mask.fetch_or(1ull << dev, std::memory_order_acq_rel);
   return e;
 }
+
+// Whole small products in one CTA (qtp_fused_small.cu): all three spectra of
+// the product in shared memory, FP32 arithmetic.
+constexpr int kFusedMaxP = 64;
+constexpr size_t kFusedSmemMax = 96 * 1024;
+size_t fused_small_smem(int m, int n, int s, int p);
+bool fused_small_eligible(int m, int n, int s, int p);  // false when QTP_NO_FUSED is set
+cudaError_t launch_fused_small(const float2* A, const float2* B, float2* C, int m, int n, int s, int p,
+                               const float2* tw, cudaStream_t st);
 
 // Programmatic dependent launch: a kernel launched with
 // cudaLaunchAttributeProgrammaticStreamSerialization may start while the

@@ -59,14 +59,21 @@ def test_mixed_batch_matches_oracle(precision, graph):
 
 
 def test_batch_matches_single_product_entry_point():
+    """Same split-BF16 arithmetic through both entry points (the single-product
+    path's one-CTA FP32 route for tiny products is switched off here)."""
+    import os
     from paper_2212_14318_gb300 import qtp
     shapes = MIXED[:6]
     As = [to_dev(synth.quat_normal(m, n, p, 50 + i)) for i, (m, n, s, p) in enumerate(shapes)]
     Bs = [to_dev(synth.quat_normal(n, s, p, 60 + i)) for i, (m, n, s, p) in enumerate(shapes)]
     Cs = qtp.BatchPlan(shapes, "bf16x3").forward(As, Bs)
-    for i, (m, n, s, p) in enumerate(shapes):
-        ref = qtp.Plan(m, n, s, p, "bf16x3").forward(As[i], Bs[i])
-        assert rel_fro(to_host(Cs[i]), to_host(ref)) <= 1e-6
+    os.environ["QTP_NO_FUSED"] = "1"
+    try:
+        for i, (m, n, s, p) in enumerate(shapes):
+            ref = qtp.Plan(m, n, s, p, "bf16x3").forward(As[i], Bs[i])
+            assert rel_fro(to_host(Cs[i]), to_host(ref)) <= 1e-6
+    finally:
+        del os.environ["QTP_NO_FUSED"]
 
 
 def test_batch_workload_4096_products_each_checked():

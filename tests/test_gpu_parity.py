@@ -179,3 +179,27 @@ def test_batched_large_p(m, n, s, p):
     for i, (a, b, c, q) in enumerate(shapes):
         ref = Q.alg51(planes_to_comp(As[i]), planes_to_comp(Bs[i]))
         assert_close(to_host(Cs[i]), ref, REL_TOL, ELEM_TOL, f"batched product {i} p={q}")
+
+
+# Products small enough for the one-CTA path (all spectra in shared memory):
+# both that path and the three-launch path (QTP_NO_FUSED=1) against the oracle.
+FUSED_SHAPES = [(1, 1, 1, 1), (3, 5, 7, 1), (5, 3, 4, 2), (8, 8, 8, 16), (17, 9, 13, 3), (4, 4, 4, 64),
+                (8, 3, 5, 31), (4, 12, 9, 12)]
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("m,n,s,p", FUSED_SHAPES)
+def test_small_fused_and_staged(fused, precision, m, n, s, p):
+    import os
+    qtp = _qtp()
+    A, B = _inputs(m, n, s, p, seed=3 * m + n + 5 * p)
+    if not fused:
+        os.environ["QTP_NO_FUSED"] = "1"
+    try:
+        plan = qtp.Plan(m, n, s, p, precision)
+        C = to_host(plan.forward(to_dev(A), to_dev(B)))
+        plan.sync()
+    finally:
+        os.environ.pop("QTP_NO_FUSED", None)
+    assert_close(C, _oracle(A, B), REL_TOL, ELEM_TOL, f"{'fused' if fused else 'staged'} {m}x{n}x{s}x{p}")
