@@ -360,6 +360,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     plan, total_ms, stage_ms = timed_leg(args.precision, args.steps, args.warmup, trace_steps=min(args.steps, 200))
+    lc = plan.launch_count()   # kernel launches per forward / backward call
     clocks = sampler.stop()
     total_ms = reduce_max(total_ms, world, dev)
     ms_per_step = total_ms / args.steps
@@ -471,7 +472,7 @@ def run_ours(args):
                     "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(A.numel() * 4 + B.numel() * 4),
                     "d2h_bytes_per_step": int(C.numel() * 4)},
-            "gpu_launches": (8 if train else 3) * args.steps,
+            "gpu_launches": (lc[0] + (lc[1] if train else 0)) * args.steps,
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -99,6 +99,15 @@ QTP_API qtp_status qtp_plan_destroy(qtp_plan* plan);
  * rule, 1 = 256 wide, 2 = 128 wide, 3 = 128 wide with split accumulators. */
 QTP_API qtp_status qtp_plan_get_tiles(const qtp_plan* plan, int* tiles3);
 
+/* Kernel launches that one qtp_forward call (*forward) and one qtp_backward
+ * call with both outputs requested (*backward) issue for this plan: 3 and 5
+ * (Steps 1, 2, 3 of Algorithm 5.1; the backward transforms A and B, then dC,
+ * forms dA and dB, and transforms both back in one launch), or 1 forward
+ * launch for products small enough to run whole in one CTA.  Library
+ * extension with no counterpart in the paper; for launch accounting.
+ * Errors: QTP_ERR_INVALID_ARG for a NULL plan or output pointer. */
+QTP_API qtp_status qtp_plan_launch_count(const qtp_plan* plan, int* forward, int* backward);
+
 /* Bytes of device workspace qtp_forward needs: the spectra of A and B in the
  * GEMM operand format of the plan's precision plus the FP32 spectrum of C. */
 QTP_API qtp_status qtp_workspace_size(const qtp_plan* plan, size_t* bytes);

@@ -568,6 +568,15 @@ qtp_status qtp_plan_get_tiles(const qtp_plan* pl, int* tiles3) {
   return QTP_OK;
 }
 
+qtp_status qtp_plan_launch_count(const qtp_plan* pl, int* forward, int* backward) {
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if (!forward || !backward) return fail(QTP_ERR_INVALID_ARG, "output pointer is NULL");
+  *forward = fused_small_eligible(pl->m, pl->n, pl->s, pl->p) ? 1 : 3;
+  *backward = 5;
+  return QTP_OK;
+}
+
 qtp_status qtp_plan_destroy(qtp_plan* pl) {
   if (!pl) return QTP_OK;
   qtp_plan_set_tracing(pl, 0);

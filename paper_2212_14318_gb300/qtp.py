@@ -31,6 +31,7 @@ SIGNATURES = {
     "qtp_plan_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, ctypes.c_uint]),
     "qtp_plan_destroy": (_i, [_vp]),
     "qtp_plan_get_tiles": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "qtp_plan_launch_count": (_i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "qtp_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "qtp_backward_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "qtp_forward": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -182,6 +183,12 @@ class Plan:
         _check(lib().qtp_backward(self._h, _ptr(dC), _ptr(A), _ptr(B), _ptr(dA), _ptr(dB), _ptr(ws),
                                   ws.numel() * ws.element_size(), _stream(stream)), "qtp_backward")
         return dA, dB
+
+    def launch_count(self):
+        """(forward, backward) kernel launches per call; see qtp_plan_launch_count."""
+        f, b = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().qtp_plan_launch_count(self._h, ctypes.byref(f), ctypes.byref(b)), "qtp_plan_launch_count")
+        return f.value, b.value
 
     def tiles(self):
         """Tensor-core tile choice per product kind (forward, dA, dB); see qtp_plan_get_tiles."""

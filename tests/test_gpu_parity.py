@@ -203,3 +203,15 @@ def test_small_fused_and_staged(fused, precision, m, n, s, p):
     finally:
         os.environ.pop("QTP_NO_FUSED", None)
     assert_close(C, _oracle(A, B), REL_TOL, ELEM_TOL, f"{'fused' if fused else 'staged'} {m}x{n}x{s}x{p}")
+
+
+def test_launch_count_reports_the_route():
+    import os
+    qtp = _qtp()
+    assert qtp.Plan(8, 8, 8, 16, "bf16x3").launch_count() == (1, 5)      # one-CTA route
+    assert qtp.Plan(64, 48, 80, 128, "bf16x3").launch_count() == (3, 5)  # Steps 1, 2, 3
+    os.environ["QTP_NO_FUSED"] = "1"
+    try:
+        assert qtp.Plan(8, 8, 8, 16, "fp32").launch_count() == (3, 5)
+    finally:
+        del os.environ["QTP_NO_FUSED"]
