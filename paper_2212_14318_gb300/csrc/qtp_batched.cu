@@ -278,7 +278,8 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
     P.tiles_n = (tcols + BNt - 1) / BNt;
     P.lda = (int)spec_ld_of(fmt, q.n);
     P.ldb = (int)spec_ld_of(fmt, q.s);
-    tiles += (long long)P.tiles_m * P.tiles_n * 2 * q.p;
+    // tensor cores: a tile computes both output halves; FP32: one tile per half
+    tiles += (long long)P.tiles_m * P.tiles_n * (tc ? 1 : 2) * q.p;
     b->h_probs.push_back(P);
     b->prod_of_prob.push_back(idx);
   }

@@ -1,23 +1,27 @@
 // Per-frequency products of Algorithm 5.1 Step 2 for a batch of products with
 // uneven (m, n, s, p): one persistent tcgen05 launch (split-BF16, forward).
 //
+// A tile is (frequency f, 128-row tile, 64-column tile) of one product and
+// computes both output halves,
+//   C1(f) = A1(f) B1(f) - A2(f) conj(B2(-f)),  C2(f) = A1(f) B2(f) + A2(f) conj(B1(-f)),
+// so each K step loads the A tile (plane kh at f) once for both halves and
+// one B tile per half (B's two planes at f for kh = 0, at -f for kh = 1):
+// operand fetch, not MMA, bounds these small products.  The MMA width is the
+// tile's valid columns rounded up to 16.  A product with trans set is computed
+// as C^T = B^T A^T, rows over s and columns over m (the larger of m and s fills
+// the MMA's 128 rows): B's MN-major spectra are then the A operands (one per
+// half) and A's K-major spectra the shared B operand, and the epilogue writes
+// C^T's rows, which are C's contiguous columns.
+//
 // All tiles of all products form one index space; product g owns
-// [tile_begin_g, tile_begin_g + tiles_m * tiles_n * 2 * p_g), ordered
-// (frequency, output half, row tile, column tile).  A tile is 128 rows by up
-// to 128 columns; its MMA width is the tile's valid columns rounded up to 16,
-// so narrow products do not pay for MMAs over padding.  A product with
-// trans set is computed as C^T = B^T A^T, rows over s and columns over m: the
-// larger of m and s fills the MMA's 128 rows (B's MN-major spectra are then
-// the MN-major A operand and A's K-major spectra the K-major B operand; the
-// epilogue writes C^T's rows, which are C's contiguous columns).  CTA i (one
-// per SM) takes
-// tiles i, i + grid, i + 2 grid, ...  Roles as in the single-product kernel:
-// warp 0 issues TMA, warp 1 issues tcgen05.mma, warps 2-5 drain TMEM.  Here
-// the TMA producer runs straight on from one tile's K loop into the next
-// tile's (the 6-stage ring never drains between tiles) and TMEM holds two
-// accumulator pairs, so the epilogue of one tile overlaps the MMAs of the
-// next.  Each product has its own two tensor maps, kept in device memory and
-// acquired for the async proxy before use.  All waits are bounded.
+// [tile_begin_g, tile_begin_g + tiles_m * tiles_n * p_g), ordered (frequency,
+// row tile, column tile).  CTA i (one per SM) takes tiles i, i + grid, ...
+// Warp 0 issues TMA, warp 1 tcgen05.mma, warps 2-5 drain TMEM; the 4-stage
+// ring runs on across tiles, and TMEM holds two sets of the four accumulators
+// (C1 and C2, real and imaginary, 64 columns each), so the epilogue of one
+// tile overlaps the MMAs of the next.  Each product has its own two tensor
+// maps in device memory, acquired for the async proxy before use.  All waits
+// are bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdio.h>
@@ -33,14 +37,13 @@ namespace {
 using namespace tcdev;
 
 constexpr int GBM = kGroupTcBM;          // 128 rows
-constexpr int GBN = kGroupTcBN;          // 128 complex columns
+constexpr int GBN = kGroupTcBN;          // 64 complex columns
 constexpr int GBK = 16;                  // K per stage
-constexpr int GSTAGES = 6;
-constexpr int G_A_TILE = GBM * GBK * 2;  // 4 KB per bf16 part
-constexpr int G_B_TILE = GBK * GBN * 2;  // 4 KB per bf16 part
-static_assert(G_A_TILE == G_B_TILE, "either tile region holds either operand");
+constexpr int GSTAGES = 4;
+constexpr int G_SLOT = 128 * GBK * 2;    // 4 KB: one bf16 part of a 128 x 16 (or 16 x 128) operand tile
 constexpr int kGThreads = 192;
-constexpr uint32_t G_TMEM_COLS = 512;    // 2 buffers x (re, im) x 128 columns
+constexpr uint32_t G_TMEM_COLS = 512;    // 2 buffers x (C1 re, C1 im, C2 re, C2 im) x 64 columns
+static_assert(4 * GBN * 2 <= (int)G_TMEM_COLS, "TMEM budget");
 
 // Operand roles of the forward product per (output half h, K half kh): A and B
 // planes, whether B is read at frequency -f, and which of the four real
@@ -55,7 +58,7 @@ struct GViews {
 __device__ __forceinline__ uint32_t gv_bit(uint32_t bits, int h, int kh) { return (bits >> (2 * h + kh)) & 1u; }
 
 struct GTile {
-  int g, f, h, mt, nt;
+  int g, f, mt, nt;
 };
 
 // Tile t of the global index space.  A CTA visits increasing t, so its
@@ -69,24 +72,24 @@ __device__ __forceinline__ GTile decode_tile(const GroupProblem* __restrict__ pr
   r.nt = (int)(local % P.tiles_n);
   local /= P.tiles_n;
   r.mt = (int)(local % P.tiles_m);
-  local /= P.tiles_m;
-  r.h = (int)(local & 1);
-  r.f = (int)(local >> 1);
+  r.f = (int)(local / P.tiles_m);
   return r;
 }
 
+// Stage s holds, per bf16 part q, three 4 KB slots: [shared operand (A's
+// spectra)][operand of half 0][operand of half 1], each role's NP parts
+// consecutive, so a role's part q sits at role_base + q * G_SLOT.
 template <int NP>
 __global__ void __launch_bounds__(kGThreads, 1)
     gemm_tc_grouped_kernel(const GroupProblem* __restrict__ probs, int nprobs, long long total_tiles, char* ws,
                            int* err, const GViews V) {
+  constexpr int STAGE = 3 * NP * G_SLOT;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint32_t tmem_base_slot;
   __shared__ int abort_flag;
 
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const uint32_t sA = base;
-  const uint32_t sB = base + GSTAGES * NP * G_A_TILE;
-  const uint32_t stg_base = sB + GSTAGES * NP * G_B_TILE;  // 4 epilogue staging areas
+  const uint32_t stg_base = base + GSTAGES * STAGE;  // 4 epilogue staging areas
   const uint32_t bars = stg_base + 4 * kStgBytes;
   const uint32_t full = bars, empty = bars + 8 * GSTAGES;
   const uint32_t acc_full = bars + 16 * GSTAGES;      // 2 barriers
@@ -148,11 +151,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
           }
         }
         const int nkb = (P.K + GBK - 1) / GBK;
-        // MMA width of this tile, and the 64-column boxes of the MN-major operand
-        const int ncols = P.trans ? P.M : P.N;
-        const int nw = min(GBN, ncols - T.nt * GBN);
-        const int nb64 = P.trans ? 2 : (nw + 63) / 64;
-        const uint32_t tx_bytes = (uint32_t)(NP * (G_A_TILE + (P.trans ? G_B_TILE : nb64 * (G_B_TILE / 2))));
+        // plain: A tile 128 rows (two 64-row boxes), B tiles one 64-column box;
+        // transposed: B tiles 128 rows of s (two 64-column boxes), A tile 64 rows
+        const uint32_t tx_bytes = (uint32_t)(NP * (P.trans ? 2 * G_SLOT + G_SLOT / 2 : G_SLOT + G_SLOT));
         for (int kk = 0; kk < 2 * nkb; ++kk, ++it) {
           const int kh = kk / nkb;
           const int k0 = (kk - kh * nkb) * GBK;
@@ -169,21 +170,29 @@ __global__ void __launch_bounds__(kGThreads, 1)
             break;
           }
           mbar_expect_tx(full + 8 * s, tx_bytes);
-          const int ga = T.f;
-          const int gb = gv_bit(V.b_fneg, T.h, kh) ? (P.p - T.f) % P.p : T.f;
-          const int pa = (int)gv_bit(V.a_plane, T.h, kh) * NP, pb = (int)gv_bit(V.b_plane, T.h, kh) * NP;
-          // A's spectra (K-major rows of m) and B's (MN-major columns of s)
-          // go to the MMA's A and B tiles, or the other way round when trans
-          const uint32_t tk = P.trans ? sB : sA;   // K-major tile: 128 rows of m
-          const uint32_t tm = P.trans ? sA : sB;   // MN-major tile: 64-column boxes of s
-          const int rowA = (P.trans ? T.nt : T.mt) * GBM;
-          const int colB = (P.trans ? T.mt : T.nt) * GBN;
+          // A plane kh at f (both halves); B planes b_plane[h][kh] at f or -f
+          const int gb = gv_bit(V.b_fneg, 0, kh) ? (P.p - T.f) % P.p : T.f;
+          const int pa = (int)gv_bit(V.a_plane, 0, kh) * NP;
+          const int pb0 = (int)gv_bit(V.b_plane, 0, kh) * NP, pb1 = (int)gv_bit(V.b_plane, 1, kh) * NP;
+          const uint32_t st0 = base + (uint32_t)s * STAGE;
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
-            const uint32_t off = (uint32_t)(s * NP + q) * G_A_TILE;  // G_A_TILE == G_B_TILE
-            tma_load_4d(tk + off, tmA, full + 8 * s, k0, rowA, ga, pa + q);
-            tma_load_4d(tm + off, tmB, full + 8 * s, colB, k0, gb, pb + q);
-            if (nb64 == 2) tma_load_4d(tm + off + 128u * GBK, tmB, full + 8 * s, colB + 64, k0, gb, pb + q);
+            const uint32_t sh = st0 + (uint32_t)q * G_SLOT;
+            const uint32_t h0 = sh + NP * G_SLOT, h1 = h0 + NP * G_SLOT;
+            if (P.trans) {
+              const int c = T.mt * GBM;  // 128 columns of s
+              tma_load_4d(h0, tmB, full + 8 * s, c, k0, gb, pb0 + q);
+              tma_load_4d(h0 + 128u * GBK, tmB, full + 8 * s, c + 64, k0, gb, pb0 + q);
+              tma_load_4d(h1, tmB, full + 8 * s, c, k0, gb, pb1 + q);
+              tma_load_4d(h1 + 128u * GBK, tmB, full + 8 * s, c + 64, k0, gb, pb1 + q);
+              tma_load_4d(sh, tmA, full + 8 * s, k0, T.nt * GBN, T.f, pa + q);
+            } else {
+              const int r = T.mt * GBM;  // 128 rows of m
+              tma_load_4d(sh, tmA, full + 8 * s, k0, r, T.f, pa + q);
+              tma_load_4d(sh + 64u * 32u, tmA, full + 8 * s, k0, r + 64, T.f, pa + q);
+              tma_load_4d(h0, tmB, full + 8 * s, T.nt * GBN, k0, gb, pb0 + q);
+              tma_load_4d(h1, tmB, full + 8 * s, T.nt * GBN, k0, gb, pb1 + q);
+            }
           }
         }
       }
@@ -195,9 +204,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      // base descriptors of the A / B tiles in either orientation
-      const uint64_t da0_k = part_desc<false, GBK>(sA, 0), da0_mn = part_desc<true, GBK>(sA, 0);
-      const uint64_t db0_k = part_desc<false, GBK>(sB, 0), db0_mn = part_desc<true, GBK>(sB, 0);
+      // base descriptors of the three slots of stage 0, K-major and MN-major
+      const uint64_t dsh_k = part_desc<false, GBK>(base, 0);
+      const uint64_t dh0_mn = part_desc<true, GBK>(base + NP * G_SLOT, 0);
+      const uint64_t dh1_mn = part_desc<true, GBK>(base + 2 * NP * G_SLOT, 0);
+      const uint32_t step = (uint32_t)(G_SLOT >> 4);
       long long it = 0;
       int lt = 0, cur = 0;
       bool ok = true;
@@ -209,8 +220,6 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const int ncols = tr ? P.M : P.N;
         const int nw = (min(GBN, ncols - T.nt * GBN) + 15) & ~15;
         const uint32_t idesc = make_idesc(tr, !tr, nw);
-        const uint64_t da0 = tr ? da0_mn : da0_k;
-        const uint64_t db0 = tr ? db0_k : db0_mn;
         const uint32_t nmask = tr ? V.negmask_t : V.negmask;
         const int nkb = (K + GBK - 1) / GBK;
         const int buf = lt & 1;
@@ -222,9 +231,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
           break;
         }
         fence_after();
-        const uint32_t d_re = tmem + (uint32_t)(buf * 2 * GBN);
-        const uint32_t d_im = d_re + (uint32_t)GBN;
-        uint32_t acc_re = 0, acc_im = 0;
+        const uint32_t d0 = tmem + (uint32_t)(buf * 4 * GBN);  // C1 re, C1 im, C2 re, C2 im
+        uint32_t a0r = 0, a0i = 0, a1r = 0, a1i = 0;
         for (int kk = 0; kk < 2 * nkb; ++kk, ++it) {
           const int kh = kk / nkb;
           const int s = (int)(it % GSTAGES);
@@ -236,12 +244,20 @@ __global__ void __launch_bounds__(kGThreads, 1)
             break;
           }
           fence_after();
-          const uint32_t neg = nmask >> (4 * (2 * T.h + kh));
-          // stage descriptors: base descriptor advanced in its start-address field
-          const uint64_t da = da0 + (uint64_t)((uint32_t)(s * NP * G_A_TILE) >> 4);
-          const uint64_t db = db0 + (uint64_t)((uint32_t)(s * NP * G_B_TILE) >> 4);
-          complex_kstep<NP, false>(da, db, (uint32_t)(G_A_TILE >> 4), (uint32_t)(G_B_TILE >> 4), idesc, neg, d_re,
-                                   d_im, d_re, d_im, acc_re, acc_im, acc_re, acc_im);
+          const uint32_t neg0 = nmask >> (4 * kh), neg1 = nmask >> (4 * (2 + kh));
+          const uint64_t so = (uint64_t)((uint32_t)(s * STAGE) >> 4);  // stage offset in descriptor units
+          if (tr) {  // A operands: B's spectra per half (MN-major); B operand: A's spectra (K-major, shared)
+            complex_kstep<NP, false>(dh0_mn + so, dsh_k + so, step, step, idesc, neg0, d0, d0 + GBN, d0, d0 + GBN,
+                                     a0r, a0i, a0r, a0i);
+            complex_kstep<NP, false>(dh1_mn + so, dsh_k + so, step, step, idesc, neg1, d0 + 2 * GBN, d0 + 3 * GBN,
+                                     d0 + 2 * GBN, d0 + 3 * GBN, a1r, a1i, a1r, a1i);
+          } else {   // A operand: A's spectra (K-major, shared); B operands: B's spectra per half (MN-major)
+            const uint64_t db1 = dh1_mn + so;
+            complex_kstep<NP, false>(dsh_k + so, dh0_mn + so, step, step, idesc, neg0, d0, d0 + GBN, d0, d0 + GBN,
+                                     a0r, a0i, a0r, a0i);
+            complex_kstep<NP, false>(dsh_k + so, db1, step, step, idesc, neg1, d0 + 2 * GBN, d0 + 3 * GBN,
+                                     d0 + 2 * GBN, d0 + 3 * GBN, a1r, a1i, a1r, a1i);
+          }
           mma_commit(empty + 8 * s);
         }
         if (!ok) break;
@@ -271,30 +287,33 @@ __global__ void __launch_bounds__(kGThreads, 1)
         break;
       }
       fence_after();
-      float2* out = reinterpret_cast<float2*>(ws + P.out_off) + (long long)T.h * P.p * P.M * P.N +
-                    (long long)T.f * P.M * P.N;
-      const uint32_t tb = tmem + (uint32_t)(buf * 2 * GBN) + lane_off;
       const int row0 = T.mt * GBM + q * 32;  // this warp's first accumulator row
       const int ncols = P.trans ? P.M : P.N;
       const int nw = min(GBN, ncols - T.nt * GBN);
 #pragma unroll 1
-      for (int c0 = 0; c0 < nw; c0 += 32) {
-        uint32_t re[32], im[32];
-        tmem_ld32(tb + (uint32_t)c0, re);
-        tmem_ld32(tb + (uint32_t)(GBN + c0), im);
-        const int col0 = T.nt * GBN + c0;
-        if (P.trans) {
-          // accumulator row = column of C (index into s), column = row of C
-          // (index into m): lane-consecutive stores along C's rows
-          const int cs = row0 + lane;
-          if (cs < P.N) {
-            const int nj = min(32, P.M - col0);
+      for (int h = 0; h < 2; ++h) {
+        float2* out = reinterpret_cast<float2*>(ws + P.out_off) + (long long)h * P.p * P.M * P.N +
+                      (long long)T.f * P.M * P.N;
+        const uint32_t tb = tmem + (uint32_t)(buf * 4 * GBN + h * 2 * GBN) + lane_off;
+#pragma unroll 1
+        for (int c0 = 0; c0 < nw; c0 += 32) {
+          uint32_t re[32], im[32];
+          tmem_ld32(tb + (uint32_t)c0, re);
+          tmem_ld32(tb + (uint32_t)(GBN + c0), im);
+          const int col0 = T.nt * GBN + c0;
+          if (P.trans) {
+            // accumulator row = column of C (index into s), column = row of C
+            // (index into m): lane-consecutive stores along C's rows
+            const int cs = row0 + lane;
+            if (cs < P.N) {
+              const int nj = min(32, P.M - col0);
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < nj) out[(long long)(col0 + j) * P.N + cs] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+              for (int j = 0; j < 32; ++j)
+                if (j < nj) out[(long long)(col0 + j) * P.N + cs] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+            }
+          } else {
+            store_chunk(stg, re, im, out + (long long)row0 * P.N + col0, P.N, P.M - row0, P.N - col0, lane);
           }
-        } else {
-          store_chunk(stg, re, im, out + (long long)row0 * P.N + col0, P.N, P.M - row0, P.N - col0, lane);
         }
       }
       fence_before();
@@ -335,8 +354,8 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 
 // Spectra tensor [plane][part][f][rows][ld] (bf16) as a 4-D tensor map for
-// the grouped kernel: box (16, 128) with the 32-byte swizzle for the K-major A
-// operand, (64, 16) with the 128-byte swizzle for the MN-major B operand.
+// the grouped kernel: box (16, 64) with the 32-byte swizzle for A's K-major
+// spectra, (64, 16) with the 128-byte swizzle for B's MN-major spectra.
 bool encode_group_map(void* tm, const void* base, int rows, int cols, int ld, int p, int nparts, bool mn_major,
                       char* msg, size_t msglen) {
   EncodeTiledFn enc = encode_fn();
@@ -346,7 +365,7 @@ bool encode_group_map(void* tm, const void* base, int rows, int cols, int ld, in
   }
   cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)p, (cuuint64_t)(2 * nparts)};
   cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * rows, (cuuint64_t)ld * 2 * rows * p};
-  cuuint32_t box[4] = {mn_major ? 64u : (cuuint32_t)GBK, mn_major ? (cuuint32_t)GBK : (cuuint32_t)GBM, 1, 1};
+  cuuint32_t box[4] = {mn_major ? 64u : (cuuint32_t)GBK, mn_major ? (cuuint32_t)GBK : 64u, 1, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(reinterpret_cast<CUtensorMap*>(tm), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base),
                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -363,7 +382,7 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
                                    char* ws, int* d_err, int num_ctas, cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;
   const int np = nparts == 4 ? 4 : 2;
-  const size_t smem = (size_t)GSTAGES * np * (G_A_TILE + G_B_TILE) + 4 * kStgBytes + 1024 + 256;
+  const size_t smem = (size_t)GSTAGES * 3 * np * G_SLOT + 4 * kStgBytes + 1024 + 256;
   const int grid = (int)(total_tiles < num_ctas ? total_tiles : num_ctas);
   // Forward product (Thm 5.1): C1 = A1 B1 - A2 conj(B2(-f)), C2 = A1 B2 + A2 conj(B1(-f)).
   // (tau ar + i tau ai)(br + i sb bi): re += tau ar.br - tau sb ai.bi, im += tau sb ar.bi + tau ai.br
@@ -393,6 +412,9 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
       V.negmask |= mask << (4 * e);
       V.negmask_t |= mask_t << (4 * e);
     }
+  // the kernel loads one A tile for both halves and reads B at one frequency per K half
+  for (int kh = 0; kh < 2; ++kh)
+    if (a_plane[0][kh] != a_plane[1][kh] || b_conj[0][kh] != b_conj[1][kh]) return cudaErrorInvalidValue;
   cudaError_t e;
   if (np == 4) {
     e = cudaFuncSetAttribute(gemm_tc_grouped_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -193,9 +193,10 @@ struct TcProblem {
 
 // Grouped (batched) per-frequency products, forward only: product g reads its
 // spectra at workspace offsets and writes C_hat at out_off.  Tiles of all
-// products form one index space; product g owns tiles
-// [tile_begin, tile_begin + tiles_m * tiles_n * 2 * p), ordered (f, h, mt, nt)
-// with nt fastest.
+// products form one index space; product g owns tiles [tile_begin, tile_begin
+// + tiles_m * tiles_n * p) ordered (f, mt, nt) on the tensor cores (a tile
+// computes both output halves), and [tile_begin, tile_begin + tiles_m *
+// tiles_n * 2 * p) ordered (f, h, mt, nt) in FP32; nt fastest.
 struct GroupProblem {
   long long tile_begin;
   long long sa_off, sb_off, out_off;  // byte offsets in the workspace
@@ -213,7 +214,7 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
 cudaError_t launch_gemm_simt_grouped(const GroupProblem* d_probs, const int* d_prob_of_tile, long long total_tiles,
                                      char* ws, cudaStream_t st);
 // Tile shapes of the grouped kernels (rows x complex columns).
-constexpr int kGroupTcBM = 128, kGroupTcBN = 128;
+constexpr int kGroupTcBM = 128, kGroupTcBN = 64;
 constexpr int kGroupSimtBM = 64, kGroupSimtBN = 128;
 // Tensor map of a spectra tensor for the grouped tensor-core kernel (K-major A
 // or MN-major B), written to host memory at *tm (128 bytes).
