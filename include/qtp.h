@@ -128,7 +128,10 @@ QTP_API qtp_status qtp_backward_workspace_size(const qtp_plan* plan, size_t* byt
  *   Step 3 (eq. ifft-C): inverse FFT of every tube of C1, C2 with scale 1/p.
  * A: 2*m*n*p complex, B: 2*n*s*p complex, C: 2*m*s*p complex (layout above).
  * C may not alias A, B or the workspace.  workspace_bytes must be at least
- * qtp_workspace_size(plan).  Asynchronous on stream. */
+ * qtp_workspace_size(plan).  Asynchronous on stream.  Products small enough
+ * to hold A, B and all three spectra in 96 KB of shared memory (p <= 64) run
+ * the three steps in one CTA with FP32 arithmetic, whatever the plan's
+ * precision (environment variable QTP_NO_FUSED=1: the three launches). */
 QTP_API qtp_status qtp_forward(const qtp_plan* plan, const float* A, const float* B, float* C,
                        void* workspace, size_t workspace_bytes, void* stream);
 
@@ -174,9 +177,10 @@ typedef struct qtp_batch_plan qtp_batch_plan;
  * size (the order the grouped kernels walk them; results are unaffected),
  * lays out every product's spectra in one workspace, builds the device job
  * and tile tables and the twiddle tables of every distinct p, and
- * synchronises the device.  Each forward call runs three grouped launches
- * (all tube FFTs of A and B; all per-frequency products in one persistent
- * tensor-core launch, or one FP32 launch; all inverse FFTs), replayed from a
+ * synchronises the device.  Each forward call runs grouped launches (the
+ * tube FFTs of A and B, one launch per distinct p; all per-frequency products
+ * in one persistent tensor-core launch, or one FP32 launch; the inverse FFTs,
+ * one launch per distinct p), replayed from a
  * CUDA graph captured on the first call (and again after the workspace
  * pointer changes) on a stream the plan owns, ordered after and before the
  * caller's stream with events. */
@@ -192,8 +196,9 @@ QTP_API qtp_status qtp_batch_workspace_size(const qtp_batch_plan* plan, size_t* 
 QTP_API qtp_status qtp_forward_batched(qtp_batch_plan* plan, const float* const* A, const float* const* B,
                                        float* const* C, void* workspace, size_t workspace_bytes, void* stream);
 
-/* Tracing of batched calls: four events around the three grouped launches;
- * ms3 receives their durations for the last traced call (waits for it). */
+/* Tracing of batched calls: four events around the three stages (forward
+ * transforms, products, inverse transforms); ms3 receives their durations for
+ * the last traced call (waits for it). */
 QTP_API qtp_status qtp_batch_plan_set_tracing(qtp_batch_plan* plan, int enable);
 QTP_API qtp_status qtp_batch_stage_times(const qtp_batch_plan* plan, float* ms3);
 
@@ -208,8 +213,9 @@ QTP_API qtp_status qtp_plan_sync(const qtp_plan* plan, void* stream);
 /* Tracing.  While enabled, every qtp_forward / qtp_forward_host /
  * qtp_backward call records four CUDA events on its stream: before Step 1,
  * after Step 1 (tube FFTs), after Step 2 (per-frequency products) and after
- * Step 3 (inverse FFTs).  qtp_plan_stage_times waits for the events of the
- * last traced call and writes the three stage durations (ms) to ms3[0..2].
+ * Step 3 (inverse FFTs); a one-CTA forward counts entirely as Step 2.
+ * qtp_plan_stage_times waits for the events of the last traced call and
+ * writes the three stage durations (ms) to ms3[0..2].
  * Enabling creates the events (no device memory); disabling destroys them. */
 QTP_API qtp_status qtp_plan_set_tracing(qtp_plan* plan, int enable);
 QTP_API qtp_status qtp_plan_stage_times(const qtp_plan* plan, float* ms3);

@@ -1,6 +1,7 @@
 // Batched T-products (qtp_batch_plan_*, qtp_forward_batched): thousands of
 // independent products C_i = A_i * B_i of uneven (m, n, s, p), each by
-// Algorithm 5.1, in three grouped launches replayed from a CUDA graph.
+// Algorithm 5.1, in grouped launches (the transforms one per tube length, the
+// products one) replayed from a CUDA graph.
 //
 //   1. fft_fwd_grouped  - every tube of every A_i and B_i (Step 1): one
 //                         launch per distinct tube length p
@@ -117,7 +118,7 @@ void trace(qtp_batch_plan* b, int i, cudaStream_t st, bool capturing) {
   else cudaEventRecord(b->ev[i], st);
 }
 
-// The three grouped launches of one forward call, on stream st.
+// The grouped launches of one forward call, on stream st.
 qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing) {
   trace(b, 0, st, capturing);
   for (const FftRange& r : b->fwd_ranges)

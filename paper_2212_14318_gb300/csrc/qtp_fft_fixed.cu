@@ -1,13 +1,13 @@
 // Tube FFTs of Algorithm 5.1 (Steps 1 and 3) specialised for a compile-time
-// tube length P (the lengths of the workloads: 8, 12, 16, 31, 32, 64, 100,
-// 128).  Same data flow as the generic kernels in qtp_fft.cu - contiguous
-// tube loads, Stockham stages in shared memory at an odd tube stride,
-// frequency-major stores with the bf16 hi/lo split fused in - but with the
-// radix plan, tube count per CTA and every index computation known to the
-// compiler, so a stage is a handful of shared-memory accesses plus the
-// butterfly arithmetic instead of runtime integer divisions.  When the tensor
-// has an even number of columns, two neighbouring tubes are stored (and, in the
-// inverse, gathered) together: 16-byte complex pairs or 4-byte bf16 pairs.
+// tube length P (the workloads' lengths 8, 12, 16, 31, 32, 64, 100, 128, and
+// 256, 512, 1024 for long tubes), with every index computation known to the
+// compiler.  Lengths with a split P = R1 R2 run the two-pass transform (one
+// register DFT per pass, one shared-memory exchange; see fs_fwd_body); P = 31
+// runs Stockham stages in shared memory at an odd tube stride.  Both store the
+// forward spectra frequency-major with the bf16 hi/lo split fused in and, when
+// the tensor has an even number of columns, two neighbouring tubes together
+// (16-byte complex pairs or 4-byte bf16 pairs; gathered the same way by the
+// inverse).  Grouped variants serve the batched path, one launch per length.
 #include "qtp_fft_common.cuh"
 #include "qtp_internal.h"
 
