@@ -145,6 +145,34 @@ QTP_API qtp_status qtp_host_buffer_size(const qtp_plan* plan, size_t* bytes);
 QTP_API qtp_status qtp_forward_host(const qtp_plan* plan, const float* A_host, const float* B_host,
                             float* C_host, void* dev_buffer, size_t dev_buffer_bytes, void* stream);
 
+/* A sequence of count independent products of the plan's shape with every
+ * operand in HOST memory (pinned for full speed): C_host[i] = A_host[i] *
+ * B_host[i], i < count, each by the three steps of qtp_forward.  The device
+ * holds two products at a time (two slots of A, B, C and one workspace), so
+ * the copies of product i + 1 to the device run while product i is computed
+ * and its C is copied back: host-to-device and device-to-host copies go on
+ * two streams of the plan's own, the compute on stream.  A long sequence then
+ * runs at the host link's rate instead of the sum of the copy and compute
+ * times.
+ * Arguments: A_host, B_host, C_host are arrays of count host pointers (each
+ * 16-byte aligned; layout of qtp_forward).  The products must be independent:
+ * no C_host[i] may overlap another C_host[j], an A_host[j] or a B_host[j].
+ * dev_buffer (device, 16-byte aligned, caller-owned) must hold at least
+ * qtp_host_many_buffer_size(plan) bytes.
+ * Ordering: work enqueued on stream before the call completes before the
+ * first copy starts; the last copy of the call is joined back onto stream, so
+ * the caller synchronises stream before reading any C_host[i] or reusing any
+ * buffer.  Calls on one plan must not run concurrently from several host
+ * threads (the copy streams are the plan's).
+ * Errors: count < 0, NULL arrays or pointers, misalignment and an undersized
+ * dev_buffer are rejected before anything is enqueued; count == 0 is a
+ * no-op.  A failed launch returns QTP_ERR_CUDA with the copies already queued
+ * joined onto stream. */
+QTP_API qtp_status qtp_host_many_buffer_size(const qtp_plan* plan, size_t* bytes);
+QTP_API qtp_status qtp_forward_host_many(const qtp_plan* plan, int count, const float* const* A_host,
+                                 const float* const* B_host, float* const* C_host, void* dev_buffer,
+                                 size_t dev_buffer_bytes, void* stream);
+
 /* Gradients of a real loss L(C), C = A * B, with each quaternion entry taken
  * as four independent reals (not in the paper; a training-style use of it):
  *     dA = dC * B^H,   dB = A^H * dC,

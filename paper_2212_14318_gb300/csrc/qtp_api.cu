@@ -577,9 +577,31 @@ qtp_status qtp_plan_launch_count(const qtp_plan* pl, int* forward, int* backward
   return QTP_OK;
 }
 
+// Copy streams and slot events of qtp_forward_host_many (one set per plan).
+struct HostPipe {
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t entry = nullptr;
+  cudaEvent_t in_ready[2] = {nullptr, nullptr};  // slot's A, B on the device
+  cudaEvent_t computed[2] = {nullptr, nullptr};  // slot's C computed (its A, B consumed)
+  cudaEvent_t out_done[2] = {nullptr, nullptr};  // slot's C copied out
+};
+
+static void destroy_pipe(HostPipe* P) {
+  if (!P) return;
+  if (P->h2d) cudaStreamDestroy(P->h2d);
+  if (P->d2h) cudaStreamDestroy(P->d2h);
+  cudaEvent_t* evs[] = {&P->entry, &P->in_ready[0], &P->in_ready[1], &P->computed[0], &P->computed[1],
+                        &P->out_done[0], &P->out_done[1]};
+  for (cudaEvent_t* e : evs)
+    if (*e) cudaEventDestroy(*e);
+  delete P;
+}
+
 qtp_status qtp_plan_destroy(qtp_plan* pl) {
   if (!pl) return QTP_OK;
   qtp_plan_set_tracing(pl, 0);
+  destroy_pipe(pl->pipe);
+  pl->pipe = nullptr;
   cudaFree(pl->d_tw);
   cudaFree(pl->d_err);
   delete pl;
@@ -651,6 +673,99 @@ qtp_status qtp_forward_host(const qtp_plan* pl, const float* A_host, const float
   r = forward_impl(pl, dA, dB, dC, ws, st);
   if (r != QTP_OK) return r;
   QTP_CUDA(cudaMemcpyAsync(C_host, dC, bC, cudaMemcpyDeviceToHost, st), "copy C to host");
+  return QTP_OK;
+}
+
+// Device slot of qtp_forward_host_many: A, B, C of one product.
+static size_t host_slot_bytes(const qtp_plan* pl) {
+  return c32_bytes(pl->p, pl->m, pl->n) + c32_bytes(pl->p, pl->n, pl->s) + c32_bytes(pl->p, pl->m, pl->s);
+}
+
+qtp_status qtp_host_many_buffer_size(const qtp_plan* pl, size_t* bytes) {
+  if (check_plan(pl) != QTP_OK) return QTP_ERR_INVALID_ARG;
+  if (!bytes) return fail(QTP_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = 2 * host_slot_bytes(pl) + fwd_layout(pl).total;
+  return QTP_OK;
+}
+
+static qtp_status ensure_pipe(const qtp_plan* pl) {
+  if (pl->pipe) return QTP_OK;
+  HostPipe* P = new HostPipe();
+  cudaError_t e = cudaStreamCreateWithFlags(&P->h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->d2h, cudaStreamNonBlocking);
+  cudaEvent_t* evs[] = {&P->entry, &P->in_ready[0], &P->in_ready[1], &P->computed[0], &P->computed[1],
+                        &P->out_done[0], &P->out_done[1]};
+  for (cudaEvent_t* ev : evs)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    destroy_pipe(P);
+    return fail(QTP_ERR_CUDA, "host pipeline streams: %s", cudaGetErrorString(e));
+  }
+  const_cast<qtp_plan*>(pl)->pipe = P;  // plan-owned, created on first use
+  return QTP_OK;
+}
+
+qtp_status qtp_forward_host_many(const qtp_plan* pl, int count, const float* const* A_host,
+                                 const float* const* B_host, float* const* C_host, void* dev_buffer,
+                                 size_t dev_buffer_bytes, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if (count < 0) return fail(QTP_ERR_INVALID_ARG, "count %d is negative", count);
+  if (count == 0) return QTP_OK;
+  if (!A_host || !B_host || !C_host) return fail(QTP_ERR_INVALID_ARG, "a host pointer array is NULL");
+  for (int i = 0; i < count; ++i) {
+    if ((r = check_host_ptr(A_host[i], "A_host[i]")) != QTP_OK) return r;
+    if ((r = check_host_ptr(B_host[i], "B_host[i]")) != QTP_OK) return r;
+    if ((r = check_host_ptr(C_host[i], "C_host[i]")) != QTP_OK) return r;
+  }
+  if ((r = check_dev_ptr(dev_buffer, "dev_buffer")) != QTP_OK) return r;
+  size_t need = 0;
+  qtp_host_many_buffer_size(pl, &need);
+  if (dev_buffer_bytes < need)
+    return fail(QTP_ERR_WORKSPACE, "dev_buffer has %zu bytes, %zu needed", dev_buffer_bytes, need);
+  if ((r = ensure_pipe(pl)) != QTP_OK) return r;
+  HostPipe& P = *pl->pipe;
+  const size_t bA = (size_t)2 * pl->m * pl->n * pl->p * sizeof(float2);
+  const size_t bB = (size_t)2 * pl->n * pl->s * pl->p * sizeof(float2);
+  const size_t bC = (size_t)2 * pl->m * pl->s * pl->p * sizeof(float2);
+  char* base = (char*)dev_buffer;
+  const size_t slot = host_slot_bytes(pl);
+  char* ws = base + 2 * slot;
+  cudaStream_t st = as_stream(stream);
+  // Everything enqueued on stream before this call precedes the first copy.
+  QTP_CUDA(cudaEventRecord(P.entry, st), "host pipeline entry");
+  QTP_CUDA(cudaStreamWaitEvent(P.h2d, P.entry, 0), "host pipeline entry");
+  QTP_CUDA(cudaStreamWaitEvent(P.d2h, P.entry, 0), "host pipeline entry");
+  for (int i = 0; i < count; ++i) {
+    const int sl = i & 1;
+    float* dA = (float*)(base + sl * slot);
+    float* dB = (float*)(base + sl * slot + c32_bytes(pl->p, pl->m, pl->n));
+    float* dC = (float*)(base + sl * slot + c32_bytes(pl->p, pl->m, pl->n) + c32_bytes(pl->p, pl->n, pl->s));
+    // in: the slot's previous product (i - 2) has consumed its A and B
+    if (i >= 2) QTP_CUDA(cudaStreamWaitEvent(P.h2d, P.computed[sl], 0), "host pipeline slot reuse");
+    QTP_CUDA(cudaMemcpyAsync(dA, A_host[i], bA, cudaMemcpyHostToDevice, P.h2d), "copy A to device");
+    QTP_CUDA(cudaMemcpyAsync(dB, B_host[i], bB, cudaMemcpyHostToDevice, P.h2d), "copy B to device");
+    QTP_CUDA(cudaEventRecord(P.in_ready[sl], P.h2d), "host pipeline copy-in");
+    // compute on stream: the slot's inputs are in and its previous C is out
+    QTP_CUDA(cudaStreamWaitEvent(st, P.in_ready[sl], 0), "host pipeline copy-in");
+    if (i >= 2) QTP_CUDA(cudaStreamWaitEvent(st, P.out_done[sl], 0), "host pipeline slot reuse");
+    r = forward_impl(pl, dA, dB, dC, ws, st);
+    if (r != QTP_OK) {
+      // copies already queued still use the caller's buffers: make stream
+      // cover them, so that synchronising it is enough before freeing those
+      if (cudaEventRecord(P.in_ready[sl], P.h2d) == cudaSuccess) cudaStreamWaitEvent(st, P.in_ready[sl], 0);
+      if (cudaEventRecord(P.out_done[sl], P.d2h) == cudaSuccess) cudaStreamWaitEvent(st, P.out_done[sl], 0);
+      return r;
+    }
+    QTP_CUDA(cudaEventRecord(P.computed[sl], st), "host pipeline compute");
+    // out
+    QTP_CUDA(cudaStreamWaitEvent(P.d2h, P.computed[sl], 0), "host pipeline compute");
+    QTP_CUDA(cudaMemcpyAsync(C_host[i], dC, bC, cudaMemcpyDeviceToHost, P.d2h), "copy C to host");
+    QTP_CUDA(cudaEventRecord(P.out_done[sl], P.d2h), "host pipeline copy-out");
+  }
+  // The last copy-out follows every other copy of the call: join it to stream.
+  QTP_CUDA(cudaStreamWaitEvent(st, P.out_done[(count - 1) & 1], 0), "host pipeline exit");
   return QTP_OK;
 }
 

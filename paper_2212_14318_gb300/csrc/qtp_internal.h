@@ -246,4 +246,6 @@ struct qtp_plan {
   qtp::RadixPlan rp;
   int tracing;
   cudaEvent_t ev[4];  // stage boundaries of the last traced call
+  // streams and events of qtp_forward_host_many, created on its first call
+  struct HostPipe* pipe;
 };

@@ -37,6 +37,9 @@ SIGNATURES = {
     "qtp_forward": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_host_buffer_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "qtp_forward_host": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "qtp_host_many_buffer_size": (_i, [_vp, ctypes.POINTER(_sz)]),
+    "qtp_forward_host_many": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _sz,
+                                   _vp]),
     "qtp_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_plan_sync": (_i, [_vp, _vp]),
     "qtp_plan_set_tracing": (_i, [_vp, _i]),
@@ -109,6 +112,16 @@ def _check_tensor(t, shape, name):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
+def _check_host_tensor(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float32")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
 class Plan:
     """A qtp_plan for C = A * B with A in Q^{m x n x p}, B in Q^{n x s x p}."""
 
@@ -163,13 +176,36 @@ class Plan:
 
     def forward_host(self, A_host, B_host, C_host, dev_buffer, stream=None):
         """A, B, C are pinned CPU tensors; dev_buffer a CUDA byte tensor."""
-        for t, nm in ((A_host, "A_host"), (B_host, "B_host"), (C_host, "C_host")):
-            if t.is_cuda or not t.is_contiguous():
-                raise TypeError(f"{nm} must be a contiguous host tensor")
+        _check_host_tensor(A_host, (2, self.m, self.n, self.p, 2), "A_host")
+        _check_host_tensor(B_host, (2, self.n, self.s, self.p, 2), "B_host")
+        _check_host_tensor(C_host, (2, self.m, self.s, self.p, 2), "C_host")
         _check(lib().qtp_forward_host(self._h, _ptr(A_host), _ptr(B_host), _ptr(C_host), _ptr(dev_buffer),
                                       dev_buffer.numel() * dev_buffer.element_size(), _stream(stream)),
                "qtp_forward_host")
         return C_host
+
+    def host_many_buffer_size(self) -> int:
+        return self._size("qtp_host_many_buffer_size")
+
+    def forward_host_many(self, A_hosts, B_hosts, C_hosts, dev_buffer, stream=None):
+        """Independent products C_hosts[i] = A_hosts[i] * B_hosts[i] from pinned
+        CPU tensors, copies overlapped with compute (qtp_forward_host_many);
+        dev_buffer is a CUDA byte tensor of host_many_buffer_size() bytes."""
+        count = len(A_hosts)
+        if len(B_hosts) != count or len(C_hosts) != count:
+            raise ValueError("A_hosts, B_hosts and C_hosts must have the same length")
+        for i in range(count):
+            _check_host_tensor(A_hosts[i], (2, self.m, self.n, self.p, 2), f"A_hosts[{i}]")
+            _check_host_tensor(B_hosts[i], (2, self.n, self.s, self.p, 2), f"B_hosts[{i}]")
+            _check_host_tensor(C_hosts[i], (2, self.m, self.s, self.p, 2), f"C_hosts[{i}]")
+        arr = ctypes.c_void_p * max(count, 1)
+        a = arr(*[_ptr(t) for t in A_hosts])
+        b = arr(*[_ptr(t) for t in B_hosts])
+        c = arr(*[_ptr(t) for t in C_hosts])
+        _check(lib().qtp_forward_host_many(self._h, count, a, b, c, _ptr(dev_buffer),
+                                           dev_buffer.numel() * dev_buffer.element_size(), _stream(stream)),
+               "qtp_forward_host_many")
+        return C_hosts
 
     def backward(self, dC, A, B, need_dA=True, need_dB=True, workspace=None, stream=None):
         import torch

@@ -64,4 +64,6 @@ def test_calls_reject_null_plan(lib):
     assert lib.qtp_forward(None, None, None, None, None, 0, None) == 1
     assert lib.qtp_backward(None, None, None, None, None, None, None, 0, None) == 1
     assert lib.qtp_forward_host(None, None, None, None, None, 0, None) == 1
+    assert lib.qtp_host_many_buffer_size(None, ctypes.byref(sz)) == 1
+    assert lib.qtp_forward_host_many(None, 1, None, None, None, None, 0, None) == 1
     assert lib.qtp_plan_destroy(None) == 0

@@ -142,6 +142,64 @@ def test_forward_host_buffers(precision):
     assert_close(hC.numpy(), _oracle(A, B), REL_TOL, ELEM_TOL, "host buffers")
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape", [(24, 20, 28, 16), (70, 40, 90, 12)])
+def test_forward_host_many(precision, shape):
+    """Five independent products through qtp_forward_host_many (copies of one
+    product overlapping the compute of the previous one): every C equals the
+    device-buffer entry point's bit for bit, and the oracle's within
+    tolerance; a second call on the same plan and buffer repeats them."""
+    import torch
+    qtp = _qtp()
+    m, n, s, p = shape
+    plan = qtp.Plan(m, n, s, p, precision)
+    count = 5
+    As = [_inputs(m, n, s, p, seed=40 + i) for i in range(count)]
+    hA = [torch.from_numpy(a).pin_memory() for a, _ in As]
+    hB = [torch.from_numpy(b).pin_memory() for _, b in As]
+    hC = [torch.full((2, m, s, p, 2), float("nan")).pin_memory() for _ in range(count)]
+    buf = torch.empty(plan.host_many_buffer_size(), dtype=torch.uint8, device="cuda")
+    plan.forward_host_many(hA, hB, hC, buf)
+    plan.sync()
+    for i in range(count):
+        ref = plan.forward(hA[i].cuda(), hB[i].cuda())
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hC[i].numpy(), ref.cpu().numpy(), err_msg=f"product {i}")
+    assert_close(hC[3].numpy(), _oracle(*As[3]), REL_TOL, ELEM_TOL, "host many, product 3")
+    first = [c.clone() for c in hC]
+    for c in hC:
+        c.fill_(float("nan"))
+    plan.forward_host_many(hA, hB, hC, buf)
+    plan.forward_host_many([], [], [], buf)       # count 0: nothing enqueued
+    plan.sync()
+    for i in range(count):
+        np.testing.assert_array_equal(hC[i].numpy(), first[i].numpy(), err_msg=f"repeat {i}")
+
+
+def test_forward_host_many_rejects_bad_arguments():
+    import ctypes
+
+    import torch
+    qtp = _qtp()
+    plan = qtp.Plan(8, 8, 8, 8, "bf16x3")
+    hA = torch.zeros((2, 8, 8, 8, 2)).pin_memory()
+    hC = torch.zeros((2, 8, 8, 8, 2)).pin_memory()
+    small = torch.empty(plan.host_many_buffer_size() - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(RuntimeError, match="dev_buffer"):
+        plan.forward_host_many([hA], [hA], [hC], small)
+    buf = torch.empty(plan.host_many_buffer_size(), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        plan.forward_host_many([hA], [hA, hA], [hC], buf)
+    with pytest.raises(ValueError):
+        plan.forward_host_many([torch.zeros((2, 8, 8, 4, 2)).pin_memory()], [hA], [hC], buf)
+    lib = qtp.lib()
+    arr = (ctypes.c_void_p * 1)(hA.data_ptr())
+    assert lib.qtp_forward_host_many(plan._h, -1, arr, arr, arr, ctypes.c_void_p(buf.data_ptr()),
+                                     buf.numel(), None) == 1
+    assert lib.qtp_forward_host_many(plan._h, 1, None, arr, arr, ctypes.c_void_p(buf.data_ptr()),
+                                     buf.numel(), None) == 1
+
+
 # Long tubes: the two-pass lengths 256, 512, 1024 (8-32 tubes per CTA) and
 # runtime-radix lengths up to the supported maximum 4096 (one to fifteen
 # tubes per CTA), odd and even column counts: sampled entries by
