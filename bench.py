@@ -205,6 +205,48 @@ def reduce_max(x, world, device):
     return float(t.item())
 
 
+def host_link_rates(hA, hB, hC, dev, reps=5):
+    """The host link's own rate for the end-to-end leg's bytes: pinned copies of
+    A and B to the device, of C back, and both directions at once on two
+    streams (best of reps, ms).  both_ms is the floor of a pipelined step."""
+    import torch
+    dA, dB, dC = (torch.empty_like(t, device=dev) for t in (hA, hB, hC))
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def best(fn):
+        out = 1e30
+        for _ in range(reps + 1):
+            torch.cuda.synchronize(dev)
+            ev[0].record()
+            fn()
+            cur = torch.cuda.current_stream(dev)
+            cur.wait_stream(s1)
+            cur.wait_stream(s2)
+            ev[1].record()
+            ev[1].synchronize()
+            out = min(out, ev[0].elapsed_time(ev[1]))
+        return out
+
+    def h2d():
+        s1.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s1):
+            dA.copy_(hA, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+
+    def d2h():
+        s2.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s2):
+            hC.copy_(dC, non_blocking=True)
+
+    t_in, t_out = best(h2d), best(d2h)
+    t_both = best(lambda: (h2d(), d2h()))
+    nin, nout = (hA.numel() + hB.numel()) * 4, hC.numel() * 4
+    return {"h2d_GBps": nin / t_in / 1e6, "d2h_GBps": nout / t_out / 1e6, "h2d_ms": t_in, "d2h_ms": t_out,
+            "both_ms": t_both, "what": "pinned copies of the same bytes, both directions concurrently = the floor "
+                                      "of a pipelined step; frac = both_ms / e2e ms_per_step"}
+
+
 def job_value(flops_per_rank, world, ms_per_step):
     """Whole-job TFLOP/s: every rank's work over the slowest rank's time per step."""
     return world * flops_per_rank / (ms_per_step * 1e-3) / 1e12
@@ -436,6 +478,7 @@ def run_ours(args):
     barrier()
     e2e_single_ms = reduce_max(e0.elapsed_time(e1) / K, world, dev)
     del dbuf1
+    link = host_link_rates(hA[0], hB[0], hC[0], dev)
 
     if rank == 0:
         peaks, peak_src = load_peaks()
@@ -491,7 +534,8 @@ def run_ours(args):
                     "api": f"qtp_forward_host_many, {K} independent products in one call (pinned host "
                            "buffers; copies of product i+1 overlap compute and copy-out of product i)",
                     "single_call": {"value": job_value(flops, world, e2e_single_ms), "unit": UNIT,
-                                    "ms_per_step": e2e_single_ms, "api": "qtp_forward_host, one call per step"}},
+                                    "ms_per_step": e2e_single_ms, "api": "qtp_forward_host, one call per step"},
+                    "link": dict(link, frac=link["both_ms"] / e2e_ms)},
             "gpu_launches": (lc[0] + (lc[1] if train else 0)) * args.steps,
             "clocks": clocks,
         }
