@@ -173,6 +173,34 @@ QTP_API qtp_status qtp_forward_host_many(const qtp_plan* plan, int count, const 
                                  const float* const* B_host, float* const* C_host, void* dev_buffer,
                                  size_t dev_buffer_bytes, void* stream);
 
+/* T-SVD of a quaternion tensor under the T-product.  The paper names
+ * T-SVD-type (low-tubal-rank) methods as what its fast T-product opens up
+ * (Sec. 6) but defines none; this one rests on the per-frequency structure
+ * of Thm 5.1: with A1_hat = fft(A1), A2_hat = fft(A2) along mode 3 and
+ * g = (-f) mod p, the 2m x 2n complex matrices
+ *     M_f(A) = [[A1_hat(f), A2_hat(f)], [-conj A2_hat(g), conj A1_hat(g)]]
+ * satisfy M_f(X * Y) = M_f(X) M_f(Y) and M_f(X^H) = M_f(X)^H, so one SVD per
+ * frequency pair {f, g} gives
+ *     A = U * S * V^H,   U^H * U = I_k,   V^H * V = I_k,   k = min(m, n),
+ * with S f-diagonal (every frontal slice diagonal, no j part).  S's spectra
+ * at f and g are the odd- and even-ranked singular values of M_f (f < g);
+ * at f = g (f = 0, and p / 2 for even p) M_f's singular values come in equal
+ * pairs and the factors are a quaternion SVD.  Truncating U, S, V to their
+ * first r columns gives the tubal-rank-r approximation that keeps the 2r
+ * largest singular values of every M_f.
+ * A: m x n x p (layout of qtp_forward); outputs U: m x k x p, S: k x k x p,
+ * V: n x k x p (same layout), sigma: p x k floats, sigma[f][i] = S's spectrum
+ * at frequency f, entry (i, i) (real, decreasing in i).  All device memory,
+ * caller-owned, 16-byte aligned; workspace_bytes >= qtp_tsvd_workspace_size.
+ * FP32 one-sided Jacobi per frequency pair.  Limits: min(m, n) <=
+ * QTP_TSVD_MAX_K, max(m, n) <= QTP_TSVD_MAX_MN, p <= 4096 (QTP_ERR_UNSUPPORTED
+ * beyond).  Asynchronous on stream. */
+#define QTP_TSVD_MAX_K 64
+#define QTP_TSVD_MAX_MN 1024
+QTP_API qtp_status qtp_tsvd_workspace_size(int m, int n, int p, size_t* bytes);
+QTP_API qtp_status qtp_tsvd(int m, int n, int p, const float* A, float* U, float* S, float* V, float* sigma,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
 /* Gradients of a real loss L(C), C = A * B, with each quaternion entry taken
  * as four independent reals (not in the paper; a training-style use of it):
  *     dA = dC * B^H,   dB = A^H * dC,

@@ -769,6 +769,104 @@ qtp_status qtp_forward_host_many(const qtp_plan* pl, int count, const float* con
   return QTP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// T-SVD (qtp_tsvd.cu)
+// ---------------------------------------------------------------------------
+
+struct TsvdLayout {
+  size_t tw, h, uh, vh, sh, scratch, total;
+};
+
+static TsvdLayout tsvd_layout(int m, int n, int p) {
+  const int k = m < n ? m : n;
+  TsvdLayout L;
+  L.tw = 0;
+  L.h = align256((size_t)p * sizeof(float2));
+  L.uh = L.h + c32_bytes(p, m, n);
+  L.vh = L.uh + c32_bytes(p, m, k);
+  L.sh = L.vh + c32_bytes(p, n, k);
+  L.scratch = L.sh + c32_bytes(p, k, k);
+  L.total = L.scratch + align256(tsvd_scratch_bytes(m, n, p));
+  return L;
+}
+
+static qtp_status check_tsvd_shape(int m, int n, int p) {
+  if (m < 1 || n < 1 || p < 1) return fail(QTP_ERR_INVALID_ARG, "T-SVD shape %d x %d x %d", m, n, p);
+  if (p > QTP_MAX_P) return fail(QTP_ERR_UNSUPPORTED, "p=%d exceeds the supported maximum %d", p, QTP_MAX_P);
+  if ((m < n ? m : n) > QTP_TSVD_MAX_K)
+    return fail(QTP_ERR_UNSUPPORTED, "min(m, n) = %d exceeds the T-SVD maximum %d", m < n ? m : n, QTP_TSVD_MAX_K);
+  if ((m > n ? m : n) > QTP_TSVD_MAX_MN)
+    return fail(QTP_ERR_UNSUPPORTED, "max(m, n) = %d exceeds the T-SVD maximum %d", m > n ? m : n, QTP_TSVD_MAX_MN);
+  return QTP_OK;
+}
+
+qtp_status qtp_tsvd_workspace_size(int m, int n, int p, size_t* bytes) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_tsvd_shape(m, n, p)) != QTP_OK) return r;
+  if (!bytes) return fail(QTP_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = tsvd_layout(m, n, p).total;
+  return QTP_OK;
+}
+
+qtp_status qtp_tsvd(int m, int n, int p, const float* A, float* U, float* S, float* V, float* sigma, void* workspace,
+                    size_t workspace_bytes, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_tsvd_shape(m, n, p)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(A, "A")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(U, "U")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(S, "S")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(V, "V")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(sigma, "sigma")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(workspace, "workspace")) != QTP_OK) return r;
+  const TsvdLayout L = tsvd_layout(m, n, p);
+  if (workspace_bytes < L.total)
+    return fail(QTP_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
+  const int k = m < n ? m : n;
+  cudaStream_t st = as_stream(stream);
+  char* ws = (char*)workspace;
+  float2* tw = (float2*)(ws + L.tw);
+  float2* H = (float2*)(ws + L.h);
+  float2* Uh = (float2*)(ws + L.uh);
+  float2* Vh = (float2*)(ws + L.vh);
+  float2* Sh = (float2*)(ws + L.sh);
+  float2* scratch = tsvd_scratch_bytes(m, n, p) ? (float2*)(ws + L.scratch) : nullptr;
+  const RadixPlan rp = make_radix_plan(p);
+  QTP_CUDA(launch_twiddles(tw, p, st), "T-SVD twiddles");
+  // spectra of A (plain transforms of both Cayley-Dickson halves)
+  FftFwdJob fj;
+  fj.in = (const float2*)A;
+  fj.out = H;
+  fj.rows = m;
+  fj.cols = n;
+  fj.ld = n;
+  fj.nblocks = nblocks_for(m, n, p, false);
+  QTP_CUDA(launch_fft_fwd(&fj, 1, FMT_C32, rp, tw, st), "T-SVD forward FFT");
+  QTP_CUDA(cudaMemsetAsync(Sh, 0, c32_bytes(p, k, k), st), "T-SVD clear S");
+  QTP_CUDA(launch_tsvd_pairs(H, m, n, p, Uh, Vh, Sh, sigma, scratch, st), "T-SVD per-frequency SVDs");
+  FftInvJob ij[2];
+  ij[0].in = Uh;
+  ij[0].out = (float2*)U;
+  ij[0].rows = m;
+  ij[0].cols = k;
+  ij[0].nblocks = nblocks_for(m, k, p, true);
+  ij[1].in = Vh;
+  ij[1].out = (float2*)V;
+  ij[1].rows = n;
+  ij[1].cols = k;
+  ij[1].nblocks = nblocks_for(n, k, p, true);
+  QTP_CUDA(launch_fft_inv(ij, 2, rp, tw, st), "T-SVD inverse FFT of U, V");
+  FftInvJob sj;
+  sj.in = Sh;
+  sj.out = (float2*)S;
+  sj.rows = k;
+  sj.cols = k;
+  sj.nblocks = nblocks_for(k, k, p, true);
+  QTP_CUDA(launch_fft_inv(&sj, 1, rp, tw, st), "T-SVD inverse FFT of S");
+  return QTP_OK;
+}
+
 qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, const float* B, float* dA,
                         float* dB, void* workspace, size_t workspace_bytes, void* stream) {
   g_err[0] = 0;

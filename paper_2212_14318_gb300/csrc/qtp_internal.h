@@ -130,6 +130,16 @@ cudaError_t launch_fft_fwd(const FftFwdJob* jobs, int njobs, int fmt, const Radi
 cudaError_t launch_fft_inv(const FftInvJob* jobs, int njobs, const RadixPlan& rp,
                            const float2* tw, cudaStream_t st);
 
+// T-SVD (qtp_tsvd.cu): one CTA per frequency pair {f, -f} factors M_f of A's
+// spectra H ([plane][f][m][n], complex FP32) and writes the spectra of U
+// ([plane][f][m][k]), V ([plane][f][n][k]) and S ([plane][f][k][k], zeroed by
+// the caller) and sigma ([f][k]); k = min(m, n) <= 64.  scratch: global
+// buffers of tsvd_scratch_bytes(m, n, p) bytes when one pair's matrices do not
+// fit in shared memory (0 bytes otherwise).
+size_t tsvd_scratch_bytes(int m, int n, int p);
+cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, float2* Vh, float2* Sh,
+                              float* sigma, float2* scratch, cudaStream_t st);
+
 // ----------------------------------------------------------------------------
 // Per-frequency complex products (Alg. 5.1 Step 2), generic operand views.
 //

@@ -1,0 +1,486 @@
+// T-SVD of a quaternion tensor under the T-product (a method the paper names
+// in Sec. 6 as enabled by its fast T-product; the decomposition is not in the
+// paper).  The per-frequency structure of Thm 5.1 in its plain-transform form
+// carries it: with A1_hat = fft(A1), A2_hat = fft(A2) along mode 3 and
+// g = (-f) mod p, the 2m x 2n complex matrix
+//     M_f(A) = [[A1_hat(f), A2_hat(f)], [-conj A2_hat(g), conj A1_hat(g)]]
+// turns T-products into matrix products and ^H into ^H, and
+// M_g = Q conj(M_f) Q^T (Q = [[0, I], [-I, 0]]).  One SVD per frequency pair
+// {f, g} therefore gives A = U * S * V^H with U, V unitary tensors and S
+// f-diagonal:
+//   f != g: the left / right singular vectors of odd rank (1st, 3rd, ...)
+//           are U's, V's spectra at f, those of even rank (through the
+//           conjugate block pattern) at g; S's spectra at f and g are the
+//           odd- and even-ranked singular values;
+//   f == g: M_f is a quaternion matrix's complex adjoint, its singular
+//           values come in equal pairs, and the factors keep the pattern
+//           (second half = Q^T conj(first half)).
+//
+// Kernel: one CTA per frequency pair runs a one-sided (Hestenes) Jacobi SVD
+// of M_f, or of M_f^H when m < n (the columns are the 2 min(m, n) side), in
+// shared memory when it fits, else in a per-pair global scratch: cyclic
+// sweeps in round-robin order (disjoint column pairs per round, one warp per
+// pair), each 2x2 step a phase that makes the off-diagonal real followed by
+// the symmetric Jacobi rotation.  Then the columns' norms are sorted, null
+// columns completed by Gram-Schmidt, and the factors written to the spectra
+// of U, V and S (frequency-major, for the inverse transform).
+#include "qtp_internal.h"
+
+namespace qtp {
+
+namespace {
+
+constexpr int kTsvdThreads = 512;
+constexpr int kTsvdWarps = kTsvdThreads / 32;
+constexpr int kTsvdMaxCols = 128;   // 2 min(m, n)
+constexpr int kTsvdMaxSweeps = 40;
+constexpr size_t kTsvdSmemMax = 200 * 1024;  // dynamic shared memory of the in-smem variant
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// x^H y over n entries, by one warp (every lane gets the sum).
+__device__ float2 warp_dot(const float2* __restrict__ x, const float2* __restrict__ y, int n, int lane) {
+  float re = 0.f, im = 0.f;
+  for (int r = lane; r < n; r += 32) {
+    const float2 a = x[r], b = y[r];
+    re = fmaf(a.x, b.x, fmaf(a.y, b.y, re));
+    im = fmaf(a.x, b.y, fmaf(-a.y, b.x, im));
+  }
+  return make_float2(warp_sum(re), warp_sum(im));
+}
+
+// y -= c x, by one warp.
+__device__ void warp_axpy(float2* __restrict__ y, const float2* __restrict__ x, float2 c, int n, int lane) {
+  for (int r = lane; r < n; r += 32) {
+    const float2 v = cmul(c, x[r]);
+    y[r].x -= v.x;
+    y[r].y -= v.y;
+  }
+  __syncwarp();
+}
+
+// The quaternion partner of a column of 2h entries: [-conj(w[h:]); conj(w[:h])].
+__device__ __forceinline__ float2 partner_at(const float2* w, int h, int r) {
+  return r < h ? make_float2(-w[h + r].x, w[h + r].y) : make_float2(w[r - h].x, -w[r - h].y);
+}
+
+// (partner of x)^H y, by one warp.
+__device__ float2 warp_dot_partner(const float2* __restrict__ x, const float2* __restrict__ y, int h, int lane) {
+  float re = 0.f, im = 0.f;
+  for (int r = lane; r < 2 * h; r += 32) {
+    const float2 a = partner_at(x, h, r), b = y[r];
+    re = fmaf(a.x, b.x, fmaf(a.y, b.y, re));
+    im = fmaf(a.x, b.y, fmaf(-a.y, b.x, im));
+  }
+  return make_float2(warp_sum(re), warp_sum(im));
+}
+
+// One warp: project column w (2h entries) off the nb columns of B (stride
+// ldb) and, when with_partners, off their partners too (two passes); return
+// its norm after projection (w is not normalised).
+__device__ float warp_project(float2* w, const float2* B, int nb, long long ldb, int h, bool with_partners,
+                              int lane) {
+  const int n = 2 * h;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = 0; j < nb; ++j) {
+      const float2* b = B + (long long)j * ldb;
+      warp_axpy(w, b, warp_dot(b, w, n, lane), n, lane);
+      if (with_partners) {
+        const float2 c = warp_dot_partner(b, w, h, lane);
+        for (int r = lane; r < n; r += 32) {
+          const float2 v = cmul(c, partner_at(b, h, r));
+          w[r].x -= v.x;
+          w[r].y -= v.y;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  const float2 d = warp_dot(w, w, n, lane);
+  return sqrtf(fmaxf(d.x, 0.f));
+}
+
+// One warp: w (2h entries) := a unit vector orthogonal to the nb columns of B
+// (and their partners when with_partners), tried from the basis vectors.
+__device__ void warp_complete(float2* w, const float2* B, int nb, long long ldb, int h, bool with_partners,
+                              int lane) {
+  const int n = 2 * h;
+  for (int t = 0; t < n; ++t) {
+    for (int r = lane; r < n; r += 32) w[r] = make_float2(r == t ? 1.f : 0.f, 0.f);
+    __syncwarp();
+    const float nw = warp_project(w, B, nb, ldb, h, with_partners, lane);
+    if (nw > 0.5f) {
+      for (int r = lane; r < n; r += 32) w[r] = cscale(w[r], 1.f / nw);
+      __syncwarp();
+      return;
+    }
+  }
+}
+
+struct TsvdArgs {
+  const float2* H;   // spectra of A: [plane][f][m][n] (complex FP32)
+  float2* Uh;        // [plane][f][m][k]
+  float2* Vh;        // [plane][f][n][k]
+  float2* Sh;        // [plane][f][k][k], zeroed by the host
+  float* sigma;      // [f][k]
+  float2* scratch;   // per-pair buffers when shared memory is too small (else null)
+  long long scratch_stride;
+  int m, n, p, k;
+  int R, C;          // rows and columns of the matrix the Jacobi sweeps work on
+  int tall;          // 1: the sweeps work on M_f (m >= n); 0: on M_f^H
+};
+
+// Round-robin schedule: pair t of round rr over C (even) columns; column 0
+// stays, the others rotate, so every pair meets once per sweep of C - 1 rounds.
+__device__ __forceinline__ void rr_pair(int C, int rr, int t, int& a, int& b) {
+  a = t == 0 ? 0 : 1 + (rr + t - 1) % (C - 1);
+  b = 1 + (rr + C - 2 - t) % (C - 1);
+}
+
+__global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
+  extern __shared__ float4 tsvd_smem[];
+  __shared__ float sig[kTsvdMaxCols];
+  __shared__ int perm[kTsvdMaxCols];
+  __shared__ int rotations;
+  const int q = blockIdx.x;
+  const int p = a.p, m = a.m, n = a.n, k = a.k, R = a.R, C = a.C;
+  const int f = q, g = (p - q) % p;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float2* X = a.scratch ? a.scratch + (long long)q * a.scratch_stride : reinterpret_cast<float2*>(tsvd_smem);
+  float2* V = X + (long long)R * C;           // C x C
+  float2* Tm = V + (long long)C * C;          // C x C: the Newton-Schulz factor
+  float2* Tmp = Tm + (long long)C * C;        // C x C: products
+  float2* Wa = Tmp + (long long)C * C;        // 2m x k (self-paired frequencies)
+  float2* Za = Wa + (long long)2 * m * k;     // 2n x k
+
+  // 1. X = M_f (tall) or M_f^H, column-major; V = I
+  const long long slab = (long long)m * n;
+  const float2* H1f = a.H + (long long)f * slab;
+  const float2* H2f = a.H + ((long long)p + f) * slab;
+  const float2* H1g = a.H + (long long)g * slab;
+  const float2* H2g = a.H + ((long long)p + g) * slab;
+  auto Mval = [&](int r, int c) -> float2 {  // M_f[r][c], r < 2m, c < 2n
+    if (r < m) return c < n ? H1f[(long long)r * n + c] : H2f[(long long)r * n + (c - n)];
+    const int rr = r - m;
+    if (c < n) {
+      const float2 v = H2g[(long long)rr * n + c];
+      return make_float2(-v.x, v.y);
+    }
+    return cconj(H1g[(long long)rr * n + (c - n)]);
+  };
+  for (long long idx = tid; idx < (long long)R * C; idx += kTsvdThreads) {
+    const int c = (int)(idx / R), r = (int)(idx - (long long)c * R);
+    X[idx] = a.tall ? Mval(r, c) : cconj(Mval(c, r));
+  }
+  for (int idx = tid; idx < C * C; idx += kTsvdThreads) V[idx] = make_float2(idx % (C + 1) == 0 ? 1.f : 0.f, 0.f);
+  __syncthreads();
+
+  // 2. cyclic one-sided Jacobi sweeps; X = M V throughout.
+  // A rotation is skipped once |x^H y| <= tol |x| |y|; FP32 dot products over
+  // R entries carry about sqrt(R / 32) eps of rounding, so the bound grows
+  // past 256 rows.  Phase 0 sweeps until no pair rotates.  V then has
+  // drifted from unitary by the rounding of its rotations (about
+  // sqrt(rotations per column) eps: 1e-5 for 128 columns, which would show in
+  // A = U S V^H), so one Newton-Schulz step T = (3 I - V^H V) / 2 is applied
+  // to V and to X (keeping X = M V), and phase 1 sweeps again (two or three
+  // sweeps restore the columns' orthogonality).
+  const float tol = 2e-6f * fmaxf(1.f, sqrtf((float)R / 256.f));
+  for (int phase = 0; phase < 2; ++phase) {
+  if (phase == 1) {
+    // Tm = (3 I - V^H V) / 2, column-major
+    for (int idx = tid; idx < C * C; idx += kTsvdThreads) {
+      const int j = idx / C, i = idx - j * C;
+      const float2* vi = V + (long long)i * C;
+      const float2* vj = V + (long long)j * C;
+      float re = 0.f, im = 0.f;
+      for (int r = 0; r < C; ++r) {
+        const float2 x = vi[r], y = vj[r];
+        re = fmaf(x.x, y.x, fmaf(x.y, y.y, re));
+        im = fmaf(x.x, y.y, fmaf(-x.y, y.x, im));
+      }
+      Tm[idx] = make_float2(0.5f * ((i == j ? 3.f : 0.f) - re), -0.5f * im);
+    }
+    __syncthreads();
+    // V <- V Tm, then X <- X Tm in blocks of C rows, through Tmp
+    for (int blk = -1; blk < (R + C - 1) / C; ++blk) {
+      float2* src = blk < 0 ? V : X;
+      const long long lds = blk < 0 ? C : R;
+      const int r0 = blk < 0 ? 0 : blk * C;
+      const int rows = blk < 0 ? C : min(C, R - r0);
+      for (int idx = tid; idx < rows * C; idx += kTsvdThreads) {
+        const int j = idx / rows, r = idx - j * rows;
+        float re = 0.f, im = 0.f;
+        for (int l = 0; l < C; ++l) {
+          const float2 x = src[(long long)l * lds + r0 + r], t = Tm[(long long)j * C + l];
+          re = fmaf(x.x, t.x, fmaf(-x.y, t.y, re));
+          im = fmaf(x.x, t.y, fmaf(x.y, t.x, im));
+        }
+        Tmp[(long long)j * rows + r] = make_float2(re, im);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < rows * C; idx += kTsvdThreads) {
+        const int j = idx / rows, r = idx - j * rows;
+        src[(long long)j * lds + r0 + r] = Tmp[idx];
+      }
+      __syncthreads();
+    }
+  }
+  for (int sweep = 0; sweep < kTsvdMaxSweeps; ++sweep) {
+    if (tid == 0) rotations = 0;
+    __syncthreads();
+    for (int rr = 0; rr < C - 1; ++rr) {
+      for (int t = warp; t < C / 2; t += kTsvdWarps) {
+        int ca, cb;
+        rr_pair(C, rr, t, ca, cb);
+        float2* x = X + (long long)ca * R;
+        float2* y = X + (long long)cb * R;
+        float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+        for (int r = lane; r < R; r += 32) {
+          const float2 u = x[r], v = y[r];
+          al = fmaf(u.x, u.x, fmaf(u.y, u.y, al));
+          be = fmaf(v.x, v.x, fmaf(v.y, v.y, be));
+          gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));
+          gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, gi));
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        gr = warp_sum(gr);
+        gi = warp_sum(gi);
+        const float gabs = hypotf(gr, gi);
+        if (gabs > tol * sqrtf(al * be) && gabs > 1e-30f) {
+          // [x, y] <- [x, conj(e) y] [[c, s], [-s, c]], e = gamma / |gamma|
+          const float zeta = (be - al) / (2.f * gabs);
+          const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float cs = 1.f / sqrtf(1.f + tt * tt), sn = cs * tt;
+          const float2 ce = make_float2(gr / gabs, -gi / gabs);
+          for (int r = lane; r < R; r += 32) {
+            const float2 u = x[r], v = cmul(ce, y[r]);
+            x[r] = make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
+            y[r] = make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+          }
+          float2* vx = V + (long long)ca * C;
+          float2* vy = V + (long long)cb * C;
+          for (int r = lane; r < C; r += 32) {
+            const float2 u = vx[r], v = cmul(ce, vy[r]);
+            vx[r] = make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
+            vy[r] = make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+          }
+          if (lane == 0) atomicAdd(&rotations, 1);
+        }
+      }
+      __syncthreads();
+    }
+    const int done = rotations == 0;
+    __syncthreads();
+    if (done) break;
+  }
+  }
+
+  // 3. singular values (column norms), sorted decreasing (ties by index)
+  for (int c = warp; c < C; c += kTsvdWarps) {
+    const float2 d = warp_dot(X + (long long)c * R, X + (long long)c * R, R, lane);
+    if (lane == 0) sig[c] = sqrtf(fmaxf(d.x, 0.f));
+  }
+  __syncthreads();
+  if (tid < C) {
+    const float s = sig[tid];
+    int rank = 0;
+    for (int j = 0; j < C; ++j) rank += (sig[j] > s) || (sig[j] == s && j < tid);
+    perm[rank] = tid;
+  }
+  __syncthreads();
+  const float smax = sig[perm[0]];
+  const float null_tol = 1e-6f * smax;
+
+  // 4. normalise the X columns (the left vectors when tall, else the right
+  //    ones); the other side is V, unitary already
+  for (long long idx = tid; idx < (long long)R * C; idx += kTsvdThreads) {
+    const int c = (int)(idx / R);
+    const float s = sig[c];
+    X[idx] = s > null_tol && s > 0.f ? cscale(X[idx], 1.f / s) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // left vectors W (2m rows), right vectors Z (2n rows), column c
+  float2* W = a.tall ? X : V;
+  float2* Z = a.tall ? V : X;
+  const long long ldw = a.tall ? R : C, ldz = a.tall ? C : R;
+
+  if (f != g) {
+    // null columns on the X side: complete against the other X columns, in
+    // rank order, by warp 0
+    if (warp == 0) {
+      for (int i = 0; i < C; ++i) {
+        const int c = perm[i];
+        if (sig[c] > null_tol && sig[c] > 0.f) continue;
+        // the columns of rank < i are final (live ones rank first): project a
+        // basis vector off each of them
+        float2* w = X + (long long)c * R;
+        for (int t = 0; t < R; ++t) {
+          for (int r = lane; r < R; r += 32) w[r] = make_float2(r == t ? 1.f : 0.f, 0.f);
+          __syncwarp();
+          for (int pass = 0; pass < 2; ++pass)
+            for (int j = 0; j < i; ++j) {
+              const float2* b = X + (long long)perm[j] * R;
+              warp_axpy(w, b, warp_dot(b, w, R, lane), R, lane);
+            }
+          const float nw = sqrtf(fmaxf(warp_dot(w, w, R, lane).x, 0.f));
+          if (nw > 0.5f) {
+            for (int r = lane; r < R; r += 32) w[r] = cscale(w[r], 1.f / nw);
+            __syncwarp();
+            break;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // scatter: rank 2i -> frequency f, rank 2i + 1 -> frequency g
+    const long long sU = (long long)m * k, sV = (long long)n * k, sS = (long long)k * k;
+    for (int idx = tid; idx < m * k; idx += kTsvdThreads) {
+      const int r = idx / k, i = idx - r * k;
+      const float2* wa = W + (long long)perm[2 * i] * ldw;
+      const float2* wb = W + (long long)perm[2 * i + 1] * ldw;
+      a.Uh[(long long)f * sU + idx] = wa[r];
+      a.Uh[((long long)p + f) * sU + idx] = wb[r];
+      a.Uh[((long long)p + g) * sU + idx] = make_float2(-wa[m + r].x, wa[m + r].y);
+      a.Uh[(long long)g * sU + idx] = cconj(wb[m + r]);
+    }
+    for (int idx = tid; idx < n * k; idx += kTsvdThreads) {
+      const int r = idx / k, i = idx - r * k;
+      const float2* za = Z + (long long)perm[2 * i] * ldz;
+      const float2* zb = Z + (long long)perm[2 * i + 1] * ldz;
+      a.Vh[(long long)f * sV + idx] = za[r];
+      a.Vh[((long long)p + f) * sV + idx] = zb[r];
+      a.Vh[((long long)p + g) * sV + idx] = make_float2(-za[n + r].x, za[n + r].y);
+      a.Vh[(long long)g * sV + idx] = cconj(zb[n + r]);
+    }
+    for (int i = tid; i < k; i += kTsvdThreads) {
+      const float sa = sig[perm[2 * i]], sb = sig[perm[2 * i + 1]];
+      a.sigma[(long long)f * k + i] = sa;
+      a.sigma[(long long)g * k + i] = sb;
+      a.Sh[(long long)f * sS + (long long)i * k + i] = make_float2(sa, 0.f);
+      a.Sh[(long long)g * sS + (long long)i * k + i] = make_float2(sb, 0.f);
+    }
+    return;
+  }
+
+  // f == g: one vector per equal pair, the partners complete the factors.
+  // Warp 0 builds Wa (2m x k) and Za (2n x k) column by column in rank order:
+  // the candidate of rank 2i, projected off the chosen columns and their
+  // partners; null or dependent candidates are completed from basis vectors.
+  if (warp == 0) {
+    for (int i = 0; i < k; ++i) {
+      const int c = perm[2 * i];
+      const bool live = sig[c] > null_tol && sig[c] > 0.f;
+      float2* wa = Wa + (long long)i * 2 * m;
+      float2* za = Za + (long long)i * 2 * n;
+      const float2* wc = W + (long long)c * ldw;
+      const float2* zc = Z + (long long)c * ldz;
+      for (int r = lane; r < 2 * m; r += 32) wa[r] = wc[r];
+      for (int r = lane; r < 2 * n; r += 32) za[r] = zc[r];
+      __syncwarp();
+      float nw = warp_project(wa, Wa, i, 2 * m, m, true, lane);
+      float nz = warp_project(za, Za, i, 2 * n, n, true, lane);
+      if (live && nw > 0.5f && nz > 0.5f) {
+        for (int r = lane; r < 2 * m; r += 32) wa[r] = cscale(wa[r], 1.f / nw);
+        for (int r = lane; r < 2 * n; r += 32) za[r] = cscale(za[r], 1.f / nz);
+        __syncwarp();
+      } else {
+        if (!(nw > 0.5f) || !live) warp_complete(wa, Wa, i, 2 * m, m, true, lane);
+        else {
+          for (int r = lane; r < 2 * m; r += 32) wa[r] = cscale(wa[r], 1.f / nw);
+          __syncwarp();
+        }
+        if (!(nz > 0.5f) || !live) warp_complete(za, Za, i, 2 * n, n, true, lane);
+        else {
+          for (int r = lane; r < 2 * n; r += 32) za[r] = cscale(za[r], 1.f / nz);
+          __syncwarp();
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const long long sU = (long long)m * k, sV = (long long)n * k, sS = (long long)k * k;
+  for (int idx = tid; idx < m * k; idx += kTsvdThreads) {
+    const int r = idx / k, i = idx - r * k;
+    const float2* wa = Wa + (long long)i * 2 * m;
+    a.Uh[(long long)f * sU + idx] = wa[r];
+    a.Uh[((long long)p + f) * sU + idx] = make_float2(-wa[m + r].x, wa[m + r].y);
+  }
+  for (int idx = tid; idx < n * k; idx += kTsvdThreads) {
+    const int r = idx / k, i = idx - r * k;
+    const float2* za = Za + (long long)i * 2 * n;
+    a.Vh[(long long)f * sV + idx] = za[r];
+    a.Vh[((long long)p + f) * sV + idx] = make_float2(-za[n + r].x, za[n + r].y);
+  }
+  for (int i = tid; i < k; i += kTsvdThreads) {
+    const float s = sig[perm[2 * i]];
+    const bool live = s > null_tol && s > 0.f;
+    a.sigma[(long long)f * k + i] = live ? s : 0.f;
+    a.Sh[(long long)f * sS + (long long)i * k + i] = make_float2(live ? s : 0.f, 0.f);
+  }
+}
+
+// Complex entries of one pair's buffers: the working matrix (R x C), V, the
+// Newton-Schulz factor and a product buffer (C x C each) and the self-paired
+// halves Wa (2m x k), Za (2n x k).
+long long tsvd_pair_elems(int m, int n) {
+  const int k = m < n ? m : n;
+  const long long R = 2LL * (m > n ? m : n), C = 2LL * k;
+  return R * C + 3 * C * C + 2LL * m * k + 2LL * n * k;
+}
+
+}  // namespace
+
+size_t tsvd_scratch_bytes(int m, int n, int p) {
+  const size_t bytes = sizeof(float2) * (size_t)tsvd_pair_elems(m, n);
+  if (bytes <= kTsvdSmemMax) return 0;
+  return bytes * (size_t)(p / 2 + 1);
+}
+
+cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, float2* Vh, float2* Sh,
+                              float* sigma, float2* scratch, cudaStream_t st) {
+  const int k = m < n ? m : n;
+  if (2 * k > kTsvdMaxCols) return cudaErrorInvalidValue;
+  TsvdArgs a;
+  a.H = H;
+  a.Uh = Uh;
+  a.Vh = Vh;
+  a.Sh = Sh;
+  a.sigma = sigma;
+  a.m = m;
+  a.n = n;
+  a.p = p;
+  a.k = k;
+  a.tall = m >= n ? 1 : 0;
+  a.R = 2 * (m > n ? m : n);
+  a.C = 2 * k;
+  const long long elems = tsvd_pair_elems(m, n);
+  const size_t bytes = sizeof(float2) * (size_t)elems;
+  size_t smem = 0;
+  if (bytes <= kTsvdSmemMax) {
+    a.scratch = nullptr;
+    a.scratch_stride = 0;
+    smem = bytes;
+    static std::atomic<unsigned long long> attr_set{0};
+    cudaError_t e = ensure_smem_attr(attr_set, tsvd_pair_kernel, kTsvdSmemMax);
+    if (e != cudaSuccess) return e;
+  } else {
+    if (!scratch) return cudaErrorInvalidValue;
+    a.scratch = scratch;
+    a.scratch_stride = elems;
+  }
+  tsvd_pair_kernel<<<p / 2 + 1, kTsvdThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace qtp

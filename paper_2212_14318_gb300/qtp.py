@@ -38,6 +38,8 @@ SIGNATURES = {
     "qtp_host_buffer_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "qtp_forward_host": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_host_many_buffer_size": (_i, [_vp, ctypes.POINTER(_sz)]),
+    "qtp_tsvd_workspace_size": (_i, [_i, _i, _i, ctypes.POINTER(_sz)]),
+    "qtp_tsvd": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_forward_host_many": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _sz,
                                    _vp]),
     "qtp_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -120,6 +122,29 @@ def _check_host_tensor(t, shape, name):
         raise TypeError(f"{name} must be contiguous float32")
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def tsvd(A, workspace=None, stream=None):
+    """T-SVD A = U * S * V^H of a CUDA tensor A (2, m, n, p, 2) (qtp_tsvd):
+    returns U (2, m, k, p, 2), S (2, k, k, p, 2), V (2, n, k, p, 2) and sigma
+    (p, k), k = min(m, n)."""
+    import torch
+    if not isinstance(A, torch.Tensor) or A.dim() != 5 or A.shape[0] != 2 or A.shape[4] != 2:
+        raise ValueError("A must have shape (2, m, n, p, 2)")
+    _, m, n, p, _ = A.shape
+    _check_tensor(A, (2, m, n, p, 2), "A")
+    k = min(m, n)
+    dev = A.device
+    U = torch.empty((2, m, k, p, 2), dtype=torch.float32, device=dev)
+    S = torch.empty((2, k, k, p, 2), dtype=torch.float32, device=dev)
+    V = torch.empty((2, n, k, p, 2), dtype=torch.float32, device=dev)
+    sigma = torch.empty((p, k), dtype=torch.float32, device=dev)
+    need = ctypes.c_size_t()
+    _check(lib().qtp_tsvd_workspace_size(m, n, p, ctypes.byref(need)), "qtp_tsvd_workspace_size")
+    ws = workspace if workspace is not None else torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=dev)
+    _check(lib().qtp_tsvd(m, n, p, _ptr(A), _ptr(U), _ptr(S), _ptr(V), _ptr(sigma), _ptr(ws),
+                          ws.numel() * ws.element_size(), _stream(stream)), "qtp_tsvd")
+    return U, S, V, sigma
 
 
 class Plan:

@@ -66,4 +66,14 @@ def test_calls_reject_null_plan(lib):
     assert lib.qtp_forward_host(None, None, None, None, None, 0, None) == 1
     assert lib.qtp_host_many_buffer_size(None, ctypes.byref(sz)) == 1
     assert lib.qtp_forward_host_many(None, 1, None, None, None, None, 0, None) == 1
+
+
+def test_tsvd_rejects_bad_shapes_and_pointers(lib):
+    sz = ctypes.c_size_t()
+    assert lib.qtp_tsvd_workspace_size(0, 4, 4, ctypes.byref(sz)) == 1
+    assert lib.qtp_tsvd_workspace_size(4, 4, 5000, ctypes.byref(sz)) == 2
+    assert lib.qtp_tsvd_workspace_size(65, 70, 4, ctypes.byref(sz)) == 2      # min(m, n) > 64
+    assert lib.qtp_tsvd_workspace_size(8, 2000, 4, ctypes.byref(sz)) == 2     # max(m, n) > 1024
+    assert lib.qtp_tsvd_workspace_size(8, 6, 4, ctypes.byref(sz)) == 0 and sz.value > 0
+    assert lib.qtp_tsvd(8, 6, 4, None, None, None, None, None, None, 0, None) == 1
     assert lib.qtp_plan_destroy(None) == 0
