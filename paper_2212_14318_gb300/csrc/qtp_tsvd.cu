@@ -127,6 +127,114 @@ __device__ void warp_complete(float2* w, const float2* B, int nb, long long ldb,
   }
 }
 
+// Whole block: project w (2h entries) off the nb columns of B (stride ldb)
+// and their partners, by two passes of classical Gram-Schmidt (all the
+// coefficients of a pass at once, one warp per column, then one subtraction
+// with the threads over the entries); returns |w| after projection (the same
+// value in every thread).  coef: 2 nb entries of shared memory.
+__device__ float block_project_partners(float2* w, const float2* B, int nb, long long ldb, int h, float2* coef,
+                                        float* nrm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = 2 * h;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = warp; j < nb; j += kTsvdWarps) {
+      const float2* b = B + (long long)j * ldb;
+      const float2 c0 = warp_dot(b, w, n, lane);
+      const float2 c1 = warp_dot_partner(b, w, h, lane);
+      if (lane == 0) {
+        coef[2 * j] = c0;
+        coef[2 * j + 1] = c1;
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += kTsvdThreads) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int j = 0; j < nb; ++j) {
+        const float2* b = B + (long long)j * ldb;
+        const float2 u = cmul(coef[2 * j], b[r]), v = cmul(coef[2 * j + 1], partner_at(b, h, r));
+        acc.x += u.x + v.x;
+        acc.y += u.y + v.y;
+      }
+      w[r].x -= acc.x;
+      w[r].y -= acc.y;
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    const float2 d = warp_dot(w, w, n, lane);
+    if (lane == 0) *nrm = sqrtf(fmaxf(d.x, 0.f));
+  }
+  __syncthreads();
+  const float v = *nrm;
+  __syncthreads();
+  return v;
+}
+
+// Rows per lane a column pair keeps in registers during one Jacobi step:
+// X columns up to 32 kRegRows rows, V columns up to 32 kRegV (C <= 128).
+constexpr int kRegRows = 16;
+constexpr int kRegV = 4;
+
+// One Jacobi step on columns x, y of X (R rows) and vx, vy of V (C rows) by
+// one warp, with every entry a lane touches loaded at once into registers
+// (one round trip to memory per pair), rotated there and stored once.
+// Returns whether it rotated.
+__device__ __forceinline__ bool jacobi_pair_reg(float2* __restrict__ x, float2* __restrict__ y,
+                                                float2* __restrict__ vx, float2* __restrict__ vy, int R, int C,
+                                                float tol, int lane) {
+  float2 xr[kRegRows], yr[kRegRows], vxr[kRegV], vyr[kRegV];
+#pragma unroll
+  for (int i = 0; i < kRegRows; ++i) {
+    const int r = lane + 32 * i;
+    xr[i] = r < R ? x[r] : make_float2(0.f, 0.f);
+    yr[i] = r < R ? y[r] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < kRegV; ++i) {
+    const int r = lane + 32 * i;
+    vxr[i] = r < C ? vx[r] : make_float2(0.f, 0.f);
+    vyr[i] = r < C ? vy[r] : make_float2(0.f, 0.f);
+  }
+  float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+#pragma unroll
+  for (int i = 0; i < kRegRows; ++i) {
+    const float2 u = xr[i], v = yr[i];
+    al = fmaf(u.x, u.x, fmaf(u.y, u.y, al));
+    be = fmaf(v.x, v.x, fmaf(v.y, v.y, be));
+    gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));
+    gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, gi));
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  gr = warp_sum(gr);
+  gi = warp_sum(gi);
+  const float gabs = hypotf(gr, gi);
+  if (!(gabs > tol * sqrtf(al * be) && gabs > 1e-30f)) return false;
+  const float zeta = (be - al) / (2.f * gabs);
+  const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float cs = 1.f / sqrtf(1.f + tt * tt), sn = cs * tt;
+  const float2 ce = make_float2(gr / gabs, -gi / gabs);
+#pragma unroll
+  for (int i = 0; i < kRegRows; ++i) {
+    const int r = lane + 32 * i;
+    const float2 u = xr[i], v = cmul(ce, yr[i]);
+    if (r < R) {
+      x[r] = make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
+      y[r] = make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kRegV; ++i) {
+    const int r = lane + 32 * i;
+    const float2 u = vxr[i], v = cmul(ce, vyr[i]);
+    if (r < C) {
+      vx[r] = make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
+      vy[r] = make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+    }
+  }
+  return true;
+}
+
 struct TsvdArgs {
   const float2* H;   // spectra of A: [plane][f][m][n] (complex FP32)
   float2* Uh;        // [plane][f][m][k]
@@ -195,6 +303,7 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   // to V and to X (keeping X = M V), and phase 1 sweeps again (two or three
   // sweeps restore the columns' orthogonality).
   const float tol = 2e-6f * fmaxf(1.f, sqrtf((float)R / 256.f));
+  const bool reg_path = R <= 32 * kRegRows && C <= 32 * kRegV;
   for (int phase = 0; phase < 2; ++phase) {
   if (phase == 1) {
     // Tm = (3 I - V^H V) / 2, column-major
@@ -244,6 +353,11 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
         rr_pair(C, rr, t, ca, cb);
         float2* x = X + (long long)ca * R;
         float2* y = X + (long long)cb * R;
+        if (reg_path) {
+          if (jacobi_pair_reg(x, y, V + (long long)ca * C, V + (long long)cb * C, R, C, tol, lane) && lane == 0)
+            atomicAdd(&rotations, 1);
+          continue;
+        }
         float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
         for (int r = lane; r < R; r += 32) {
           const float2 u = x[r], v = y[r];
@@ -374,41 +488,36 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   }
 
   // f == g: one vector per equal pair, the partners complete the factors.
-  // Warp 0 builds Wa (2m x k) and Za (2n x k) column by column in rank order:
-  // the candidate of rank 2i, projected off the chosen columns and their
-  // partners; null or dependent candidates are completed from basis vectors.
-  if (warp == 0) {
-    for (int i = 0; i < k; ++i) {
-      const int c = perm[2 * i];
-      const bool live = sig[c] > null_tol && sig[c] > 0.f;
-      float2* wa = Wa + (long long)i * 2 * m;
-      float2* za = Za + (long long)i * 2 * n;
-      const float2* wc = W + (long long)c * ldw;
-      const float2* zc = Z + (long long)c * ldz;
-      for (int r = lane; r < 2 * m; r += 32) wa[r] = wc[r];
-      for (int r = lane; r < 2 * n; r += 32) za[r] = zc[r];
-      __syncwarp();
-      float nw = warp_project(wa, Wa, i, 2 * m, m, true, lane);
-      float nz = warp_project(za, Za, i, 2 * n, n, true, lane);
-      if (live && nw > 0.5f && nz > 0.5f) {
-        for (int r = lane; r < 2 * m; r += 32) wa[r] = cscale(wa[r], 1.f / nw);
-        for (int r = lane; r < 2 * n; r += 32) za[r] = cscale(za[r], 1.f / nz);
-        __syncwarp();
-      } else {
-        if (!(nw > 0.5f) || !live) warp_complete(wa, Wa, i, 2 * m, m, true, lane);
-        else {
-          for (int r = lane; r < 2 * m; r += 32) wa[r] = cscale(wa[r], 1.f / nw);
-          __syncwarp();
-        }
-        if (!(nz > 0.5f) || !live) warp_complete(za, Za, i, 2 * n, n, true, lane);
-        else {
-          for (int r = lane; r < 2 * n; r += 32) za[r] = cscale(za[r], 1.f / nz);
-          __syncwarp();
-        }
-      }
+  // Column by column in rank order, the whole block takes the candidate of
+  // rank 2i and projects it off the chosen columns and their partners (two
+  // passes of classical Gram-Schmidt); a null or dependent candidate is
+  // completed from basis vectors by warp 0.
+  __shared__ float2 coef[2 * kTsvdMaxCols];
+  __shared__ float nrm;
+  for (int i = 0; i < k; ++i) {
+    const int c = perm[2 * i];
+    const bool live = sig[c] > null_tol && sig[c] > 0.f;
+    float2* wa = Wa + (long long)i * 2 * m;
+    float2* za = Za + (long long)i * 2 * n;
+    const float2* wc = W + (long long)c * ldw;
+    const float2* zc = Z + (long long)c * ldz;
+    for (int r = tid; r < 2 * m; r += kTsvdThreads) wa[r] = wc[r];
+    for (int r = tid; r < 2 * n; r += kTsvdThreads) za[r] = zc[r];
+    __syncthreads();
+    const float nw = block_project_partners(wa, Wa, i, 2 * m, m, coef, &nrm);
+    const float nz = block_project_partners(za, Za, i, 2 * n, n, coef, &nrm);
+    const bool keep_w = live && nw > 0.5f, keep_z = live && nz > 0.5f;
+    for (int r = tid; r < 2 * m; r += kTsvdThreads)
+      if (keep_w) wa[r] = cscale(wa[r], 1.f / nw);
+    for (int r = tid; r < 2 * n; r += kTsvdThreads)
+      if (keep_z) za[r] = cscale(za[r], 1.f / nz);
+    __syncthreads();
+    if (warp == 0) {
+      if (!keep_w) warp_complete(wa, Wa, i, 2 * m, m, true, lane);
+      if (!keep_z) warp_complete(za, Za, i, 2 * n, n, true, lane);
     }
+    __syncthreads();
   }
-  __syncthreads();
   const long long sU = (long long)m * k, sV = (long long)n * k, sS = (long long)k * k;
   for (int idx = tid; idx < m * k; idx += kTsvdThreads) {
     const int r = idx / k, i = idx - r * k;
