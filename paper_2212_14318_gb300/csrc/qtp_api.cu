@@ -120,6 +120,11 @@ int nblocks_for(long long rows, long long cols, int p, bool inv) {
   return (int)((2 * rows * cols + T - 1) / T);
 }
 
+// Forward-transform runs of a rows x cols tensor written in format fmt.
+int nblocks_fwd(long long rows, long long cols, int p, int fmt) {
+  return nblocks_for(rows, fft_fwd_run_cols(p, fmt, (int)cols), p, false);
+}
+
 // Operand view helpers on complex FP32 spectra [plane][f][rows][cols].
 CView view(const float2* spec, int plane, int p, long long rows, long long cols, bool row_is_first_index,
            int fneg, int conj) {
@@ -467,11 +472,11 @@ qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, floa
   jobs[0].in = (const float2*)A;
   jobs[0].out = ws + L.sa;
   jobs[0].rows = pl->m; jobs[0].cols = pl->n; jobs[0].ld = (int)spec_ld(fmt, pl->n);
-  jobs[0].nblocks = nblocks_for(pl->m, pl->n, pl->p, false);
+  jobs[0].nblocks = nblocks_fwd(pl->m, pl->n, pl->p, fmt);
   jobs[1].in = (const float2*)B;
   jobs[1].out = ws + L.sb;
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
-  jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p, false);
+  jobs[1].nblocks = nblocks_fwd(pl->n, pl->s, pl->p, fmt);
   trace(pl, 0, st);
   QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "forward tube FFT");
   trace(pl, 1, st);
@@ -841,7 +846,7 @@ qtp_status qtp_tsvd(int m, int n, int p, const float* A, float* U, float* S, flo
   fj.rows = m;
   fj.cols = n;
   fj.ld = n;
-  fj.nblocks = nblocks_for(m, n, p, false);
+  fj.nblocks = nblocks_fwd(m, n, p, FMT_C32);
   QTP_CUDA(launch_fft_fwd(&fj, 1, FMT_C32, rp, tw, st), "T-SVD forward FFT");
   QTP_CUDA(cudaMemsetAsync(Sh, 0, c32_bytes(p, k, k), st), "T-SVD clear S");
   QTP_CUDA(launch_tsvd_pairs(H, m, n, p, Uh, Vh, Sh, sigma, scratch, st), "T-SVD per-frequency SVDs");
@@ -890,18 +895,18 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
   jobs[0].in = (const float2*)A;
   jobs[0].out = ws + L.sa;
   jobs[0].rows = pl->m; jobs[0].cols = pl->n; jobs[0].ld = (int)spec_ld(fmt, pl->n);
-  jobs[0].nblocks = nblocks_for(pl->m, pl->n, pl->p, false);
+  jobs[0].nblocks = nblocks_fwd(pl->m, pl->n, pl->p, fmt);
   jobs[1].in = (const float2*)B;
   jobs[1].out = ws + L.sb;
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
-  jobs[1].nblocks = nblocks_for(pl->n, pl->s, pl->p, false);
+  jobs[1].nblocks = nblocks_fwd(pl->n, pl->s, pl->p, fmt);
   trace(pl, 0, st);
   QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "backward FFT of A, B");
   FftFwdJob gj;
   gj.in = (const float2*)dC;
   gj.out = ws + L.sg;
   gj.rows = pl->m; gj.cols = pl->s; gj.ld = (int)spec_ld(fmt, pl->s);
-  gj.nblocks = nblocks_for(pl->m, pl->s, pl->p, false);
+  gj.nblocks = nblocks_fwd(pl->m, pl->s, pl->p, fmt);
   QTP_CUDA(launch_fft_fwd(&gj, 1, fmt, pl->rp, pl->d_tw, st), "backward FFT of dC");
   trace(pl, 1, st);
   // Step 2.

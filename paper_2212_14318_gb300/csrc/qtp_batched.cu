@@ -247,7 +247,8 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
       j.T = T;
       j.tw_off = tw_off[q.p];
       j.rp = rp;
-      counter += (2LL * rows * cols + T - 1) / T;
+      const int run_cols = which == 2 ? cols : fft_fwd_run_cols(q.p, fmt, cols);
+      counter += (2LL * rows * run_cols + T - 1) / T;
       return j;
     };
     fwd.push_back(job(0, q.m, q.n, sa, fb));

@@ -308,7 +308,12 @@ __device__ __forceinline__ void fs_fwd_body(const FftFwdJob& job, long long b, c
   constexpr int NPARTS = FMT == FMT_BF16X3 ? 4 : (FMT == FMT_BF16 ? 2 : 1);
   static_assert(R1 * R2 == P && kThreads % T == 0, "two-pass split");
 
-  const long long per_plane = (long long)job.rows * job.cols;
+  // Run space: the tubes row by row, each row padded to an even count for the
+  // bf16 spectra (a phantom tube after an odd row: zero input, and its stores
+  // land in the spectra's row padding, ld >= cols + 1), so that pass 2 always
+  // stores tube pairs.  fft_fwd_run_cols gives the host the same count.
+  const int cp = (FMT != FMT_C32 && (job.cols & 1)) ? job.cols + 1 : job.cols;
+  const long long per_plane = (long long)job.rows * cp;
   const long long ntubes = 2 * per_plane;
   const long long t0 = b * T;
   if (t0 >= ntubes) return;
@@ -317,15 +322,45 @@ __device__ __forceinline__ void fs_fwd_body(const FftFwdJob& job, long long b, c
   // pass 1: every load of the thread's NI items is issued before the first
   // DFT, to keep more bytes in flight
   constexpr int NI = (T * R2 + kThreads - 1) / kThreads;
-  const float2* src = job.in + t0 * P;
   float2 v[NI][R1];
+  if (cp == job.cols) {
+    // no phantom tubes: the run space is the tensor's, tubes contiguous
+    const float2* src = job.in + t0 * P;
 #pragma unroll
-  for (int it = 0; it < NI; ++it) {
-    const int idx = threadIdx.x + it * kThreads;
-    const int tube = idx / R2;
-    if (idx < T * R2 && tube < Tb) {
+    for (int it = 0; it < NI; ++it) {
+      const int idx = threadIdx.x + it * kThreads;
+      const int tube = idx / R2;
+      if (idx < T * R2 && tube < Tb) {
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) v[it][n1] = __ldg(src + tube * P + R2 * n1 + idx % R2);
+        for (int n1 = 0; n1 < R1; ++n1) v[it][n1] = __ldg(src + tube * P + R2 * n1 + idx % R2);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      const int idx = threadIdx.x + it * kThreads;
+      const int tube = idx / R2;
+      bool real = idx < T * R2 && tube < Tb;
+      const float2* src = job.in;
+      if (real) {
+        const long long t = t0 + tube;
+        const int plane = t >= per_plane;
+        const long long rem = t - (plane ? per_plane : 0);
+        long long row;
+        int col;
+        if (per_plane <= 0x7fffffffLL) {
+          const unsigned r32 = (unsigned)rem, row32 = r32 / (unsigned)cp;
+          row = row32;
+          col = (int)(r32 - row32 * (unsigned)cp);
+        } else {
+          row = rem / cp;
+          col = (int)(rem - row * cp);
+        }
+        real = col < job.cols;  // a phantom tube reads nothing and transforms zeros
+        src = job.in + (((long long)plane * job.rows + row) * job.cols + col) * P;
+      }
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) v[it][n1] = real ? __ldg(src + R2 * n1 + idx % R2) : make_float2(0.f, 0.f);
     }
   }
 #pragma unroll
@@ -347,16 +382,16 @@ __device__ __forceinline__ void fs_fwd_body(const FftFwdJob& job, long long b, c
   const long long ld = job.ld;
   const long long slab = (long long)job.rows * ld;  // one (plane, part, f) slab
   const long long part = (long long)P * slab;
-  auto spec_off = [&](long long t) {  // [plane][part 0][f 0][row][col] of tube t
+  auto spec_off = [&](long long t) {  // [plane][part 0][f 0][row][col] of run tube t
     const long long plane = t / per_plane;
     const long long rem = t - plane * per_plane;
-    const long long row = rem / job.cols;
-    return plane * NPARTS * P * slab + row * ld + (rem - row * job.cols);
+    const long long row = rem / cp;
+    return plane * NPARTS * P * slab + row * ld + (rem - row * cp);
   };
-  // Tube pairs (4-byte bf16 pair stores) when the row has an even number of
-  // columns and two tubes' R2 values fit in registers.
+  // Tube pairs (4-byte bf16 pair stores) when the run rows are even and two
+  // tubes' R2 values fit in registers.
   constexpr bool kPairs = R2 <= 10;
-  if (kPairs && (job.cols & 1) == 0) {
+  if (kPairs && (cp & 1) == 0) {
     // tube pairs share a row: 16-byte / 4-byte stores
     constexpr int TH = T / 2;
     const int tube = 2 * (threadIdx.x % TH);
@@ -864,6 +899,11 @@ cudaError_t launch_fft_inv_grouped(const FftGroupJob* d_jobs, const int* d_job_o
     default: return inv_grouped_launch<0>(d_jobs, d_job_of_block, block0, nblocks, d_ptrs, ws, d_tw, smem, st);
   }
 #undef QTP_INV_GROUPED_CASE
+}
+
+int fft_fwd_run_cols(int p, int fmt, int cols) {
+  const bool two_pass = fft_fixed_tubes(p, false) != 0 && split_of(p, false).r1 != 0;
+  return two_pass && fmt != FMT_C32 && (cols & 1) ? cols + 1 : cols;
 }
 
 int fft_fixed_tubes(int p, bool inv) {

@@ -91,6 +91,11 @@ struct FftInvJob {
 };
 
 int fft_tubes_per_block(int p, bool inv);  // tubes per CTA of the forward / inverse transform
+// Columns of the forward transform's run space for a tensor of `cols`
+// columns written in format fmt: cols + 1 when the two-pass body pads odd
+// rows for bf16 spectra (the phantom tube's stores land in the row padding),
+// else cols.  Runs = ceil(2 rows fft_fwd_run_cols / tubes per CTA).
+int fft_fwd_run_cols(int p, int fmt, int cols);
 size_t fft_smem_bytes_for(int p, bool inv);  // dynamic shared memory of one such CTA
 
 // Grouped (batched) tube FFTs: one job per tensor of each product.
