@@ -149,9 +149,9 @@ qtp_status encode_tmaps(qtp_batch_plan* b, char* ws, cudaStream_t st) {
   for (int i = 0; i < b->n_probs; ++i) {
     const GroupProblem& P = b->h_probs[i];
     char* tA = (char*)b->h_tmaps + (size_t)i * 256;
-    if (!encode_group_map(tA, ws + P.sa_off, P.M, P.K, P.lda, P.p, np, false, msg, sizeof(msg)))
+    if (!encode_group_map(tA, ws + P.sa_off, P.M, P.K, P.lda, P.p, np, false, !P.trans, msg, sizeof(msg)))
       return set_error(QTP_ERR_CUDA, "batched tensor map (A of product %d): %s", b->prod_of_prob[i], msg);
-    if (!encode_group_map(tA + 128, ws + P.sb_off, P.K, P.N, P.ldb, P.p, np, true, msg, sizeof(msg)))
+    if (!encode_group_map(tA + 128, ws + P.sb_off, P.K, P.N, P.ldb, P.p, np, true, false, msg, sizeof(msg)))
       return set_error(QTP_ERR_CUDA, "batched tensor map (B of product %d): %s", b->prod_of_prob[i], msg);
   }
   BP_CUDA(cudaMemcpyAsync(b->d_tmaps, b->h_tmaps, (size_t)b->n_probs * 256, cudaMemcpyHostToDevice, st),

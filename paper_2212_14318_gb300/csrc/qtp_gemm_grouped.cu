@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
           }
         }
         const int nkb = (P.K + GBK - 1) / GBK;
-        // plain: A tile 128 rows (two 64-row boxes), B tiles one 64-column box;
+        // plain: A tile 128 rows of all parts (one box), B tiles one 64-column box;
         // transposed: B tiles 128 rows of s (two 64-column boxes), A tile 64 rows
         const uint32_t tx_bytes = (uint32_t)(NP * (P.trans ? 2 * G_SLOT + G_SLOT / 2 : G_SLOT + G_SLOT));
         for (int kk = 0; kk < 2 * nkb; ++kk, ++it) {
@@ -175,6 +175,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
           const int pa = (int)gv_bit(V.a_plane, 0, kh) * NP;
           const int pb0 = (int)gv_bit(V.b_plane, 0, kh) * NP, pb1 = (int)gv_bit(V.b_plane, 1, kh) * NP;
           const uint32_t st0 = base + (uint32_t)s * STAGE;
+          // plain: the 128-row A tile of all NP parts in one copy (its tensor
+          // map's box spans the parts)
+          if (!P.trans) tma_load_4d(st0, tmA, full + 8 * s, k0, T.mt * GBM, T.f, pa);
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             const uint32_t sh = st0 + (uint32_t)q * G_SLOT;
@@ -187,9 +190,6 @@ __global__ void __launch_bounds__(kGThreads, 1)
               tma_load_4d(h1 + 128u * GBK, tmB, full + 8 * s, c + 64, k0, gb, pb1 + q);
               tma_load_4d(sh, tmA, full + 8 * s, k0, T.nt * GBN, T.f, pa + q);
             } else {
-              const int r = T.mt * GBM;  // 128 rows of m
-              tma_load_4d(sh, tmA, full + 8 * s, k0, r, T.f, pa + q);
-              tma_load_4d(sh + 64u * 32u, tmA, full + 8 * s, k0, r + 64, T.f, pa + q);
               tma_load_4d(h0, tmB, full + 8 * s, T.nt * GBN, k0, gb, pb0 + q);
               tma_load_4d(h1, tmB, full + 8 * s, T.nt * GBN, k0, gb, pb1 + q);
             }
@@ -357,7 +357,7 @@ EncodeTiledFn encode_fn() {
 // the grouped kernel: box (16, 64) with the 32-byte swizzle for A's K-major
 // spectra, (64, 16) with the 128-byte swizzle for B's MN-major spectra.
 bool encode_group_map(void* tm, const void* base, int rows, int cols, int ld, int p, int nparts, bool mn_major,
-                      char* msg, size_t msglen) {
+                      bool all_parts, char* msg, size_t msglen) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) {
     snprintf(msg, msglen, "cuTensorMapEncodeTiled unavailable");
@@ -365,7 +365,10 @@ bool encode_group_map(void* tm, const void* base, int rows, int cols, int ld, in
   }
   cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)p, (cuuint64_t)(2 * nparts)};
   cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * rows, (cuuint64_t)ld * 2 * rows * p};
-  cuuint32_t box[4] = {mn_major ? 64u : (cuuint32_t)GBK, mn_major ? (cuuint32_t)GBK : 64u, 1, 1};
+  // all_parts (K-major only): one box is a whole 128-row A tile in all nparts
+  // bf16 parts of one plane, landing part after part 4 KB apart
+  cuuint32_t box[4] = {mn_major ? 64u : (cuuint32_t)GBK, mn_major ? (cuuint32_t)GBK : (all_parts ? (cuuint32_t)GBM : 64u),
+                       1, all_parts ? (cuuint32_t)nparts : 1u};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(reinterpret_cast<CUtensorMap*>(tm), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base),
                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -234,7 +234,7 @@ constexpr int kGroupSimtBM = 64, kGroupSimtBN = 128;
 // Tensor map of a spectra tensor for the grouped tensor-core kernel (K-major A
 // or MN-major B), written to host memory at *tm (128 bytes).
 bool encode_group_map(void* tm, const void* base, int rows, int cols, int ld, int p, int nparts, bool mn_major,
-                      char* msg, size_t msglen);
+                      bool all_parts, char* msg, size_t msglen);
 
 bool tc_supported();
 
