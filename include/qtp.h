@@ -57,7 +57,7 @@ extern "C" {
 typedef enum {
   QTP_OK = 0,
   QTP_ERR_INVALID_ARG = 1,  /* bad shape, null or misaligned pointer       */
-  QTP_ERR_UNSUPPORTED = 2,  /* precision or size this build does not do   */
+  QTP_ERR_UNSUPPORTED = 2,  /* precision or size the library does not do */
   QTP_ERR_WORKSPACE = 3,    /* workspace missing or smaller than required */
   QTP_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed          */
   QTP_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up         */

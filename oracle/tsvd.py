@@ -37,10 +37,10 @@ So U, S, V follow from one SVD M_f = W diag(s) Z^H per frequency pair
   (a quaternion SVD).  The first half takes one vector per pair, projected
   off the vectors already chosen and their partners.
 
-Reading (the design doc lists it): the paper defines no T-SVD; the split of each
-pair's 2k singular values into odd and even ranks is this build's
-convention (it makes the tubal-rank-r truncation keep the 2r largest
-singular values of every M_f, the best rank-2r approximation of each).
+Reading: the paper defines no T-SVD; the split of each pair's 2k singular
+values into odd and even ranks is a convention chosen here (it makes the
+tubal-rank-r truncation keep the 2r largest singular values of every M_f,
+the best rank-2r approximation of each).
 
 Parity pins (``tests/test_oracle_tsvd.py``): reconstruction, orthogonality
 and f-diagonality checked with the T-product by its definition
