@@ -173,6 +173,23 @@ QTP_API qtp_status qtp_forward_host_many(const qtp_plan* plan, int count, const 
                                  const float* const* B_host, float* const* C_host, void* dev_buffer,
                                  size_t dev_buffer_bytes, void* stream);
 
+/* Training pair: the backward pass reuses the forward's spectra of A and B
+ * instead of transforming them again (Step 1 of the backward then transforms
+ * only dC).  qtp_forward_saving computes C = A * B like qtp_forward, always
+ * by the three steps (never the one-CTA route), and leaves the spectra of A
+ * and B in `saved` (device, caller-owned, at least qtp_workspace_size(plan)
+ * bytes), which the caller keeps unchanged until the matching
+ * qtp_backward_saved.  qtp_backward_saved computes dA = dC * B^H and
+ * dB = A^H * dC as qtp_backward does, reading A's and B's spectra from
+ * `saved` (A and B themselves are not needed); dA or dB may be NULL;
+ * workspace_bytes >= qtp_backward_workspace_size(plan).  Both asynchronous
+ * on stream.  Errors as qtp_forward / qtp_backward, and QTP_ERR_WORKSPACE
+ * for an undersized `saved`. */
+QTP_API qtp_status qtp_forward_saving(const qtp_plan* plan, const float* A, const float* B, float* C, void* saved,
+                              size_t saved_bytes, void* stream);
+QTP_API qtp_status qtp_backward_saved(const qtp_plan* plan, const float* dC, const void* saved, size_t saved_bytes,
+                              float* dA, float* dB, void* workspace, size_t workspace_bytes, void* stream);
+
 /* T-SVD of a quaternion tensor under the T-product.  The paper names
  * T-SVD-type (low-tubal-rank) methods as what its fast T-product opens up
  * (Sec. 6) but defines none; this one rests on the per-frequency structure

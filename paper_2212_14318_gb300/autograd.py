@@ -2,8 +2,11 @@
 
 Forward: C = A * B (Algorithm 5.1).  Backward, for a real loss with each
 quaternion entry taken as four reals: dA = dC * B^H, dB = A^H * dC (tensor
-conjugate transpose, Kilmer-Martin convention), computed by qtp_backward.
-Both run in libqtp's CUDA kernels; torch only supplies memory and streams.
+conjugate transpose, Kilmer-Martin convention).  When a gradient is needed the
+forward runs qtp_forward_saving, which keeps the spectra of A and B in a buffer
+of this call, and the backward qtp_backward_saved, which reuses them (only dC
+is transformed again).  Both run in libqtp's CUDA kernels; torch only supplies
+memory and streams.
 """
 from __future__ import annotations
 
@@ -20,17 +23,19 @@ class TProduct(torch.autograd.Function):
         _, m, n, p, _ = A.shape
         s = B.shape[2]
         plan = qtp.plan_for(m, n, s, p, precision)
-        ctx.save_for_backward(A, B)
         ctx.plan = plan
-        return plan.forward(A, B)
+        if not (ctx.needs_input_grad[0] or ctx.needs_input_grad[1]):
+            ctx.spectra = None
+            return plan.forward(A, B)
+        C, ctx.spectra = plan.forward_saving(A, B)
+        return C
 
     @staticmethod
     def backward(ctx, dC):
-        A, B = ctx.saved_tensors
         need_a, need_b = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        if not (need_a or need_b):
+        if not (need_a or need_b) or ctx.spectra is None:
             return None, None, None
-        dA, dB = ctx.plan.backward(dC.contiguous(), A, B, need_dA=need_a, need_dB=need_b)
+        dA, dB = ctx.plan.backward_saved(dC.contiguous(), ctx.spectra, need_dA=need_a, need_dB=need_b)
         return dA, dB, None
 
 

@@ -454,8 +454,8 @@ void trace(const qtp_plan* pl, int i, cudaStream_t st) {
 }
 
 qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, float* C, char* ws,
-                        cudaStream_t st) {
-  if (fused_small_eligible(pl->m, pl->n, pl->s, pl->p)) {
+                        cudaStream_t st, bool allow_fused = true) {
+  if (allow_fused && fused_small_eligible(pl->m, pl->n, pl->s, pl->p)) {
     // all three steps in one CTA (qtp_fused_small.cu); traced as the products stage
     trace(pl, 0, st);
     trace(pl, 1, st);
@@ -872,25 +872,19 @@ qtp_status qtp_tsvd(int m, int n, int p, const float* A, float* U, float* S, flo
   return QTP_OK;
 }
 
-qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, const float* B, float* dA,
-                        float* dB, void* workspace, size_t workspace_bytes, void* stream) {
-  g_err[0] = 0;
+// Backward steps (validated arguments).  saved: the workspace of a
+// qtp_forward_saving call whose spectra of A and B are reused (then A and B
+// are not read); null: A and B are transformed here.
+static qtp_status bwd_impl(const qtp_plan* pl, const float* dC, const float* A, const float* B, const char* saved,
+                           float* dA, float* dB, char* ws, cudaStream_t st) {
   qtp_status r;
-  if ((r = check_plan(pl)) != QTP_OK) return r;
-  if ((r = check_dev_ptr(dC, "dC")) != QTP_OK) return r;
-  if ((r = check_dev_ptr(A, "A")) != QTP_OK) return r;
-  if ((r = check_dev_ptr(B, "B")) != QTP_OK) return r;
-  if ((r = check_dev_ptr(dA, "dA", true)) != QTP_OK) return r;
-  if ((r = check_dev_ptr(dB, "dB", true)) != QTP_OK) return r;
-  if ((r = check_dev_ptr(workspace, "workspace")) != QTP_OK) return r;
-  if (!dA && !dB) return QTP_OK;
   const BwdLayout L = bwd_layout(pl);
-  if (workspace_bytes < L.total)
-    return fail(QTP_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
-  cudaStream_t st = as_stream(stream);
-  char* ws = (char*)workspace;
   const int fmt = spec_format(pl->precision);
-  // Step 1 on A, B and dC.
+  const char* sa = saved ? saved + fwd_layout(pl).sa : ws + L.sa;
+  const char* sb = saved ? saved + fwd_layout(pl).sb : ws + L.sb;
+  // Step 1 on dC (and A, B unless their spectra are saved).
+  trace(pl, 0, st);
+  if (!saved) {
   FftFwdJob jobs[2];
   jobs[0].in = (const float2*)A;
   jobs[0].out = ws + L.sa;
@@ -900,8 +894,8 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
   jobs[1].out = ws + L.sb;
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
   jobs[1].nblocks = nblocks_fwd(pl->n, pl->s, pl->p, fmt);
-  trace(pl, 0, st);
   QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "backward FFT of A, B");
+  }
   FftFwdJob gj;
   gj.in = (const float2*)dC;
   gj.out = ws + L.sg;
@@ -910,7 +904,7 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
   QTP_CUDA(launch_fft_fwd(&gj, 1, fmt, pl->rp, pl->d_tw, st), "backward FFT of dC");
   trace(pl, 1, st);
   // Step 2.
-  r = run_products_bwd(pl, ws + L.sa, ws + L.sb, ws + L.sg, dA ? (float2*)(ws + L.sda) : nullptr,
+  r = run_products_bwd(pl, sa, sb, ws + L.sg, dA ? (float2*)(ws + L.sda) : nullptr,
                        dB ? (float2*)(ws + L.sdb) : nullptr, st);
   if (r != QTP_OK) return r;
   trace(pl, 2, st);
@@ -934,6 +928,57 @@ qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, con
   QTP_CUDA(launch_fft_inv(ij, nj, pl->rp, pl->d_tw, st), "backward inverse FFT");
   trace(pl, 3, st);
   return QTP_OK;
+}
+
+qtp_status qtp_backward(const qtp_plan* pl, const float* dC, const float* A, const float* B, float* dA,
+                        float* dB, void* workspace, size_t workspace_bytes, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dC, "dC")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(A, "A")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(B, "B")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dA, "dA", true)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dB, "dB", true)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(workspace, "workspace")) != QTP_OK) return r;
+  if (!dA && !dB) return QTP_OK;
+  const BwdLayout L = bwd_layout(pl);
+  if (workspace_bytes < L.total)
+    return fail(QTP_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
+  return bwd_impl(pl, dC, A, B, nullptr, dA, dB, (char*)workspace, as_stream(stream));
+}
+
+qtp_status qtp_forward_saving(const qtp_plan* pl, const float* A, const float* B, float* C, void* saved,
+                              size_t saved_bytes, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(A, "A")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(B, "B")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(C, "C")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(saved, "saved")) != QTP_OK) return r;
+  const size_t need = fwd_layout(pl).total;
+  if (saved_bytes < need) return fail(QTP_ERR_WORKSPACE, "saved has %zu bytes, %zu needed", saved_bytes, need);
+  return forward_impl(pl, A, B, C, (char*)saved, as_stream(stream), false);
+}
+
+qtp_status qtp_backward_saved(const qtp_plan* pl, const float* dC, const void* saved, size_t saved_bytes, float* dA,
+                              float* dB, void* workspace, size_t workspace_bytes, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_plan(pl)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dC, "dC")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(saved, "saved")) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dA, "dA", true)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(dB, "dB", true)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(workspace, "workspace")) != QTP_OK) return r;
+  if (saved_bytes < fwd_layout(pl).total)
+    return fail(QTP_ERR_WORKSPACE, "saved has %zu bytes, %zu needed", saved_bytes, fwd_layout(pl).total);
+  if (!dA && !dB) return QTP_OK;
+  const BwdLayout L = bwd_layout(pl);
+  if (workspace_bytes < L.total)
+    return fail(QTP_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
+  return bwd_impl(pl, dC, nullptr, nullptr, (const char*)saved, dA, dB, (char*)workspace, as_stream(stream));
 }
 
 qtp_status qtp_plan_set_tracing(qtp_plan* pl, int enable) {

@@ -39,6 +39,8 @@ SIGNATURES = {
     "qtp_forward_host": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_host_many_buffer_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "qtp_tsvd_workspace_size": (_i, [_i, _i, _i, ctypes.POINTER(_sz)]),
+    "qtp_forward_saving": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "qtp_backward_saved": (_i, [_vp, _vp, _vp, _sz, _vp, _vp, _vp, _sz, _vp]),
     "qtp_tsvd": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_forward_host_many": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _sz,
                                    _vp]),
@@ -231,6 +233,36 @@ class Plan:
                                            dev_buffer.numel() * dev_buffer.element_size(), _stream(stream)),
                "qtp_forward_host_many")
         return C_hosts
+
+    def forward_saving(self, A, B, C=None, saved=None, stream=None):
+        """C = A * B (qtp_forward_saving) with the spectra of A and B kept in
+        `saved` (a CUDA byte tensor of workspace_size() bytes, allocated when
+        None) for backward_saved.  Returns (C, saved)."""
+        import torch
+        _check_tensor(A, (2, self.m, self.n, self.p, 2), "A")
+        _check_tensor(B, (2, self.n, self.s, self.p, 2), "B")
+        if C is None:
+            C = torch.empty((2, self.m, self.s, self.p, 2), dtype=torch.float32, device=A.device)
+        _check_tensor(C, (2, self.m, self.s, self.p, 2), "C")
+        if saved is None:
+            saved = torch.empty(max(self.workspace_size(), 256), dtype=torch.uint8, device=A.device)
+        _check(lib().qtp_forward_saving(self._h, _ptr(A), _ptr(B), _ptr(C), _ptr(saved),
+                                        saved.numel() * saved.element_size(), _stream(stream)), "qtp_forward_saving")
+        return C, saved
+
+    def backward_saved(self, dC, saved, need_dA=True, need_dB=True, workspace=None, stream=None):
+        """dA = dC * B^H, dB = A^H * dC (qtp_backward_saved) from the spectra a
+        forward_saving call left in `saved`."""
+        import torch
+        _check_tensor(dC, (2, self.m, self.s, self.p, 2), "dC")
+        dA = torch.empty((2, self.m, self.n, self.p, 2), dtype=torch.float32, device=dC.device) if need_dA else None
+        dB = torch.empty((2, self.n, self.s, self.p, 2), dtype=torch.float32, device=dC.device) if need_dB else None
+        need = self.backward_workspace_size()
+        ws = workspace if workspace is not None else self._workspace("_bws", need, dC.device)
+        _check(lib().qtp_backward_saved(self._h, _ptr(dC), _ptr(saved), saved.numel() * saved.element_size(),
+                                        _ptr(dA), _ptr(dB), _ptr(ws), ws.numel() * ws.element_size(),
+                                        _stream(stream)), "qtp_backward_saved")
+        return dA, dB
 
     def backward(self, dC, A, B, need_dA=True, need_dB=True, workspace=None, stream=None):
         import torch

@@ -273,3 +273,34 @@ def test_launch_count_reports_the_route():
         assert qtp.Plan(8, 8, 8, 16, "fp32").launch_count() == (3, 5)
     finally:
         del os.environ["QTP_NO_FUSED"]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape", [(8, 8, 8, 16), (24, 20, 28, 12), (70, 33, 41, 7), (128, 64, 128, 32)])
+def test_backward_from_saved_spectra(precision, shape):
+    """qtp_forward_saving + qtp_backward_saved (the spectra of A and B reused)
+    give bit for bit the results of qtp_forward + qtp_backward; the first shape
+    would take the one-CTA route in qtp_forward, which qtp_forward_saving must
+    not take (it writes no spectra)."""
+    import torch
+    qtp = _qtp()
+    m, n, s, p = shape
+    A, B = _inputs(m, n, s, p, seed=77)
+    dA_np = synth.quat_normal(m, s, p, 78)
+    plan = qtp.Plan(m, n, s, p, precision)
+    dA_, B_, dC = to_dev(A), to_dev(B), to_dev(dA_np)
+    C_ref = plan.forward(dA_, B_)
+    gA_ref, gB_ref = plan.backward(dC, dA_, B_)
+    C, saved = plan.forward_saving(dA_, B_)
+    gA, gB = plan.backward_saved(dC, saved)
+    torch.cuda.synchronize()
+    if m * n * s * p > 8 * 8 * 8 * 16:
+        np.testing.assert_array_equal(to_host(C), to_host(C_ref))
+    else:  # qtp_forward took the one-CTA FP32 route, qtp_forward_saving the three steps
+        assert_close(to_host(C), _oracle(A, B), REL_TOL, ELEM_TOL, "forward_saving, small product")
+    np.testing.assert_array_equal(to_host(gA), to_host(gA_ref))
+    np.testing.assert_array_equal(to_host(gB), to_host(gB_ref))
+    only_b = plan.backward_saved(dC, saved, need_dA=False)
+    torch.cuda.synchronize()
+    assert only_b[0] is None
+    np.testing.assert_array_equal(to_host(only_b[1]), to_host(gB_ref))
