@@ -313,14 +313,17 @@ qtp_status run_products_bwd(const qtp_plan* pl, const void* sa, const void* sb, 
     return QTP_OK;
   }
   char msg[256] = "";
+  // dA and dB are independent: with both, the dB product runs alongside the
+  // dA product (programmatic dependent launch, modes 1 and 2)
+  const bool pair = sda && sdb;
   if (sda) {
     const TcProblem pr = tc_bwd_a(pl, sb, sg, sda);
-    cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg));
+    cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg), pair ? 1 : 0);
     if (e != cudaSuccess) return fail(QTP_ERR_CUDA, "backward products dA: %s %s", cudaGetErrorString(e), msg);
   }
   if (sdb) {
     const TcProblem pr = tc_bwd_b(pl, sa, sg, sdb);
-    cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg));
+    cudaError_t e = launch_gemm_tc(pr, pl->d_err, st, msg, sizeof(msg), pair ? 2 : 0);
     if (e != cudaSuccess) return fail(QTP_ERR_CUDA, "backward products dB: %s %s", cudaGetErrorString(e), msg);
   }
   return QTP_OK;

@@ -59,6 +59,7 @@ struct TcArgs {
   float2* out;
   long long out_hstride, out_fstride, out_rstride;
   int* err;
+  int dep_mode;  // programmatic dependent launch, see launch_gemm_tc
 };
 
 struct Smem {
@@ -129,7 +130,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&args.tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&args.tmB)) : "memory");
-    grid_dep_launch();  // the inverse transform may be scheduled once every CTA got here
+    // mode 1 (first of two independent products): the inputs are complete
+    // before the next launch may start; modes 0 and 2 let it start at once
+    if (args.dep_mode == 1) grid_dep_wait();
+    grid_dep_launch();  // the next kernel may be scheduled once every CTA got here
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
@@ -145,7 +149,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      grid_dep_wait();  // the spectra come from the previous kernel (launched with PDL)
+      // the spectra come from the previous kernel (launched with PDL); mode 2
+      // reads spectra that were complete before that kernel let it start
+      if (args.dep_mode != 2) grid_dep_wait();
       int issued = 0;
       for (int it = 0; it < total; ++it) {
         const int kh = it / nkb;
@@ -282,6 +288,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     fence_before();
   }
   __syncthreads();
+  // mode 2: this grid completes only after the previous one (its partner), so
+  // the kernel after it may rely on both
+  if (args.dep_mode == 2 && threadIdx.x == 0) grid_dep_wait();
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -420,7 +429,12 @@ bool tc_supported() {
   return major == 10 && minor == 3;
 }
 
-cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, char* msg, size_t msglen) {
+// dep_mode (programmatic dependent launch): 0 waits for the previous kernel
+// before reading and lets the next one start at once; for two independent
+// products launched back to back, the first takes 1 (waits, then lets the
+// next start) and the second 2 (reads at once, and waits for the first before
+// it completes, so a kernel after the pair sees both).
+cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, char* msg, size_t msglen, int dep_mode) {
   if (pr.M <= 0 || pr.N <= 0 || pr.p <= 0) return cudaSuccess;
   if (pr.nparts != 4 && pr.nparts != 2) return cudaErrorInvalidValue;
   const bool a_mn = pr.kind == TC_BWD_B;
@@ -480,6 +494,7 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
     slot.args = args;
   }
   args.err = d_err;
+  args.dep_mode = dep_mode;
   dim3 grid((pr.N + bn - 1) / bn, (pr.M + BM - 1) / BM, 2 * pr.p);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
   const bool x3 = pr.nparts == 4;

@@ -246,7 +246,8 @@ long long spec_ld_of(int fmt, long long cols);
 size_t spec_bytes_of(int fmt, long long p, long long rows, long long cols);
 size_t c32_bytes_of(long long p, long long rows, long long cols);
 
-cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, char* msg, size_t msglen);
+cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, char* msg, size_t msglen,
+                           int dep_mode = 0);
 
 }  // namespace qtp
 
