@@ -103,8 +103,10 @@ QTP_API qtp_status qtp_plan_get_tiles(const qtp_plan* plan, int* tiles3);
  * call with both outputs requested (*backward) issue for this plan: 3 and 5
  * (Steps 1, 2, 3 of Algorithm 5.1; the backward transforms A and B, then dC,
  * forms dA and dB, and transforms both back in one launch), or 1 forward
- * launch for products small enough to run whole in one CTA.  Library
- * extension with no counterpart in the paper; for launch accounting.
+ * launch for products small enough to run whole in one CTA.  The training
+ * pair issues 3 (qtp_forward_saving) and *backward - 1 (qtp_backward_saved,
+ * which does not transform A and B).  Library extension with no counterpart
+ * in the paper; for launch accounting.
  * Errors: QTP_ERR_INVALID_ARG for a NULL plan or output pointer. */
 QTP_API qtp_status qtp_plan_launch_count(const qtp_plan* plan, int* forward, int* backward);
 
