@@ -5,9 +5,11 @@
 // computes both output halves,
 //   C1(f) = A1(f) B1(f) - A2(f) conj(B2(-f)),  C2(f) = A1(f) B2(f) + A2(f) conj(B1(-f)),
 // so each K step loads the A tile (plane kh at f) once for both halves and
-// one B tile per half (B's two planes at f for kh = 0, at -f for kh = 1):
-// operand fetch, not MMA, bounds these small products.  The MMA width is the
-// tile's valid columns rounded up to 16.  A product with trans set is computed
+// one B tile per half (B's two planes at f for kh = 0, at -f for kh = 1).  The
+// MMA width is the tile's valid columns rounded up to 16.  On these small
+// products the time goes to issuing the many narrow (N <= 64) MMAs, about 80
+// cycles each against 37 of tensor work (per-role timestamps), not to operand
+// fetch or the epilogue.  A product with trans set is computed
 // as C^T = B^T A^T, rows over s and columns over m (the larger of m and s fills
 // the MMA's 128 rows): B's MN-major spectra are then the A operands (one per
 // half) and A's K-major spectra the shared B operand, and the epilogue writes
