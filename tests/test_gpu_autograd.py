@@ -106,7 +106,8 @@ def _step_size(Aq, Bq):
 
 
 def test_low_tubal_rank_factorisation_200_steps_with_replay_and_resume():
-    """Gradient descent on ||A*B - T||^2 (tubal rank <= 64 of a 128 x 128 target)."""
+    """Gradient descent on ||A*B - T||^2 (tubal rank <= 64 of a 128 x 128 target),
+    bounded below by the truncated T-SVD of T."""
     import torch
     from paper_2212_14318_gb300.autograd import tprod
     rng = np.random.default_rng(33)
@@ -140,6 +141,13 @@ def test_low_tubal_rank_factorisation_200_steps_with_replay_and_resume():
     losses = np.array(losses)
     assert np.all(np.diff(losses) <= 1e-6 * losses[:-1]), "loss increased"
     assert losses[-1] < 0.75 * losses[0]
+    # A*B has tubal rank <= 64, so by Eckart-Young on every M_f (and Parseval)
+    # no step can go below the truncated T-SVD of T (FP64 oracle); the descent
+    # gets within 1% of it in 200 steps (FP64 replay: 1.008)
+    from oracle import tsvd as TS
+    best = TS.truncation_error_sq(TS.tsvd(Tq)[3], N)
+    assert losses[-1] >= best * (1 - 1e-4), (losses[-1], best)
+    assert losses[-1] <= 1.03 * best, losses[-1] / best
 
     # FP64 replay of the first 10 steps with oracle gradients
     Aq, Bq = planes_to_comp(A0), planes_to_comp(B0)
