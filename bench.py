@@ -306,21 +306,22 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- traffic record
 
-def kernel_source_digest():
+def kernel_source_digest(files=None):
+    """Hash of the CUDA sources (all of them, or the named files of csrc/)."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2212_14318_gb300", "csrc"))):
+    for f in sorted(files or os.listdir(os.path.join(ROOT, "paper_2212_14318_gb300", "csrc"))):
         h.update(open(os.path.join(ROOT, "paper_2212_14318_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(stage, workload):
     """DRAM bytes per launch from the committed ncu record, if it was taken on this workload and the
-    sources have not changed since."""
+    sources the captured kernels are built from (the record's `sources`) have not changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    if rec.get("source_digest") != kernel_source_digest() or rec.get("workload") != workload:
+    if rec.get("source_digest") != kernel_source_digest(rec.get("sources")) or rec.get("workload") != workload:
         return None
     ent = rec.get("stages", {}).get(stage)
     return None if ent is None else ent.get("dram_bytes_per_launch")

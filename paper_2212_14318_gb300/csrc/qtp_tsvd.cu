@@ -16,14 +16,20 @@
 //           values come in equal pairs, and the factors keep the pattern
 //           (second half = Q^T conj(first half)).
 //
-// Kernel: one CTA per frequency pair runs a one-sided (Hestenes) Jacobi SVD
-// of M_f, or of M_f^H when m < n (the columns are the 2 min(m, n) side), in
-// shared memory when it fits, else in a per-pair global scratch: cyclic
+// Kernel: each frequency pair runs a one-sided (Hestenes) Jacobi SVD of M_f,
+// or of M_f^H when m < n (the columns are the 2 min(m, n) side): cyclic
 // sweeps in round-robin order (disjoint column pairs per round, one warp per
 // pair), each 2x2 step a phase that makes the off-diagonal real followed by
 // the symmetric Jacobi rotation.  Then the columns' norms are sorted, null
 // columns completed by Gram-Schmidt, and the factors written to the spectra
-// of U, V and S (frequency-major, for the inverse transform).
+// of U, V and S (frequency-major, for the inverse transform).  When a pair's
+// buffers fit in shared memory one CTA does all of it there; otherwise they
+// sit in a per-pair global scratch (resident in L2) and a cluster of up to
+// four CTAs shares the sweeps, the round's column pairs dealt over all its
+// warps with a cluster barrier between rounds, and the cluster's first CTA
+// finishes alone.  The rotations and their order are the same either way.
+#include <cooperative_groups.h>
+
 #include "qtp_internal.h"
 
 namespace qtp {
@@ -35,6 +41,29 @@ constexpr int kTsvdWarps = kTsvdThreads / 32;
 constexpr int kTsvdMaxCols = 128;   // 2 min(m, n)
 constexpr int kTsvdMaxSweeps = 40;
 constexpr size_t kTsvdSmemMax = 200 * 1024;  // dynamic shared memory of the in-smem variant
+constexpr int kTsvdClusterMax = 4;            // CTAs per pair of the global-scratch variant
+
+namespace cg = cooperative_groups;
+
+// Loads and stores of the working buffers.  In the global-scratch variant
+// several CTAs (SMs) of a cluster write and read the same columns, so those
+// go through L2 only (.cg), and no SM keeps a stale copy in its L1.
+template <bool G>
+__device__ __forceinline__ float2 ldw(const float2* p) {
+  if constexpr (G) return __ldcg(p);
+  else return *p;
+}
+template <bool G>
+__device__ __forceinline__ void stw(float2* p, float2 v) {
+  if constexpr (G) __stcg(p, v);
+  else *p = v;
+}
+// Barrier over the CTAs that share a pair (release / acquire at cluster scope).
+template <bool G>
+__device__ __forceinline__ void pair_sync() {
+  if constexpr (G) cg::this_cluster().sync();
+  else __syncthreads();
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -170,39 +199,54 @@ __device__ float block_project_partners(float2* w, const float2* B, int nb, long
   return v;
 }
 
-// Rows per lane a column pair keeps in registers during one Jacobi step:
-// X columns up to 32 kRegRows rows, V columns up to 32 kRegV (C <= 128).
-constexpr int kRegRows = 16;
-constexpr int kRegV = 4;
+template <bool G>
+__device__ __forceinline__ float4 ldw4(const float4* p) {
+  if constexpr (G) return __ldcg(p);
+  else return *p;
+}
+template <bool G>
+__device__ __forceinline__ void stw4(float4* p, float4 v) {
+  if constexpr (G) __stcg(p, v);
+  else *p = v;
+}
 
 // One Jacobi step on columns x, y of X (R rows) and vx, vy of V (C rows) by
-// one warp, with every entry a lane touches loaded at once into registers
-// (one round trip to memory per pair), rotated there and stored once.
-// Returns whether it rotated.
+// one warp, every entry a lane touches loaded at once into registers (one
+// round trip to memory per pair), rotated there and stored once.  Entries
+// move in 16-byte pairs (R, C even; columns 16-byte aligned): a lane holds
+// up to NX pairs of an X column (R <= 64 NX) and NV of a V column
+// (C <= 64 NV).  Returns whether it rotated.
+template <bool G, int NX, int NV>
 __device__ __forceinline__ bool jacobi_pair_reg(float2* __restrict__ x, float2* __restrict__ y,
                                                 float2* __restrict__ vx, float2* __restrict__ vy, int R, int C,
                                                 float tol, int lane) {
-  float2 xr[kRegRows], yr[kRegRows], vxr[kRegV], vyr[kRegV];
+  float4* x4 = reinterpret_cast<float4*>(x);
+  float4* y4 = reinterpret_cast<float4*>(y);
+  float4* vx4 = reinterpret_cast<float4*>(vx);
+  float4* vy4 = reinterpret_cast<float4*>(vy);
+  const int R2 = R >> 1, C2 = C >> 1;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 xr[NX], yr[NX], vxr[NV], vyr[NV];
 #pragma unroll
-  for (int i = 0; i < kRegRows; ++i) {
+  for (int i = 0; i < NX; ++i) {
     const int r = lane + 32 * i;
-    xr[i] = r < R ? x[r] : make_float2(0.f, 0.f);
-    yr[i] = r < R ? y[r] : make_float2(0.f, 0.f);
+    xr[i] = r < R2 ? ldw4<G>(x4 + r) : z4;
+    yr[i] = r < R2 ? ldw4<G>(y4 + r) : z4;
   }
 #pragma unroll
-  for (int i = 0; i < kRegV; ++i) {
+  for (int i = 0; i < NV; ++i) {
     const int r = lane + 32 * i;
-    vxr[i] = r < C ? vx[r] : make_float2(0.f, 0.f);
-    vyr[i] = r < C ? vy[r] : make_float2(0.f, 0.f);
+    vxr[i] = r < C2 ? ldw4<G>(vx4 + r) : z4;
+    vyr[i] = r < C2 ? ldw4<G>(vy4 + r) : z4;
   }
   float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
 #pragma unroll
-  for (int i = 0; i < kRegRows; ++i) {
-    const float2 u = xr[i], v = yr[i];
-    al = fmaf(u.x, u.x, fmaf(u.y, u.y, al));
-    be = fmaf(v.x, v.x, fmaf(v.y, v.y, be));
-    gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));
-    gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, gi));
+  for (int i = 0; i < NX; ++i) {
+    const float4 u = xr[i], v = yr[i];
+    al = fmaf(u.x, u.x, fmaf(u.y, u.y, fmaf(u.z, u.z, fmaf(u.w, u.w, al))));
+    be = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, be))));
+    gr = fmaf(u.x, v.x, fmaf(u.y, v.y, fmaf(u.z, v.z, fmaf(u.w, v.w, gr))));
+    gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, fmaf(u.z, v.w, fmaf(-u.w, v.z, gi))));
   }
   al = warp_sum(al);
   be = warp_sum(be);
@@ -214,22 +258,30 @@ __device__ __forceinline__ bool jacobi_pair_reg(float2* __restrict__ x, float2* 
   const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
   const float cs = 1.f / sqrtf(1.f + tt * tt), sn = cs * tt;
   const float2 ce = make_float2(gr / gabs, -gi / gabs);
+  // [x, y] <- [x, conj(e) y] [[c, s], [-s, c]] on both entries of a pair
+  auto rot = [&](const float4 u, const float4 w, float4& xo, float4& yo) {
+    const float2 v0 = cmul(ce, make_float2(w.x, w.y)), v1 = cmul(ce, make_float2(w.z, w.w));
+    xo = make_float4(cs * u.x - sn * v0.x, cs * u.y - sn * v0.y, cs * u.z - sn * v1.x, cs * u.w - sn * v1.y);
+    yo = make_float4(sn * u.x + cs * v0.x, sn * u.y + cs * v0.y, sn * u.z + cs * v1.x, sn * u.w + cs * v1.y);
+  };
 #pragma unroll
-  for (int i = 0; i < kRegRows; ++i) {
+  for (int i = 0; i < NX; ++i) {
     const int r = lane + 32 * i;
-    const float2 u = xr[i], v = cmul(ce, yr[i]);
-    if (r < R) {
-      x[r] = make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
-      y[r] = make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+    if (r < R2) {
+      float4 xo, yo;
+      rot(xr[i], yr[i], xo, yo);
+      stw4<G>(x4 + r, xo);
+      stw4<G>(y4 + r, yo);
     }
   }
 #pragma unroll
-  for (int i = 0; i < kRegV; ++i) {
+  for (int i = 0; i < NV; ++i) {
     const int r = lane + 32 * i;
-    const float2 u = vxr[i], v = cmul(ce, vyr[i]);
-    if (r < C) {
-      vx[r] = make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
-      vy[r] = make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+    if (r < C2) {
+      float4 xo, yo;
+      rot(vxr[i], vyr[i], xo, yo);
+      stw4<G>(vx4 + r, xo);
+      stw4<G>(vy4 + r, yo);
     }
   }
   return true;
@@ -241,7 +293,7 @@ struct TsvdArgs {
   float2* Vh;        // [plane][f][n][k]
   float2* Sh;        // [plane][f][k][k], zeroed by the host
   float* sigma;      // [f][k]
-  float2* scratch;   // per-pair buffers when shared memory is too small (else null)
+  float2* scratch;   // per-pair buffers when shared memory is too small (G variant; else null)
   long long scratch_stride;
   int m, n, p, k;
   int R, C;          // rows and columns of the matrix the Jacobi sweeps work on
@@ -255,16 +307,29 @@ __device__ __forceinline__ void rr_pair(int C, int rr, int t, int& a, int& b) {
   b = 1 + (rr + C - 2 - t) % (C - 1);
 }
 
+// G = false: one CTA per pair, buffers in dynamic shared memory.  G = true:
+// a cluster of nc CTAs per pair (blockIdx.x = pair * nc + rank), buffers in
+// the global scratch; every CTA of the cluster takes the same barriers in the
+// same order (the loop bounds and the convergence test are cluster-uniform).
+template <bool G>
 __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   extern __shared__ float4 tsvd_smem[];
   __shared__ float sig[kTsvdMaxCols];
   __shared__ int perm[kTsvdMaxCols];
   __shared__ int rotations;
-  const int q = blockIdx.x;
+  int nc = 1, rank = 0;
+  if constexpr (G) {
+    nc = (int)cg::this_cluster().num_blocks();
+    rank = (int)cg::this_cluster().block_rank();
+  }
+  const int q = blockIdx.x / nc;
   const int p = a.p, m = a.m, n = a.n, k = a.k, R = a.R, C = a.C;
   const int f = q, g = (p - q) % p;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float2* X = a.scratch ? a.scratch + (long long)q * a.scratch_stride : reinterpret_cast<float2*>(tsvd_smem);
+  // thread and warp indices over the CTAs that share the pair
+  const int gtid = rank * kTsvdThreads + tid, gthreads = nc * kTsvdThreads;
+  const int gwarp = rank * kTsvdWarps + warp, gwarps = nc * kTsvdWarps;
+  float2* X = G ? a.scratch + (long long)q * a.scratch_stride : reinterpret_cast<float2*>(tsvd_smem);
   float2* V = X + (long long)R * C;           // C x C
   float2* Tm = V + (long long)C * C;          // C x C: the Newton-Schulz factor
   float2* Tmp = Tm + (long long)C * C;        // C x C: products
@@ -286,12 +351,13 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
     }
     return cconj(H1g[(long long)rr * n + (c - n)]);
   };
-  for (long long idx = tid; idx < (long long)R * C; idx += kTsvdThreads) {
+  for (long long idx = gtid; idx < (long long)R * C; idx += gthreads) {
     const int c = (int)(idx / R), r = (int)(idx - (long long)c * R);
-    X[idx] = a.tall ? Mval(r, c) : cconj(Mval(c, r));
+    stw<G>(X + idx, a.tall ? Mval(r, c) : cconj(Mval(c, r)));
   }
-  for (int idx = tid; idx < C * C; idx += kTsvdThreads) V[idx] = make_float2(idx % (C + 1) == 0 ? 1.f : 0.f, 0.f);
-  __syncthreads();
+  for (int idx = gtid; idx < C * C; idx += gthreads)
+    stw<G>(V + idx, make_float2(idx % (C + 1) == 0 ? 1.f : 0.f, 0.f));
+  pair_sync<G>();
 
   // 2. cyclic one-sided Jacobi sweeps; X = M V throughout.
   // A rotation is skipped once |x^H y| <= tol |x| |y|; FP32 dot products over
@@ -303,64 +369,67 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   // to V and to X (keeping X = M V), and phase 1 sweeps again (two or three
   // sweeps restore the columns' orthogonality).
   const float tol = 2e-6f * fmaxf(1.f, sqrtf((float)R / 256.f));
-  const bool reg_path = R <= 32 * kRegRows && C <= 32 * kRegV;
+  const bool reg_path = R <= 512 && C <= 128;  // jacobi_pair_reg's register capacity
   for (int phase = 0; phase < 2; ++phase) {
   if (phase == 1) {
     // Tm = (3 I - V^H V) / 2, column-major
-    for (int idx = tid; idx < C * C; idx += kTsvdThreads) {
+    for (int idx = gtid; idx < C * C; idx += gthreads) {
       const int j = idx / C, i = idx - j * C;
       const float2* vi = V + (long long)i * C;
       const float2* vj = V + (long long)j * C;
       float re = 0.f, im = 0.f;
       for (int r = 0; r < C; ++r) {
-        const float2 x = vi[r], y = vj[r];
+        const float2 x = ldw<G>(vi + r), y = ldw<G>(vj + r);
         re = fmaf(x.x, y.x, fmaf(x.y, y.y, re));
         im = fmaf(x.x, y.y, fmaf(-x.y, y.x, im));
       }
-      Tm[idx] = make_float2(0.5f * ((i == j ? 3.f : 0.f) - re), -0.5f * im);
+      stw<G>(Tm + idx, make_float2(0.5f * ((i == j ? 3.f : 0.f) - re), -0.5f * im));
     }
-    __syncthreads();
+    pair_sync<G>();
     // V <- V Tm, then X <- X Tm in blocks of C rows, through Tmp
     for (int blk = -1; blk < (R + C - 1) / C; ++blk) {
       float2* src = blk < 0 ? V : X;
       const long long lds = blk < 0 ? C : R;
       const int r0 = blk < 0 ? 0 : blk * C;
       const int rows = blk < 0 ? C : min(C, R - r0);
-      for (int idx = tid; idx < rows * C; idx += kTsvdThreads) {
+      for (int idx = gtid; idx < rows * C; idx += gthreads) {
         const int j = idx / rows, r = idx - j * rows;
         float re = 0.f, im = 0.f;
         for (int l = 0; l < C; ++l) {
-          const float2 x = src[(long long)l * lds + r0 + r], t = Tm[(long long)j * C + l];
+          const float2 x = ldw<G>(src + (long long)l * lds + r0 + r), t = ldw<G>(Tm + (long long)j * C + l);
           re = fmaf(x.x, t.x, fmaf(-x.y, t.y, re));
           im = fmaf(x.x, t.y, fmaf(x.y, t.x, im));
         }
-        Tmp[(long long)j * rows + r] = make_float2(re, im);
+        stw<G>(Tmp + (long long)j * rows + r, make_float2(re, im));
       }
-      __syncthreads();
-      for (int idx = tid; idx < rows * C; idx += kTsvdThreads) {
+      pair_sync<G>();
+      for (int idx = gtid; idx < rows * C; idx += gthreads) {
         const int j = idx / rows, r = idx - j * rows;
-        src[(long long)j * lds + r0 + r] = Tmp[idx];
+        stw<G>(src + (long long)j * lds + r0 + r, ldw<G>(Tmp + idx));
       }
-      __syncthreads();
+      pair_sync<G>();
     }
   }
   for (int sweep = 0; sweep < kTsvdMaxSweeps; ++sweep) {
     if (tid == 0) rotations = 0;
-    __syncthreads();
+    pair_sync<G>();
     for (int rr = 0; rr < C - 1; ++rr) {
-      for (int t = warp; t < C / 2; t += kTsvdWarps) {
+      for (int t = gwarp; t < C / 2; t += gwarps) {
         int ca, cb;
         rr_pair(C, rr, t, ca, cb);
         float2* x = X + (long long)ca * R;
         float2* y = X + (long long)cb * R;
         if (reg_path) {
-          if (jacobi_pair_reg(x, y, V + (long long)ca * C, V + (long long)cb * C, R, C, tol, lane) && lane == 0)
-            atomicAdd(&rotations, 1);
+          float2* vx = V + (long long)ca * C;
+          float2* vy = V + (long long)cb * C;
+          const bool rotated = R <= 256 ? jacobi_pair_reg<G, 4, 2>(x, y, vx, vy, R, C, tol, lane)
+                                        : jacobi_pair_reg<G, 8, 2>(x, y, vx, vy, R, C, tol, lane);
+          if (rotated && lane == 0) atomicAdd(&rotations, 1);
           continue;
         }
         float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
         for (int r = lane; r < R; r += 32) {
-          const float2 u = x[r], v = y[r];
+          const float2 u = ldw<G>(x + r), v = ldw<G>(y + r);
           al = fmaf(u.x, u.x, fmaf(u.y, u.y, al));
           be = fmaf(v.x, v.x, fmaf(v.y, v.y, be));
           gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));
@@ -378,27 +447,38 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
           const float cs = 1.f / sqrtf(1.f + tt * tt), sn = cs * tt;
           const float2 ce = make_float2(gr / gabs, -gi / gabs);
           for (int r = lane; r < R; r += 32) {
-            const float2 u = x[r], v = cmul(ce, y[r]);
-            x[r] = make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
-            y[r] = make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+            const float2 u = ldw<G>(x + r), v = cmul(ce, ldw<G>(y + r));
+            stw<G>(x + r, make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y));
+            stw<G>(y + r, make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y));
           }
           float2* vx = V + (long long)ca * C;
           float2* vy = V + (long long)cb * C;
           for (int r = lane; r < C; r += 32) {
-            const float2 u = vx[r], v = cmul(ce, vy[r]);
-            vx[r] = make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
-            vy[r] = make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+            const float2 u = ldw<G>(vx + r), v = cmul(ce, ldw<G>(vy + r));
+            stw<G>(vx + r, make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y));
+            stw<G>(vy + r, make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y));
           }
           if (lane == 0) atomicAdd(&rotations, 1);
         }
       }
-      __syncthreads();
+      pair_sync<G>();
     }
-    const int done = rotations == 0;
-    __syncthreads();
+    // every CTA of the pair sums the same counters, after the round's barrier
+    // and before the next sweep clears them (the barrier below)
+    int total = rotations;
+    if constexpr (G) {
+      total = 0;
+      for (int j = 0; j < nc; ++j) total += *cg::this_cluster().map_shared_rank(&rotations, j);
+    }
+    const bool done = total == 0;
+    pair_sync<G>();
     if (done) break;
   }
   }
+  // the rest (sorting, completion, scatter) is the first CTA's alone; the
+  // others leave after the last barrier, with no access to their shared
+  // memory pending
+  if (rank != 0) return;
 
   // 3. singular values (column norms), sorted decreasing (ties by index)
   for (int c = warp; c < C; c += kTsvdWarps) {
@@ -575,20 +655,36 @@ cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, 
   a.C = 2 * k;
   const long long elems = tsvd_pair_elems(m, n);
   const size_t bytes = sizeof(float2) * (size_t)elems;
-  size_t smem = 0;
   if (bytes <= kTsvdSmemMax) {
     a.scratch = nullptr;
     a.scratch_stride = 0;
-    smem = bytes;
     static std::atomic<unsigned long long> attr_set{0};
-    cudaError_t e = ensure_smem_attr(attr_set, tsvd_pair_kernel, kTsvdSmemMax);
+    cudaError_t e = ensure_smem_attr(attr_set, tsvd_pair_kernel<false>, kTsvdSmemMax);
     if (e != cudaSuccess) return e;
-  } else {
-    if (!scratch) return cudaErrorInvalidValue;
-    a.scratch = scratch;
-    a.scratch_stride = elems;
+    tsvd_pair_kernel<false><<<p / 2 + 1, kTsvdThreads, bytes, st>>>(a);
+    return cudaGetLastError();
   }
-  tsvd_pair_kernel<<<p / 2 + 1, kTsvdThreads, smem, st>>>(a);
+  if (!scratch) return cudaErrorInvalidValue;
+  a.scratch = scratch;
+  a.scratch_stride = elems;
+  // enough CTAs that every column pair of a round has its own warp (C / 2
+  // pairs), at most kTsvdClusterMax
+  int nc = (a.C / 2 + kTsvdWarps - 1) / kTsvdWarps;
+  nc = nc < 1 ? 1 : (nc > kTsvdClusterMax ? kTsvdClusterMax : nc);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((p / 2 + 1) * nc));
+  cfg.blockDim = dim3(kTsvdThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, tsvd_pair_kernel<true>, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
