@@ -210,35 +210,14 @@ __device__ __forceinline__ void stw4(float4* p, float4 v) {
   else *p = v;
 }
 
-// One Jacobi step on columns x, y of X (R rows) and vx, vy of V (C rows) by
-// one warp, every entry a lane touches loaded at once into registers (one
-// round trip to memory per pair), rotated there and stored once.  Entries
-// move in 16-byte pairs (R, C even; columns 16-byte aligned): a lane holds
-// up to NX pairs of an X column (R <= 64 NX) and NV of a V column
-// (C <= 64 NV).  Returns whether it rotated.
-template <bool G, int NX, int NV>
-__device__ __forceinline__ bool jacobi_pair_reg(float2* __restrict__ x, float2* __restrict__ y,
-                                                float2* __restrict__ vx, float2* __restrict__ vy, int R, int C,
-                                                float tol, int lane) {
-  float4* x4 = reinterpret_cast<float4*>(x);
-  float4* y4 = reinterpret_cast<float4*>(y);
-  float4* vx4 = reinterpret_cast<float4*>(vx);
-  float4* vy4 = reinterpret_cast<float4*>(vy);
-  const int R2 = R >> 1, C2 = C >> 1;
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 xr[NX], yr[NX], vxr[NV], vyr[NV];
-#pragma unroll
-  for (int i = 0; i < NX; ++i) {
-    const int r = lane + 32 * i;
-    xr[i] = r < R2 ? ldw4<G>(x4 + r) : z4;
-    yr[i] = r < R2 ? ldw4<G>(y4 + r) : z4;
-  }
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    const int r = lane + 32 * i;
-    vxr[i] = r < C2 ? ldw4<G>(vx4 + r) : z4;
-    vyr[i] = r < C2 ? ldw4<G>(vy4 + r) : z4;
-  }
+// One Jacobi step on a column pair held in registers by one warp: columns x,
+// y of X (R rows) and vx, vy of V (C rows), in 16-byte pairs of entries
+// (R, C even), pair r = lane + 32 i of a column in element i (NX pairs of an
+// X column, R <= 64 NX; NV of a V column, C <= 64 NV; the pairs past the
+// column are zero and stay zero).  Rotates in place; returns whether it did.
+template <int NX, int NV>
+__device__ __forceinline__ bool rotate_regs(float4 (&xr)[NX], float4 (&yr)[NX], float4 (&vxr)[NV],
+                                            float4 (&vyr)[NV], float tol) {
   float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
 #pragma unroll
   for (int i = 0; i < NX; ++i) {
@@ -259,31 +238,57 @@ __device__ __forceinline__ bool jacobi_pair_reg(float2* __restrict__ x, float2* 
   const float cs = 1.f / sqrtf(1.f + tt * tt), sn = cs * tt;
   const float2 ce = make_float2(gr / gabs, -gi / gabs);
   // [x, y] <- [x, conj(e) y] [[c, s], [-s, c]] on both entries of a pair
-  auto rot = [&](const float4 u, const float4 w, float4& xo, float4& yo) {
+  auto rot = [&](float4& u, float4& w) {
     const float2 v0 = cmul(ce, make_float2(w.x, w.y)), v1 = cmul(ce, make_float2(w.z, w.w));
-    xo = make_float4(cs * u.x - sn * v0.x, cs * u.y - sn * v0.y, cs * u.z - sn * v1.x, cs * u.w - sn * v1.y);
-    yo = make_float4(sn * u.x + cs * v0.x, sn * u.y + cs * v0.y, sn * u.z + cs * v1.x, sn * u.w + cs * v1.y);
+    const float4 xo =
+        make_float4(cs * u.x - sn * v0.x, cs * u.y - sn * v0.y, cs * u.z - sn * v1.x, cs * u.w - sn * v1.y);
+    w = make_float4(sn * u.x + cs * v0.x, sn * u.y + cs * v0.y, sn * u.z + cs * v1.x, sn * u.w + cs * v1.y);
+    u = xo;
   };
 #pragma unroll
-  for (int i = 0; i < NX; ++i) {
-    const int r = lane + 32 * i;
-    if (r < R2) {
-      float4 xo, yo;
-      rot(xr[i], yr[i], xo, yo);
-      stw4<G>(x4 + r, xo);
-      stw4<G>(y4 + r, yo);
-    }
-  }
+  for (int i = 0; i < NX; ++i) rot(xr[i], yr[i]);
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    const int r = lane + 32 * i;
-    if (r < C2) {
-      float4 xo, yo;
-      rot(vxr[i], vyr[i], xo, yo);
-      stw4<G>(vx4 + r, xo);
-      stw4<G>(vy4 + r, yo);
-    }
+  for (int i = 0; i < NV; ++i) rot(vxr[i], vyr[i]);
+  return true;
+}
+
+// A column (n2 16-byte pairs) into / out of the register layout of rotate_regs.
+template <bool G, int N>
+__device__ __forceinline__ void load_col(float4 (&r)[N], const float4* src, int n2, int lane) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int e = lane + 32 * i;
+    r[i] = e < n2 ? ldw4<G>(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+}
+template <bool G, int N>
+__device__ __forceinline__ void store_col(const float4 (&r)[N], float4* dst, int n2, int lane) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int e = lane + 32 * i;
+    if (e < n2) stw4<G>(dst + e, r[i]);
+  }
+}
+
+// One Jacobi step on columns x, y of X and vx, vy of V in memory, by one
+// warp: every entry a lane touches loaded at once into registers (one round
+// trip to memory per pair), rotated there and stored once.  Columns 16-byte
+// aligned.  Returns whether it rotated.
+template <bool G, int NX, int NV>
+__device__ __forceinline__ bool jacobi_pair_reg(float2* __restrict__ x, float2* __restrict__ y,
+                                                float2* __restrict__ vx, float2* __restrict__ vy, int R, int C,
+                                                float tol, int lane) {
+  const int R2 = R >> 1, C2 = C >> 1;
+  float4 xr[NX], yr[NX], vxr[NV], vyr[NV];
+  load_col<G>(xr, reinterpret_cast<const float4*>(x), R2, lane);
+  load_col<G>(yr, reinterpret_cast<const float4*>(y), R2, lane);
+  load_col<G>(vxr, reinterpret_cast<const float4*>(vx), C2, lane);
+  load_col<G>(vyr, reinterpret_cast<const float4*>(vy), C2, lane);
+  if (!rotate_regs(xr, yr, vxr, vyr, tol)) return false;
+  store_col<G>(xr, reinterpret_cast<float4*>(x), R2, lane);
+  store_col<G>(yr, reinterpret_cast<float4*>(y), R2, lane);
+  store_col<G>(vxr, reinterpret_cast<float4*>(vx), C2, lane);
+  store_col<G>(vyr, reinterpret_cast<float4*>(vy), C2, lane);
   return true;
 }
 
@@ -307,11 +312,107 @@ __device__ __forceinline__ void rr_pair(int C, int rr, int t, int& a, int& b) {
   b = 1 + (rr + C - 2 - t) % (C - 1);
 }
 
+// Jacobi sweeps with the columns in registers (the cluster variant when
+// R <= 256).  Pair slot t (one per warp of the cluster) keeps its two columns
+// of X and V in registers for a whole phase; between rounds every slot hands
+// one column to each neighbour through shared memory (distributed shared
+// memory between the cluster's CTAs), which is the round-robin order of
+// rr_pair run as a ring (T = C/2 - 1):
+//   slot 0 keeps column 0 and takes slot 1's first column as its second;
+//   slot t, 0 < t < T, takes slot t+1's first column and slot t-1's second;
+//   slot T moves its second column to first and takes slot T-1's second.
+// At a sweep boundary slot t holds rr_pair(C, 0, t) again.  The hand-over
+// buffers alternate between two sets, so the one cluster barrier per round
+// orders both the hand-over and the reuse of a set two rounds later.  The
+// rotations and their order are those of the sweeps from memory.
+__device__ __forceinline__ void ring_sweeps(float2* X, float2* V, int R, int C, float tol, int nc, int rank,
+                                            int warp, int lane, int tid, int* rotations, float4* slots) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int R2 = R >> 1, C2 = C >> 1, L = R2 + C2;
+  const int T = C / 2 - 1;
+  const int t = rank * kTsvdWarps + warp;
+  const bool active = t <= T;
+  float4 xa[4], xb[4], va[2], vb[2];
+  int ca = 0, cb = 0;
+  if (active) {
+    rr_pair(C, 0, t, ca, cb);
+    load_col<true>(xa, reinterpret_cast<const float4*>(X + (long long)ca * R), R2, lane);
+    load_col<true>(xb, reinterpret_cast<const float4*>(X + (long long)cb * R), R2, lane);
+    load_col<true>(va, reinterpret_cast<const float4*>(V + (long long)ca * C), C2, lane);
+    load_col<true>(vb, reinterpret_cast<const float4*>(V + (long long)cb * C), C2, lane);
+  }
+  // hand-over buffer of slot u: set s, kind 0 (its first column) or 1 (its second)
+  auto local_slot = [&](int s, int kind, int w) { return slots + ((s * 2 + kind) * kTsvdWarps + w) * L; };
+  auto slot_of = [&](int s, int kind, int u) -> const float4* {
+    return cl.map_shared_rank(local_slot(s, kind, u % kTsvdWarps), u / kTsvdWarps);
+  };
+  int set = 0;
+  for (int sweep = 0; sweep < kTsvdMaxSweeps; ++sweep) {
+    if (tid == 0) *rotations = 0;
+    cl.sync();
+    for (int rr = 0; rr < C - 1; ++rr) {
+      if (active && rotate_regs(xa, xb, va, vb, tol) && lane == 0) atomicAdd(rotations, 1);
+      if (T == 0) continue;  // one pair: nothing moves
+      if (active && t >= 1) {
+        float4* s = local_slot(set, 0, warp);
+        store_col<false>(xa, s, R2, lane);
+        store_col<false>(va, s + R2, C2, lane);
+      }
+      if (active && t < T) {
+        float4* s = local_slot(set, 1, warp);
+        store_col<false>(xb, s, R2, lane);
+        store_col<false>(vb, s + R2, C2, lane);
+      }
+      cl.sync();
+      if (active) {
+        if (t == 0) {
+          const float4* s = slot_of(set, 0, 1);
+          load_col<false>(xb, s, R2, lane);
+          load_col<false>(vb, s + R2, C2, lane);
+        } else {
+          if (t < T) {
+            const float4* s = slot_of(set, 0, t + 1);
+            load_col<false>(xa, s, R2, lane);
+            load_col<false>(va, s + R2, C2, lane);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xa[i] = xb[i];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) va[i] = vb[i];
+          }
+          const float4* s = slot_of(set, 1, t - 1);
+          load_col<false>(xb, s, R2, lane);
+          load_col<false>(vb, s + R2, C2, lane);
+        }
+      }
+      set ^= 1;
+    }
+    // every CTA sums the same counters, after the last round's increments and
+    // before the next sweep clears them
+    cl.sync();
+    int total = 0;
+    for (int j = 0; j < nc; ++j) total += *cl.map_shared_rank(rotations, j);
+    const bool done = total == 0;
+    cl.sync();
+    if (done) break;
+  }
+  if (active) {
+    rr_pair(C, 0, t, ca, cb);
+    store_col<true>(xa, reinterpret_cast<float4*>(X + (long long)ca * R), R2, lane);
+    store_col<true>(xb, reinterpret_cast<float4*>(X + (long long)cb * R), R2, lane);
+    store_col<true>(va, reinterpret_cast<float4*>(V + (long long)ca * C), C2, lane);
+    store_col<true>(vb, reinterpret_cast<float4*>(V + (long long)cb * C), C2, lane);
+  }
+  cl.sync();
+}
+
 // G = false: one CTA per pair, buffers in dynamic shared memory.  G = true:
 // a cluster of nc CTAs per pair (blockIdx.x = pair * nc + rank), buffers in
-// the global scratch; every CTA of the cluster takes the same barriers in the
-// same order (the loop bounds and the convergence test are cluster-uniform).
-template <bool G>
+// the global scratch, the sweeps from memory or (RING) in registers; every
+// CTA of the cluster takes the same barriers in the same order (the loop
+// bounds and the convergence test are cluster-uniform).  The sweep variants
+// are separate kernels so that neither's registers constrain the other's.
+template <bool G, bool RING = false>
 __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   extern __shared__ float4 tsvd_smem[];
   __shared__ float sig[kTsvdMaxCols];
@@ -409,6 +510,10 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
       }
       pair_sync<G>();
     }
+  }
+  if constexpr (RING) {
+    ring_sweeps(X, V, R, C, tol, nc, rank, warp, lane, tid, &rotations, reinterpret_cast<float4*>(tsvd_smem));
+    continue;
   }
   for (int sweep = 0; sweep < kTsvdMaxSweeps; ++sweep) {
     if (tid == 0) rotations = 0;
@@ -667,6 +772,17 @@ cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, 
   if (!scratch) return cudaErrorInvalidValue;
   a.scratch = scratch;
   a.scratch_stride = elems;
+  // columns in registers when a lane's share fits rotate_regs<4, 2> (R <= 256,
+  // C <= 128); the hand-over buffers: 2 sets x 2 columns x 16 slots per CTA
+  const bool ring = a.R <= 256;
+  const size_t ring_smem = ring ? (size_t)4 * kTsvdWarps * (a.R / 2 + a.C / 2) * sizeof(float4) : 0;
+  if (ring_smem > kTsvdSmemMax) return cudaErrorInvalidValue;
+  auto kfn = ring ? tsvd_pair_kernel<true, true> : tsvd_pair_kernel<true, false>;
+  static std::atomic<unsigned long long> attr_set{0};
+  if (ring) {
+    cudaError_t e = ensure_smem_attr(attr_set, tsvd_pair_kernel<true, true>, kTsvdSmemMax);
+    if (e != cudaSuccess) return e;
+  }
   // enough CTAs that every column pair of a round has its own warp (C / 2
   // pairs), at most kTsvdClusterMax
   int nc = (a.C / 2 + kTsvdWarps - 1) / kTsvdWarps;
@@ -674,7 +790,7 @@ cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((p / 2 + 1) * nc));
   cfg.blockDim = dim3(kTsvdThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = ring_smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -683,7 +799,7 @@ cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, tsvd_pair_kernel<true>, a);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kfn, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
