@@ -27,7 +27,10 @@
 // sit in a per-pair global scratch (resident in L2) and a cluster of up to
 // four CTAs shares the sweeps, the round's column pairs dealt over all its
 // warps with a cluster barrier between rounds, and the cluster's first CTA
-// finishes alone.  The rotations and their order are the same either way.
+// finishes alone.  When 2 max(m, n) <= 256 the columns stay in registers for
+// a whole phase and pass between neighbouring warps (ring_sweeps) instead of
+// going through L2 every round.  The rotations and their order are the same
+// in every variant.
 #include <cooperative_groups.h>
 
 #include "qtp_internal.h"
