@@ -35,8 +35,13 @@
  *   or misaligned pointers, an unsupported precision and an undersized
  *   workspace are rejected on the host before any launch.  A failed launch
  *   maps to QTP_ERR_CUDA.  Kernels that wait on a barrier give up after a
- *   bounded number of polls, record it in the plan's error word and return;
- *   qtp_plan_sync reports that as QTP_ERR_TIMEOUT.
+ *   bounded time (2 s), record it in the plan's error word and return;
+ *   qtp_plan_sync reports that as QTP_ERR_TIMEOUT.  For tests of that path
+ *   the environment variables QTP_INJECT_WITHHOLD=<k> and
+ *   QTP_INJECT_WAIT_NS=<ns>, read at every tensor-core launch, make the
+ *   products' operand producer skip K step k (its operands never arrive) and
+ *   bound every wait by ns nanoseconds: the waits expire, the kernels unwind
+ *   and the next sync returns QTP_ERR_TIMEOUT.  Unset, they change nothing.
  * - qtp_last_error() returns a thread-local message for the last failure.
  */
 #ifndef QTP_H_
@@ -70,7 +75,10 @@ typedef enum {
  *   QTP_PREC_BF16X3 : each FP32 operand x is split x = hi + lo with
  *                     hi = bf16(x), lo = bf16(x - hi); the products
  *                     hi*hi + hi*lo + lo*hi run on the tcgen05 tensor cores
- *                     with FP32 accumulation (relative error ~1e-6).
+ *                     with FP32 accumulation (relative error 4e-6 to 7e-6 on
+ *                     N(0,1) data, at most 1e-5, for every reduction length:
+ *                     long reductions fold their tensor-core partial sums
+ *                     into FP32 at least every 512 terms).
  *   QTP_PREC_BF16   : hi*hi only (relative error ~1e-3; comparison only). */
 typedef enum { QTP_PREC_FP32 = 0, QTP_PREC_BF16X3 = 1, QTP_PREC_BF16 = 2 } qtp_precision;
 
@@ -96,22 +104,32 @@ QTP_API qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p,
 QTP_API qtp_status qtp_plan_destroy(qtp_plan* plan);
 
 /* Tile shapes the plan uses for its (forward, dA, dB) products: 0 = built-in
- * rule, 1 = 256 wide, 2 = 128 wide, 3 = 128 wide with split accumulators. */
+ * rule, 1 = 256 wide, 2 = 128 wide, 3 = 128 wide with split accumulators,
+ * 4 = 128 wide with accumulators promoted to FP32 every 512 terms of the
+ * reduction.  The built-in rule picks by the reduction length K per half
+ * (n forward, s for dA, m for dB): 1 or 2 up to 384, 3 up to 1024, 4 beyond,
+ * which keeps QTP_PREC_BF16X3 within 1e-5 relative error for every K the
+ * plan accepts. */
 QTP_API qtp_status qtp_plan_get_tiles(const qtp_plan* plan, int* tiles3);
 
 /* Kernel launches that one qtp_forward call (*forward) and one qtp_backward
  * call with both outputs requested (*backward) issue for this plan: 3 and 5
  * (Steps 1, 2, 3 of Algorithm 5.1; the backward transforms A and B, then dC,
  * forms dA and dB, and transforms both back in one launch), or 1 forward
- * launch for products small enough to run whole in one CTA.  The training
- * pair issues 3 (qtp_forward_saving) and *backward - 1 (qtp_backward_saved,
- * which does not transform A and B).  Library extension with no counterpart
- * in the paper; for launch accounting.
+ * launch for products small enough to run whole in one CTA.  Long tubes
+ * (p > 128 without a one-kernel transform, and with a factor between 4 and
+ * sqrt(p)) transform in two launches each (through an intermediate in the
+ * workspace): 5 and 8.  The training pair issues *forward
+ * (qtp_forward_saving, never the one-CTA route) and *backward minus the
+ * transform launches of A and B (qtp_backward_saved).  Library extension
+ * with no counterpart in the paper; for launch accounting.
  * Errors: QTP_ERR_INVALID_ARG for a NULL plan or output pointer. */
 QTP_API qtp_status qtp_plan_launch_count(const qtp_plan* plan, int* forward, int* backward);
 
 /* Bytes of device workspace qtp_forward needs: the spectra of A and B in the
- * GEMM operand format of the plan's precision plus the FP32 spectrum of C. */
+ * GEMM operand format of the plan's precision plus the FP32 spectrum of C,
+ * and for long tubes (see qtp_plan_launch_count) the FP32 intermediate of the
+ * two-pass transforms. */
 QTP_API qtp_status qtp_workspace_size(const qtp_plan* plan, size_t* bytes);
 
 /* Bytes of device workspace qtp_backward needs (spectra of A, B and dC and
@@ -309,9 +327,11 @@ QTP_API qtp_status qtp_plan_stage_times(const qtp_plan* plan, float* ms3);
  * - Products whose scratch (twiddles + spectra of A, B and C, see
  *   qtp_workspace_size) exceeds the array are rejected with
  *   QTP_ERR_WORKSPACE before any launch.
- * - The first call on each device looks up the array's device address with
- *   that device current (cudaGetSymbolAddress); make that first call before
- *   any stream capture begins.
+ * - Every call looks up the array's device address in the current device's
+ *   context (cudaGetSymbolAddress, which allocates nothing), so the address
+ *   stays valid after a device reset.  The first call on a device loads the
+ *   library's module there; make that first call before any stream capture
+ *   begins.
  * - All calls share the one array and it keeps the last call's contents; each
  *   call clears its error word and rewrites its twiddles.  Calls that overlap
  *   on the GPU (other streams, other threads) race on the array: order them.

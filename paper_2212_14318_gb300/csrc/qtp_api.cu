@@ -55,8 +55,18 @@ size_t c32_bytes(long long p, long long rows, long long cols) {
   return align256((size_t)2 * p * rows * cols * sizeof(float2));
 }
 
+// Intermediate of the two-pass long-tube transforms: the largest set of
+// tensors transformed in one launch (A with B, dC alone, C alone, dA with dB).
+size_t split_scratch_bytes(const qtp_plan* pl) {
+  if (!pl->fft_split_fwd && !pl->fft_split_inv) return 0;
+  const size_t a = align256(fft_split_scratch_bytes(pl->p, pl->m, pl->n));
+  const size_t b = align256(fft_split_scratch_bytes(pl->p, pl->n, pl->s));
+  const size_t c = align256(fft_split_scratch_bytes(pl->p, pl->m, pl->s));
+  return std::max(a + b, c);
+}
+
 struct FwdLayout {
-  size_t sa, sb, sc, total;
+  size_t sa, sb, sc, scr, total;
 };
 
 FwdLayout fwd_layout(const qtp_plan* pl) {
@@ -65,12 +75,13 @@ FwdLayout fwd_layout(const qtp_plan* pl) {
   L.sa = 0;
   L.sb = L.sa + spec_bytes(fmt, pl->p, pl->m, pl->n);
   L.sc = L.sb + spec_bytes(fmt, pl->p, pl->n, pl->s);
-  L.total = L.sc + c32_bytes(pl->p, pl->m, pl->s);
+  L.scr = L.sc + c32_bytes(pl->p, pl->m, pl->s);
+  L.total = L.scr + split_scratch_bytes(pl);
   return L;
 }
 
 struct BwdLayout {
-  size_t sa, sb, sg, sda, sdb, total;
+  size_t sa, sb, sg, sda, sdb, scr, total;
 };
 
 BwdLayout bwd_layout(const qtp_plan* pl) {
@@ -81,8 +92,22 @@ BwdLayout bwd_layout(const qtp_plan* pl) {
   L.sg = L.sb + spec_bytes(fmt, pl->p, pl->n, pl->s);
   L.sda = L.sg + spec_bytes(fmt, pl->p, pl->m, pl->s);
   L.sdb = L.sda + c32_bytes(pl->p, pl->m, pl->n);
-  L.total = L.sdb + c32_bytes(pl->p, pl->n, pl->s);
+  L.scr = L.sdb + c32_bytes(pl->p, pl->n, pl->s);
+  L.total = L.scr + split_scratch_bytes(pl);
   return L;
+}
+
+// Step 1 / Step 3 transforms of a plan: one kernel, or the two-pass form for
+// long tubes (scratch: the layout's intermediate).
+cudaError_t plan_fft_fwd(const qtp_plan* pl, const FftFwdJob* jobs, int njobs, int fmt, char* scratch,
+                         cudaStream_t st) {
+  if (pl->fft_split_fwd) return launch_fft_fwd_split(jobs, njobs, fmt, pl->p, pl->d_tw, (float2*)scratch, st);
+  return launch_fft_fwd(jobs, njobs, fmt, pl->rp, pl->d_tw, st);
+}
+
+cudaError_t plan_fft_inv(const qtp_plan* pl, const FftInvJob* jobs, int njobs, char* scratch, cudaStream_t st) {
+  if (pl->fft_split_inv) return launch_fft_inv_split(jobs, njobs, pl->p, pl->d_tw, (float2*)scratch, st);
+  return launch_fft_inv(jobs, njobs, pl->rp, pl->d_tw, st);
 }
 
 qtp_status check_plan(const qtp_plan* pl) {
@@ -152,13 +177,19 @@ TcView tcv(int tensor, int plane, int fneg, int conj) {
 // bf16 spectra: which planes, frequencies, conjugations and signs feed each
 // (output half, K half).  See run_products_fwd / run_products_bwd.
 TcProblem tc_fwd(const qtp_plan* pl, const void* sa, const void* sb, float2* sc) {
-  const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
+  return make_tc_fwd(pl->m, pl->n, pl->s, pl->p, pl->precision == QTP_PREC_BF16X3 ? 4 : 2, pl->tile[0], sa, sb, sc);
+}
+
+}  // namespace
+
+TcProblem qtp::make_tc_fwd(int m, int n, int s, int p, int nparts, int tile, const void* sa, const void* sb,
+                           float2* sc) {
   TcProblem pr;
   memset(&pr, 0, sizeof(pr));
   pr.kind = TC_FWD;
-  pr.tile = pl->tile[0];
+  pr.tile = tile;
   pr.M = m; pr.N = s; pr.K = n; pr.p = p;
-  pr.nparts = pl->precision == QTP_PREC_BF16X3 ? 4 : 2;
+  pr.nparts = nparts;
   pr.a_base[0] = sa; pr.a_rows[0] = m; pr.a_cols[0] = n; pr.a_ld[0] = (int)spec_ld(FMT_BF16, n);
   pr.b_base[0] = sb; pr.b_rows[0] = n; pr.b_cols[0] = s; pr.b_ld[0] = (int)spec_ld(FMT_BF16, s);
   for (int h = 0; h < 2; ++h) {
@@ -175,6 +206,8 @@ TcProblem tc_fwd(const qtp_plan* pl, const void* sa, const void* sb, float2* sc)
   pr.out_rstride = s;
   return pr;
 }
+
+namespace {
 
 TcProblem tc_bwd_a(const qtp_plan* pl, const void* sb, const void* sg, float2* sda) {
   const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
@@ -332,9 +365,9 @@ qtp_status run_products_bwd(const qtp_plan* pl, const void* sa, const void* sb, 
 // ----------------------------------------------------------------------------
 // Autotuner (QTP_PLAN_AUTOTUNE): for each product kind, time the tensor-core
 // tile candidates that keep the split-BF16 accuracy bound for that kind's
-// reduction length K (128-wide with split accumulators always; 256- and
-// 128-wide single accumulators only for K <= 384) on scratch spectra and keep
-// the fastest.  Results are cached per (device, shape, precision) for the
+// reduction length K (128-wide with promoted accumulators always, with split
+// accumulators for K <= kTcSplitMaxK, 256- and 128-wide single accumulators
+// for K <= kTcSingleMaxK) on scratch spectra and keep the fastest.  Results are cached per (device, shape, precision) for the
 // process and, when QTP_AUTOTUNE_CACHE names a file, across processes.
 // ----------------------------------------------------------------------------
 std::mutex g_tune_mu;
@@ -421,8 +454,10 @@ qtp_status autotune(qtp_plan* pl) {
   std::array<int, 3> best = {TILE_AUTO, TILE_AUTO, TILE_AUTO};
   for (int kind = 0; kind < 3; ++kind) {
     TcProblem pr = kind == 0 ? tc_fwd(pl, sa, sb, out) : kind == 1 ? tc_bwd_a(pl, sb, sg, out) : tc_bwd_b(pl, sa, sg, out);
-    std::vector<int> cands = {TILE_128_SPLIT};
-    if (pr.nparts == 2 || pr.K <= 384) {
+    // candidates that keep split-BF16 within 1e-5 at this reduction length
+    std::vector<int> cands = {TILE_128_PROMOTE};
+    if (pr.nparts == 2 || pr.K <= kTcSplitMaxK) cands.push_back(TILE_128_SPLIT);
+    if (pr.nparts == 2 || pr.K <= kTcSingleMaxK) {
       cands.push_back(TILE_128);
       if (pr.N > 128) cands.push_back(TILE_256);
     }
@@ -481,7 +516,7 @@ qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, floa
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
   jobs[1].nblocks = nblocks_fwd(pl->n, pl->s, pl->p, fmt);
   trace(pl, 0, st);
-  QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "forward tube FFT");
+  QTP_CUDA(plan_fft_fwd(pl, jobs, 2, fmt, ws + L.scr, st), "forward tube FFT");
   trace(pl, 1, st);
   qtp_status r = run_products_fwd(pl, ws + L.sa, ws + L.sb, (float2*)(ws + L.sc), st);
   if (r != QTP_OK) return r;
@@ -491,7 +526,7 @@ qtp_status forward_impl(const qtp_plan* pl, const float* A, const float* B, floa
   ij.out = (float2*)C;
   ij.rows = pl->m; ij.cols = pl->s;
   ij.nblocks = nblocks_for(pl->m, pl->s, pl->p, true);
-  QTP_CUDA(launch_fft_inv(&ij, 1, pl->rp, pl->d_tw, st), "inverse tube FFT");
+  QTP_CUDA(plan_fft_inv(pl, &ij, 1, ws + L.scr, st), "inverse tube FFT");
   trace(pl, 3, st);
   return QTP_OK;
 }
@@ -539,6 +574,8 @@ qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int preci
   pl->m = m; pl->n = n; pl->s = s; pl->p = p;
   pl->precision = precision;
   pl->rp = make_radix_plan(p);
+  pl->fft_split_fwd = fft_split_eligible(p, false) ? 1 : 0;
+  pl->fft_split_inv = fft_split_eligible(p, true) ? 1 : 0;
   pl->d_tw = nullptr;
   pl->d_err = nullptr;
   pl->tracing = 0;
@@ -580,8 +617,10 @@ qtp_status qtp_plan_launch_count(const qtp_plan* pl, int* forward, int* backward
   qtp_status r;
   if ((r = check_plan(pl)) != QTP_OK) return r;
   if (!forward || !backward) return fail(QTP_ERR_INVALID_ARG, "output pointer is NULL");
-  *forward = fused_small_eligible(pl->m, pl->n, pl->s, pl->p) ? 1 : 3;
-  *backward = 5;
+  // each transform step takes two launches in its two-pass form
+  const int sf = pl->fft_split_fwd, si = pl->fft_split_inv;
+  *forward = fused_small_eligible(pl->m, pl->n, pl->s, pl->p) ? 1 : 3 + sf + si;
+  *backward = 5 + 2 * sf + si;
   return QTP_OK;
 }
 
@@ -897,14 +936,14 @@ static qtp_status bwd_impl(const qtp_plan* pl, const float* dC, const float* A, 
   jobs[1].out = ws + L.sb;
   jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
   jobs[1].nblocks = nblocks_fwd(pl->n, pl->s, pl->p, fmt);
-  QTP_CUDA(launch_fft_fwd(jobs, 2, fmt, pl->rp, pl->d_tw, st), "backward FFT of A, B");
+  QTP_CUDA(plan_fft_fwd(pl, jobs, 2, fmt, ws + L.scr, st), "backward FFT of A, B");
   }
   FftFwdJob gj;
   gj.in = (const float2*)dC;
   gj.out = ws + L.sg;
   gj.rows = pl->m; gj.cols = pl->s; gj.ld = (int)spec_ld(fmt, pl->s);
   gj.nblocks = nblocks_fwd(pl->m, pl->s, pl->p, fmt);
-  QTP_CUDA(launch_fft_fwd(&gj, 1, fmt, pl->rp, pl->d_tw, st), "backward FFT of dC");
+  QTP_CUDA(plan_fft_fwd(pl, &gj, 1, fmt, ws + L.scr, st), "backward FFT of dC");
   trace(pl, 1, st);
   // Step 2.
   r = run_products_bwd(pl, sa, sb, ws + L.sg, dA ? (float2*)(ws + L.sda) : nullptr,
@@ -928,7 +967,7 @@ static qtp_status bwd_impl(const qtp_plan* pl, const float* dC, const float* A, 
     ij[nj].nblocks = nblocks_for(pl->n, pl->s, pl->p, true);
     ++nj;
   }
-  QTP_CUDA(launch_fft_inv(ij, nj, pl->rp, pl->d_tw, st), "backward inverse FFT");
+  QTP_CUDA(plan_fft_inv(pl, ij, nj, ws + L.scr, st), "backward inverse FFT");
   trace(pl, 3, st);
   return QTP_OK;
 }
@@ -1035,35 +1074,19 @@ qtp_status qtp_plan_sync(const qtp_plan* pl, void* stream) {
 // QTP_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library holds
 // until the process exits.
 // ----------------------------------------------------------------------------
-#include <mutex>
-
-#define QTP_NOALLOC_MAX_DEVICES 64
-
 static __device__ __align__(256) unsigned char g_noalloc_scratch[QTP_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[QTP_NOALLOC_MAX_DEVICES];
-
-// Device address of the static array on the current device.  In host code the
-// array's name only stands for it, so the address is looked up once per
-// device, with that device current, and cached.
+// Device address of the static array in the current device's context.  In
+// host code the array's name only stands for it; cudaGetSymbolAddress (which
+// allocates nothing) gives the address, looked up on every call so that it
+// stays valid after a device reset or a new primary context.
 qtp_status noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= QTP_NOALLOC_MAX_DEVICES)
-    return fail(QTP_ERR_UNSUPPORTED, "device %d is beyond the %d devices qtp_forward_noalloc tracks", dev,
-                QTP_NOALLOC_MAX_DEVICES);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch array");
-    g_noalloc_ptr[dev] = ptr;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch array");
+  *out = ptr;
   return QTP_OK;
 }
 
@@ -1084,6 +1107,8 @@ extern "C" qtp_status qtp_forward_noalloc(int m, int n, int s, int p, int precis
   pl.m = m; pl.n = n; pl.s = s; pl.p = p;
   pl.precision = precision;
   pl.rp = make_radix_plan(p);
+  pl.fft_split_fwd = fft_split_eligible(p, false) ? 1 : 0;
+  pl.fft_split_inv = fft_split_eligible(p, true) ? 1 : 0;
   // static scratch: [twiddles][error word][forward workspace]
   const size_t tw_bytes = align256((size_t)p * sizeof(float2));
   const size_t ws_off = tw_bytes + 256;

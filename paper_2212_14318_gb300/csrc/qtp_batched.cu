@@ -12,6 +12,10 @@
 // The plan buckets the products by tube length p, then by size, so that CTAs
 // working at the same time share a kernel specialisation and their
 // products' spectra stay in L2; the pointer table keeps the caller's order.
+// A split-BF16 product whose reduction (n per half) is longer than the grouped
+// kernel's single accumulator keeps within 1e-5 (kTcSingleMaxK) runs its
+// products through the single-product kernel instead, whose accumulator mode
+// follows K (one launch each, after the grouped launch, in the same graph).
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -59,6 +63,12 @@ struct qtp_batch_plan {
   // host copies needed to encode tensor maps
   std::vector<GroupProblem> h_probs;
   std::vector<int> prod_of_prob;  // product index of each GroupProblem
+  // products that take the single-product tensor-core kernel (long reductions)
+  struct LongProduct {
+    int m, n, s, p;
+    size_t sa, sb, sc;  // workspace offsets of the spectra of A, B and C_hat
+  };
+  std::vector<LongProduct> long_probs;
   void* h_tmaps = nullptr;        // pinned
   char* tmaps_for_ws = nullptr;   // workspace base the device tensor maps point into
   // per-call pointer staging (pinned, 2 slots) and stream plumbing
@@ -129,9 +139,16 @@ qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing)
   if (b->precision == QTP_PREC_FP32) {
     BP_CUDA(launch_gemm_simt_grouped(b->d_probs, b->d_prob_tile, b->total_tiles, ws, st), "batched products (fp32)");
   } else {
-    BP_CUDA(launch_gemm_tc_grouped(b->d_probs, b->n_probs, b->total_tiles, b->fmt == FMT_BF16X3 ? 4 : 2, ws,
-                                   b->d_err, b->num_sms, st),
+    const int np = b->fmt == FMT_BF16X3 ? 4 : 2;
+    BP_CUDA(launch_gemm_tc_grouped(b->d_probs, b->n_probs, b->total_tiles, np, ws, b->d_err, b->num_sms, st),
             "batched products (tensor cores)");
+    for (const auto& L : b->long_probs) {
+      const TcProblem pr = make_tc_fwd(L.m, L.n, L.s, L.p, np, TILE_AUTO, ws + L.sa, ws + L.sb, (float2*)(ws + L.sc));
+      char msg[256] = "";
+      cudaError_t e = launch_gemm_tc(pr, b->d_err, st, msg, sizeof(msg));
+      if (e != cudaSuccess)
+        return set_error(QTP_ERR_CUDA, "batched products (long reduction): %s %s", cudaGetErrorString(e), msg);
+    }
   }
   trace(b, 2, st, capturing);
   for (const FftRange& r : b->inv_ranges)
@@ -254,6 +271,10 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
     fwd.push_back(job(0, q.m, q.n, sa, fb));
     fwd.push_back(job(1, q.n, q.s, sb, fb));
     inv.push_back(job(2, q.m, q.s, sc, ib));
+    if (tc && fmt == FMT_BF16X3 && q.n > kTcSingleMaxK) {
+      b->long_probs.push_back({q.m, q.n, q.s, q.p, sa, sb, sc});
+      continue;
+    }
     GroupProblem P;
     memset(&P, 0, sizeof(P));
     P.tile_begin = tiles;
@@ -316,12 +337,14 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tw, sizeof(float2) * tw_total);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_fwd, sizeof(FftGroupJob) * fwd.size());
   if (e == cudaSuccess) e = cudaMalloc(&b->d_inv, sizeof(FftGroupJob) * inv.size());
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, sizeof(GroupProblem) * b->n_probs);
+  // (every table at least one entry: a batch of long-reduction products only has no grouped tiles)
+  const size_t nprob_alloc = (size_t)std::max(b->n_probs, 1);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, sizeof(GroupProblem) * nprob_alloc);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(float2*) * 3 * count);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
-  if (e == cudaSuccess && tc) e = cudaMalloc(&b->d_tmaps, (size_t)b->n_probs * 256);
-  if (e == cudaSuccess && tc) e = cudaMallocHost(&b->h_tmaps, (size_t)b->n_probs * 256);
+  if (e == cudaSuccess && tc) e = cudaMalloc(&b->d_tmaps, nprob_alloc * 256);
+  if (e == cudaSuccess && tc) e = cudaMallocHost(&b->h_tmaps, nprob_alloc * 256);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaMallocHost(&b->h_ptrs[i], sizeof(float2*) * 3 * count);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged[i], cudaEventDisableTiming);
@@ -361,7 +384,7 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->d_fwd_job, sizeof(int) * fwd_job.size());
   if (e == cudaSuccess) e = cudaMalloc(&b->d_inv_job, sizeof(int) * inv_job.size());
-  if (e == cudaSuccess && !tc) e = cudaMalloc(&b->d_prob_tile, sizeof(int) * prob_tile.size());
+  if (e == cudaSuccess && !tc) e = cudaMalloc(&b->d_prob_tile, sizeof(int) * std::max(prob_tile.size(), (size_t)1));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_fwd_job, fwd_job.data(), sizeof(int) * fwd_job.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_inv_job, inv_job.data(), sizeof(int) * inv_job.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !tc)

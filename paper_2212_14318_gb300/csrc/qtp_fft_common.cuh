@@ -196,12 +196,14 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 // One radix-R Stockham stage for butterfly j of one tube: the inputs sit at
 // stride p/R, are twiddled by w_{Ns R}^(r (j mod Ns)), transformed, and written
 // to (j / Ns) Ns R + (j mod Ns) + r Ns.  Ns is the length already transformed.
+// tw holds w_p^e at entry e * tws (tws > 1: a sub-length p of a longer
+// transform whose table is read with stride tws).
 template <int R, bool INV>
 __device__ __forceinline__ void butterfly(const float2* __restrict__ in, float2* __restrict__ out, int j,
-                                          int Ns, int p, const float2* __restrict__ tw) {
+                                          int Ns, int p, const float2* __restrict__ tw, int tws = 1) {
   const int stride = p / R;
   const int k = j % Ns;
-  const int twstep = p / (Ns * R);
+  const int twstep = p / (Ns * R) * tws;
   float2 v[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -218,17 +220,17 @@ __device__ __forceinline__ void butterfly(const float2* __restrict__ in, float2*
 template <bool INV>
 __device__ __forceinline__ void butterfly_generic(const float2* __restrict__ in, float2* __restrict__ out,
                                                   int j, int Ns, int R, int p,
-                                                  const float2* __restrict__ tw) {
+                                                  const float2* __restrict__ tw, int tws = 1) {
   const int stride = p / R;
   const int k = j % Ns;
-  const int twstep = p / (Ns * R);
+  const int twstep = p / (Ns * R) * tws;
   const int base = (j / Ns) * Ns * R + k;
   for (int u = 0; u < R; ++u) {
     float2 acc = make_float2(0.f, 0.f);
     for (int r = 0; r < R; ++r) {
       float2 x = in[j + r * stride];
       if (r > 0 && k > 0) x = cmul(x, twid<INV>(tw, r * k * twstep));
-      const int e = ((r * u) % R) * stride;
+      const int e = ((r * u) % R) * stride * tws;
       acc = cadd(acc, e ? cmul(x, twid<INV>(tw, e)) : x);
     }
     out[base + u * Ns] = acc;
@@ -236,10 +238,11 @@ __device__ __forceinline__ void butterfly_generic(const float2* __restrict__ in,
 }
 
 // All stages over T tubes held at tube stride P in buf0.  Returns the buffer
-// that holds the result (natural order).
+// that holds the result (natural order).  tws: stride of the twiddle table
+// (see butterfly).
 template <bool INV>
 __device__ inline float2* run_stages(float2* buf0, float2* buf1, int T, int P, const RadixPlan& rp,
-                              const float2* __restrict__ tw) {
+                              const float2* __restrict__ tw, int tws = 1) {
   const int p = rp.p;
   float2* in = buf0;
   float2* out = buf1;
@@ -256,13 +259,13 @@ __device__ inline float2* run_stages(float2* buf0, float2* buf1, int T, int P, c
       const float2* ti = in + tube * P;
       float2* to = out + tube * P;
       switch (R) {
-        case 2: butterfly<2, INV>(ti, to, j, Ns, p, tw); break;
-        case 3: butterfly<3, INV>(ti, to, j, Ns, p, tw); break;
-        case 4: butterfly<4, INV>(ti, to, j, Ns, p, tw); break;
-        case 5: butterfly<5, INV>(ti, to, j, Ns, p, tw); break;
-        case 7: butterfly<7, INV>(ti, to, j, Ns, p, tw); break;
-        case 8: butterfly<8, INV>(ti, to, j, Ns, p, tw); break;
-        default: butterfly_generic<INV>(ti, to, j, Ns, R, p, tw); break;
+        case 2: butterfly<2, INV>(ti, to, j, Ns, p, tw, tws); break;
+        case 3: butterfly<3, INV>(ti, to, j, Ns, p, tw, tws); break;
+        case 4: butterfly<4, INV>(ti, to, j, Ns, p, tw, tws); break;
+        case 5: butterfly<5, INV>(ti, to, j, Ns, p, tw, tws); break;
+        case 7: butterfly<7, INV>(ti, to, j, Ns, p, tw, tws); break;
+        case 8: butterfly<8, INV>(ti, to, j, Ns, p, tw, tws); break;
+        default: butterfly_generic<INV>(ti, to, j, Ns, R, p, tw, tws); break;
       }
     }
     __syncthreads();

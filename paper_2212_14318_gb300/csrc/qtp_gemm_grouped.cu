@@ -84,7 +84,7 @@ __device__ __forceinline__ GTile decode_tile(const GroupProblem* __restrict__ pr
 template <int NP>
 __global__ void __launch_bounds__(kGThreads, 1)
     gemm_tc_grouped_kernel(const GroupProblem* __restrict__ probs, int nprobs, long long total_tiles, char* ws,
-                           int* err, const GViews V) {
+                           int* err, const GViews V, long long withhold, unsigned long long wait_ns) {
   constexpr int STAGE = 3 * NP * G_SLOT;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint32_t tmem_base_slot;
@@ -124,11 +124,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_base_slot;
+  long long it = 0;  // producer: stages issued (or withheld) so far
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      long long it = 0;
       int cur = 0, prev = -1;
       bool ok = true;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
           const int k0 = (kk - kh * nkb) * GBK;
           const int s = (int)(it % GSTAGES);
           const uint32_t ph = (uint32_t)(it / GSTAGES) & 1u;
-          if (!mbar_wait(empty + 8 * s, ph ^ 1u)) {
+          if (!mbar_wait(empty + 8 * s, ph ^ 1u, wait_ns)) {
             atomicExch(err, QTP_DEVERR_TIMEOUT_EMPTY);
             atomicExch(&abort_flag, 1);
             ok = false;
@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             ok = false;
             break;
           }
+          if (it == withhold) continue;  // failure-path test: this stage never arrives
           mbar_expect_tx(full + 8 * s, tx_bytes);
           // A plane kh at f (both halves); B planes b_plane[h][kh] at f or -f
           const int gb = gv_bit(V.b_fneg, 0, kh) ? (P.p - T.f) % P.p : T.f;
@@ -198,10 +199,6 @@ __global__ void __launch_bounds__(kGThreads, 1)
           }
         }
       }
-      if (!ok) {  // never leave with copies in flight
-        const long long first = it - GSTAGES < 0 ? 0 : it - GSTAGES;
-        for (long long j = first; j < it; ++j) mbar_wait(full + 8 * (int)(j % GSTAGES), (uint32_t)(j / GSTAGES) & 1u);
-      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -226,7 +223,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const int nkb = (K + GBK - 1) / GBK;
         const int buf = lt & 1;
         const uint32_t uph = (uint32_t)(lt >> 1) & 1u;
-        if (!mbar_wait(acc_empty + 8 * buf, uph ^ 1u)) {
+        if (!mbar_wait(acc_empty + 8 * buf, uph ^ 1u, wait_ns)) {
           atomicExch(err, QTP_DEVERR_TIMEOUT_ACC);
           atomicExch(&abort_flag, 1);
           ok = false;
@@ -239,7 +236,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
           const int kh = kk / nkb;
           const int s = (int)(it % GSTAGES);
           const uint32_t ph = (uint32_t)(it / GSTAGES) & 1u;
-          if (!mbar_wait(full + 8 * s, ph)) {
+          if (!mbar_wait(full + 8 * s, ph, wait_ns)) {
             atomicExch(err, QTP_DEVERR_TIMEOUT_FULL);
             atomicExch(&abort_flag, 1);
             ok = false;
@@ -267,7 +264,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       }
       if (!ok) {
         mma_commit(mma_done);
-        mbar_wait(mma_done, 0);
+        mbar_wait(mma_done, 0, wait_ns);
       }
     }
   } else {
@@ -281,7 +278,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       const GroupProblem& P = probs[T.g];
       const int buf = lt & 1;
       const uint32_t uph = (uint32_t)(lt >> 1) & 1u;
-      if (!mbar_wait(acc_full + 8 * buf, uph)) {
+      if (!mbar_wait(acc_full + 8 * buf, uph, wait_ns)) {
         if (lane == 0) {
           atomicExch(err, QTP_DEVERR_TIMEOUT_ACC);
           atomicExch(&abort_flag, 1);
@@ -326,6 +323,14 @@ __global__ void __launch_bounds__(kGThreads, 1)
     fence_before();
   }
   __syncthreads();
+  // Never leave with copies in flight: after an abort (final here) the
+  // producer waits (bounded) for the last GSTAGES stages it issued, which
+  // hold every stage the MMA warp did not consume.
+  if (warp == 0 && lane == 0 && *(volatile int*)&abort_flag) {
+    const long long first = it - GSTAGES < 0 ? 0 : it - GSTAGES;
+    for (long long j = first; j < it; ++j)
+      if (j != withhold) mbar_wait(full + 8 * (int)(j % GSTAGES), (uint32_t)(j / GSTAGES) & 1u, wait_ns);
+  }
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G_TMEM_COLS) : "memory");
@@ -420,15 +425,20 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
   // the kernel loads one A tile for both halves and reads B at one frequency per K half
   for (int kh = 0; kh < 2; ++kh)
     if (a_plane[0][kh] != a_plane[1][kh] || b_conj[0][kh] != b_conj[1][kh]) return cudaErrorInvalidValue;
+  int withhold = -1;
+  unsigned long long wait_ns = 0;
+  fault_injection(&withhold, &wait_ns);
   cudaError_t e;
   if (np == 4) {
     e = cudaFuncSetAttribute(gemm_tc_grouped_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    gemm_tc_grouped_kernel<4><<<grid, kGThreads, smem, st>>>(d_probs, nprobs, total_tiles, ws, d_err, V);
+    gemm_tc_grouped_kernel<4><<<grid, kGThreads, smem, st>>>(d_probs, nprobs, total_tiles, ws, d_err, V, withhold,
+                                                             wait_ns);
   } else {
     e = cudaFuncSetAttribute(gemm_tc_grouped_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    gemm_tc_grouped_kernel<2><<<grid, kGThreads, smem, st>>>(d_probs, nprobs, total_tiles, ws, d_err, V);
+    gemm_tc_grouped_kernel<2><<<grid, kGThreads, smem, st>>>(d_probs, nprobs, total_tiles, ws, d_err, V, withhold,
+                                                             wait_ns);
   }
   return cudaGetLastError();
 }

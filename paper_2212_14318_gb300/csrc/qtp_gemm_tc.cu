@@ -40,7 +40,8 @@ using namespace tcdev;
 constexpr int BM = 128;                 // output rows per tile (UMMA M)
 constexpr int kSmemBudget = 196608;     // operand stages per CTA
 constexpr int kMaxStages = 6;
-constexpr int kThreads = 192;           // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kEpiWarps = 8;            // two per TMEM lane quarter, each half of the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 
 // Pipeline depth for a tile of BN complex columns, K depth BK and NP bf16 parts.
 __host__ __device__ constexpr int stages_for(int np, int bn, int bk) {
@@ -60,26 +61,43 @@ struct TcArgs {
   long long out_hstride, out_fstride, out_rstride;
   int* err;
   int dep_mode;  // programmatic dependent launch, see launch_gemm_tc
+  int seg;       // ACC_PROMOTE: K steps folded into TMEM before each promotion
+  int withhold;  // K step whose operands the producer never loads (-1: none; failure-path tests)
+  unsigned long long wait_ns;  // bound of every mbarrier wait of this launch
 };
 
 struct Smem {
   uint32_t a;        // stage s, part q tile at a + (s * NP + q) * A_TILE
   uint32_t b;        // stage s, part q tile at b + (s * NP + q) * B_TILE
-  uint32_t full, empty, acc_full, mma_done;  // mbarrier addresses (8 B each)
+  uint32_t full, empty, acc_full, mma_done, acc_empty;  // mbarrier addresses (8 B each)
 };
 
-// SPLIT: the hi.hi products go to one pair of accumulators and the two
-// correction products (hi.lo + lo.hi, 2^-8 smaller) to a second pair, summed in
-// FP32 by the epilogue.  The tensor core's FP32 accumulation error grows with
-// the number of MMAs folded into an accumulator; this cuts that number for the
-// dominant accumulator threefold (needs 4 BN <= 512 TMEM columns).
-template <bool A_MN, bool B_MN, int NP, int BN, int BK, bool SPLIT>
+// Accumulator modes.  The tensor core's FP32 accumulation error grows with the
+// number of MMAs folded into one TMEM accumulator (measured on N(0,1) data:
+// 4.5e-6 at 8 K steps of 16, 5.6e-6 at 32, 1.5e-5 at 128, 2.9e-5 at 256), so
+// long reductions must not fold all their MMAs into one accumulator.
+//   ACC_SINGLE : one accumulator pair (real, imaginary): 2 BN TMEM columns.
+//   ACC_SPLIT  : the hi.hi products in one pair, the two correction products
+//                (hi.lo + lo.hi, 2^-8 smaller) in a second, summed in FP32 by
+//                the epilogue; cuts the dominant accumulator's MMA count
+//                threefold (4 BN <= 512 columns).
+//   ACC_PROMOTE: every args.seg K steps the MMA warp hands the accumulator
+//                pair to the epilogue, which adds it in FP32 to a running sum
+//                kept in a second pair of TMEM columns and releases it; the
+//                next segment restarts the accumulator at zero.  The error is
+//                that of one segment whatever the reduction length (4 BN <= 512
+//                columns; the tensor pipe pauses for each promotion).
+enum AccMode : int { ACC_SINGLE = 0, ACC_SPLIT = 1, ACC_PROMOTE = 2 };
+
+template <bool A_MN, bool B_MN, int NP, int BN, int BK, int ACC>
 __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_constant__ TcArgs args) {
-  static_assert(!SPLIT || (NP == 4 && BN <= 128), "split accumulators need bf16x3 parts and BN <= 128");
+  static_assert(ACC == ACC_SINGLE || (NP == 4 && BN <= 128), "split / promoted accumulators need bf16x3 and BN <= 128");
+  constexpr bool SPLIT = ACC == ACC_SPLIT;
+  constexpr bool PROMOTE = ACC == ACC_PROMOTE;
   constexpr int A_TILE = BM * BK * 2;
   constexpr int B_TILE = BK * BN * 2;
   constexpr int STAGES = stages_for(NP, BN, BK);
-  constexpr uint32_t TMEM_COLS = (SPLIT ? 4 : 2) * BN;  // real + imaginary (x2 when split)
+  constexpr uint32_t TMEM_COLS = (ACC == ACC_SINGLE ? 2 : 4) * BN;  // real + imaginary (x2: split or running sum)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint32_t tmem_base_slot;
   __shared__ int abort_flag;
@@ -94,6 +112,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   S.empty = bars + 8 * STAGES;
   S.acc_full = bars + 16 * STAGES;
   S.mma_done = S.acc_full + 8;
+  S.acc_empty = S.acc_full + 16;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -118,6 +137,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   }
   const int nkb = (args.K + BK - 1) / BK;
   const int total = 2 * nkb;
+  const unsigned long long wait_ns = args.wait_ns;
+  // ACC_PROMOTE: segments of args.seg K steps (the last one may be shorter)
+  const int seg = PROMOTE ? args.seg : total;
+  const int nseg = (total + seg - 1) / seg;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -126,6 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     }
     mbar_init(S.acc_full, 1);
     mbar_init(S.mma_done, 1);
+    mbar_init(S.acc_empty, kEpiWarps);  // ACC_PROMOTE: one arrival per epilogue warp
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&args.tmA)) : "memory");
@@ -145,6 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_base_slot;
+  int issued = 0;  // producer: K steps whose copies were issued (or withheld)
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -152,18 +177,21 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       // the spectra come from the previous kernel (launched with PDL); mode 2
       // reads spectra that were complete before that kernel let it start
       if (args.dep_mode != 2) grid_dep_wait();
-      int issued = 0;
       for (int it = 0; it < total; ++it) {
         const int kh = it / nkb;
         const int kb = it - kh * nkb;
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(S.empty + 8 * s, ph ^ 1u)) {
+        if (!mbar_wait(S.empty + 8 * s, ph ^ 1u, wait_ns)) {
           atomicExch(args.err, QTP_DEVERR_TIMEOUT_EMPTY);
           atomicExch(&abort_flag, 1);
           break;
         }
         if (*(volatile int*)&abort_flag) break;
+        if (it == args.withhold) {  // failure-path test: this stage never arrives
+          issued = it + 1;
+          continue;
+        }
         mbar_expect_tx(S.full + 8 * s, (uint32_t)(NP * (A_TILE + B_TILE)));
         const int ga = args.a_fneg[h][kh] ? (p - f) % p : f;
         const int gb = args.b_fneg[h][kh] ? (p - f) % p : f;
@@ -190,11 +218,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         }
         issued = it + 1;
       }
-      // Never leave with copies in flight: wait (bounded) for the last stages issued.
-      if (*(volatile int*)&abort_flag) {
-        for (int it = issued - STAGES < 0 ? 0 : issued - STAGES; it < issued; ++it)
-          mbar_wait(S.full + 8 * (it % STAGES), (uint32_t)(it / STAGES) & 1u);
-      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -215,7 +238,21 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         const int kh = it / nkb;
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(S.full + 8 * s, ph)) {
+        if (PROMOTE && it > 0 && it % seg == 0) {
+          // a new segment: wait until the epilogue has folded the previous
+          // one into the running sum, then restart the accumulators at zero
+          const int j = it / seg - 1;
+          if (!mbar_wait(S.acc_empty, (uint32_t)j & 1u, wait_ns)) {
+            atomicExch(args.err, QTP_DEVERR_TIMEOUT_ACC);
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          fence_after();
+          acc_re = 0u;
+          acc_im = 0u;
+        }
+        if (!mbar_wait(S.full + 8 * s, ph, wait_ns)) {
           atomicExch(args.err, QTP_DEVERR_TIMEOUT_FULL);
           atomicExch(&abort_flag, 1);
           ok = false;
@@ -236,19 +273,57 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
                                    d_re, d_im, c_re, c_im, acc_re, acc_im, acc_cre, acc_cim);
         }
         mma_commit(S.empty + 8 * s);  // frees the stage when these MMAs complete
+        // end of a segment other than the last: hand the accumulators over
+        if (PROMOTE && (it + 1) % seg == 0 && it + 1 < total) mma_commit(S.acc_full);
       }
       if (ok) {
         mma_commit(S.acc_full);
       } else {
         // Unwind: wait (bounded) for MMAs already issued before freeing TMEM.
         mma_commit(S.mma_done);
-        mbar_wait(S.mma_done, 0);
+        mbar_wait(S.mma_done, 0, wait_ns);
       }
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
-    bool ok = mbar_wait(S.acc_full, 0);
+    // Warp w may read TMEM lanes 32 (w mod 4) .. +31 (its row quarter); the
+    // two warps of a quarter take one half of the tile's columns each.
+    const int q = warp & 3;
+    const int c_begin = ((warp - 2) >> 2) * (BN / 2);
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    bool ok = true;
+    // ACC_PROMOTE: fold every segment but the last into the running sum
+    // (columns 2 BN .. 4 BN) and release the accumulators to the MMA warp
+    for (int j = 0; PROMOTE && j + 1 < nseg; ++j) {
+      if (!mbar_wait(S.acc_full, (uint32_t)j & 1u, wait_ns)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+#pragma unroll 1
+      for (int c0 = c_begin; c0 < c_begin + BN / 2; c0 += 32) {
+        const uint32_t t = tmem + lane_off + (uint32_t)c0;
+        uint32_t re[32], im[32];
+        if (j == 0) {
+          tmem_ld32x2(t, t + BN, re, im);
+        } else {
+          uint32_t rre[32], rim[32];
+          tmem_ld32x4(t, t + BN, t + 2 * BN, t + 3 * BN, re, im, rre, rim);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            re[i] = __float_as_uint(__uint_as_float(re[i]) + __uint_as_float(rre[i]));
+            im[i] = __float_as_uint(__uint_as_float(im[i]) + __uint_as_float(rim[i]));
+          }
+        }
+        tmem_st32(t + 2 * BN, re);
+        tmem_st32(t + 3 * BN, im);
+      }
+      tmem_st_wait();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(S.acc_empty);
+    }
+    if (ok) ok = mbar_wait(S.acc_full, (uint32_t)(nseg - 1) & 1u, wait_ns);
     if (!ok) {
       if (lane == 0) {
         atomicExch(args.err, QTP_DEVERR_TIMEOUT_ACC);
@@ -258,36 +333,45 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       fence_after();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // ring: async-proxy use -> generic writes
       float2* out = args.out + (long long)h * args.out_hstride + (long long)f * args.out_fstride;
-      const uint32_t lane_off = (uint32_t)(q * 32) << 16;
       // The operand ring is idle once the accumulators are final (every TMA
       // load was consumed and every MMA has completed): it holds the staging
-      // areas of the four epilogue warps.
-      static_assert(STAGES * NP * (A_TILE + B_TILE) >= 4 * kStgBytes, "staging areas must fit in the operand ring");
-      float2* stg = reinterpret_cast<float2*>(smem_raw + (S.a - raw) + q * kStgBytes);
+      // areas of the epilogue warps.
+      static_assert(STAGES * NP * (A_TILE + B_TILE) >= kEpiWarps * kStgBytes,
+                    "staging areas must fit in the operand ring");
+      float2* stg = reinterpret_cast<float2*>(smem_raw + (S.a - raw) + (warp - 2) * kStgBytes);
       const int row0 = mt * BM + q * 32;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = c_begin; c0 < c_begin + BN / 2; c0 += 32) {
+        const uint32_t t = tmem + lane_off + (uint32_t)c0;
         uint32_t re[32], im[32];
-        tmem_ld32(tmem + lane_off + (uint32_t)c0, re);
-        tmem_ld32(tmem + lane_off + (uint32_t)(BN + c0), im);
-        if constexpr (SPLIT) {
+        if (SPLIT || (PROMOTE && nseg > 1)) {  // plus the correction pair, or the running sum
           uint32_t cre[32], cim[32];
-          tmem_ld32(tmem + lane_off + (uint32_t)(2 * BN + c0), cre);
-          tmem_ld32(tmem + lane_off + (uint32_t)(3 * BN + c0), cim);
+          tmem_ld32x4(t, t + BN, t + 2 * BN, t + 3 * BN, re, im, cre, cim);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            re[j] = __float_as_uint(__uint_as_float(re[j]) + __uint_as_float(cre[j]));
-            im[j] = __float_as_uint(__uint_as_float(im[j]) + __uint_as_float(cim[j]));
+          for (int i = 0; i < 32; ++i) {
+            re[i] = __float_as_uint(__uint_as_float(re[i]) + __uint_as_float(cre[i]));
+            im[i] = __float_as_uint(__uint_as_float(im[i]) + __uint_as_float(cim[i]));
           }
+        } else {
+          tmem_ld32x2(t, t + BN, re, im);
         }
         const int col0 = nt * BN + c0;
-        store_chunk(stg, re, im, out + (long long)row0 * args.out_rstride + col0, args.out_rstride, args.M - row0,
-                    args.N - col0, lane);
+        if (col0 < args.N)
+          store_chunk(stg, re, im, out + (long long)row0 * args.out_rstride + col0, args.out_rstride, args.M - row0,
+                      args.N - col0, lane);
       }
     }
     fence_before();
   }
   __syncthreads();
+  // After an abort the MMA warp may have stopped before consuming stages whose
+  // copies are still in flight.  The flag is final here: the producer waits
+  // (bounded) for the last STAGES it issued, which hold every unconsumed one,
+  // so the CTA never exits with a copy into its shared memory outstanding.
+  if (warp == 0 && lane == 0 && *(volatile int*)&abort_flag) {
+    for (int it = issued - STAGES < 0 ? 0 : issued - STAGES; it < issued; ++it)
+      if (it != args.withhold) mbar_wait(S.full + 8 * (it % STAGES), (uint32_t)(it / STAGES) & 1u, wait_ns);
+  }
   // mode 2: this grid completes only after the previous one (its partner), so
   // the kernel after it may rely on both
   if (args.dep_mode == 2 && threadIdx.x == 0) grid_dep_wait();
@@ -353,9 +437,9 @@ bool encode_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, i
   return true;
 }
 
-template <bool A_MN, bool B_MN, int NP, int BN, int BK, bool SPLIT = false>
+template <bool A_MN, bool B_MN, int NP, int BN, int BK, int ACC = ACC_SINGLE>
 cudaError_t launch_kind(const TcArgs& args, dim3 grid, cudaStream_t st) {
-  auto kfn = gemm_tc_kernel<A_MN, B_MN, NP, BN, BK, SPLIT>;
+  auto kfn = gemm_tc_kernel<A_MN, B_MN, NP, BN, BK, ACC>;
   const size_t smem =
       (size_t)stages_for(NP, BN, BK) * NP * (BM * BK * 2 + BK * BN * 2) + 1024 /*align*/ + 256 /*barriers*/;
   static std::atomic<unsigned long long> attr_set{0};
@@ -417,6 +501,16 @@ bool build_args(const TcProblem& pr, bool a_mn, bool b_mn, int bn, int bk, TcArg
 
 }  // namespace
 
+void fault_injection(int* withhold, unsigned long long* wait_ns) {
+  *withhold = -1;
+  *wait_ns = kWaitNs;
+  if (const char* w = getenv("QTP_INJECT_WITHHOLD")) *withhold = atoi(w);
+  if (const char* t = getenv("QTP_INJECT_WAIT_NS")) {
+    const unsigned long long v = strtoull(t, nullptr, 10);
+    if (v > 0 && v < kWaitNs) *wait_ns = v;
+  }
+}
+
 bool tc_supported() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -441,23 +535,29 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
   const bool b_mn = pr.kind != TC_BWD_A;
   // Tile choice.  256-wide tiles halve the shared-memory operand traffic per
   // MMA; narrow products keep 128-wide tiles to avoid padding waste.  The
-  // tensor core's FP32 accumulation error grows with the number of MMAs folded
-  // into one accumulator (measured: 5.6e-6 at K = 256, 1.5e-5 at K = 1024 per
-  // half for N(0,1) data), so long reductions use split accumulators (128 wide)
-  // to stay within 1e-5.  QTP_TC_TILE = "256", "128" or "128s" overrides.
+  // accumulator mode follows the reduction length K per half so that split-BF16
+  // stays within 1e-5 (see AccMode): one accumulator pair up to
+  // kTcSingleMaxK, split accumulators up to kTcSplitMaxK (measured 6.2e-6 at
+  // K = 1024), periodic promotion to FP32 beyond.  QTP_TC_TILE = "256", "128",
+  // "128s" or "128p" overrides.
   int bn = pr.N > 160 ? 256 : 128;
-  bool split = pr.nparts == 4 && pr.K > 384;
-  if (split) bn = 128;
+  int acc = ACC_SINGLE;
+  if (pr.nparts == 4 && pr.K > kTcSingleMaxK) {
+    bn = 128;
+    acc = pr.K > kTcSplitMaxK ? ACC_PROMOTE : ACC_SPLIT;
+  }
   switch (pr.tile) {  // a tuned choice (autotuner) replaces the heuristic
-    case TILE_256: bn = 256; split = false; break;
-    case TILE_128: bn = 128; split = false; break;
-    case TILE_128_SPLIT: bn = 128; split = pr.nparts == 4; break;
+    case TILE_256: bn = 256; acc = ACC_SINGLE; break;
+    case TILE_128: bn = 128; acc = ACC_SINGLE; break;
+    case TILE_128_SPLIT: bn = 128; acc = pr.nparts == 4 ? ACC_SPLIT : ACC_SINGLE; break;
+    case TILE_128_PROMOTE: bn = 128; acc = pr.nparts == 4 ? ACC_PROMOTE : ACC_SINGLE; break;
     default: break;
   }
   if (const char* env = getenv("QTP_TC_TILE")) {
-    if (!strcmp(env, "256")) { bn = 256; split = false; }
-    else if (!strcmp(env, "128")) { bn = 128; split = false; }
-    else if (!strcmp(env, "128s") && pr.nparts == 4) { bn = 128; split = true; }
+    if (!strcmp(env, "256")) { bn = 256; acc = ACC_SINGLE; }
+    else if (!strcmp(env, "128")) { bn = 128; acc = ACC_SINGLE; }
+    else if (!strcmp(env, "128s") && pr.nparts == 4) { bn = 128; acc = ACC_SPLIT; }
+    else if (!strcmp(env, "128p") && pr.nparts == 4) { bn = 128; acc = ACC_PROMOTE; }
   }
   const int bk = 16;
   // The encoded arguments (two tensor maps and the operand roles) depend only
@@ -466,8 +566,7 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
   // encoding the tensor maps again.
   struct CacheEntry {
     bool valid;
-    int dev, bn;
-    bool split;
+    int dev, bn, acc;
     TcProblem pr;
     TcArgs args;
   };
@@ -478,7 +577,7 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
   TcArgs args;
   const CacheEntry* hit = nullptr;
   for (const CacheEntry& ce : cache)
-    if (ce.valid && ce.dev == dev && ce.bn == bn && ce.split == split && memcmp(&ce.pr, &pr, sizeof(pr)) == 0)
+    if (ce.valid && ce.dev == dev && ce.bn == bn && ce.acc == acc && memcmp(&ce.pr, &pr, sizeof(pr)) == 0)
       hit = &ce;
   if (hit) {
     args = hit->args;
@@ -489,17 +588,20 @@ cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, cha
     slot.valid = true;
     slot.dev = dev;
     slot.bn = bn;
-    slot.split = split;
+    slot.acc = acc;
     slot.pr = pr;
     slot.args = args;
   }
   args.err = d_err;
   args.dep_mode = dep_mode;
+  args.seg = kTcPromoteSteps;
+  fault_injection(&args.withhold, &args.wait_ns);
   dim3 grid((pr.N + bn - 1) / bn, (pr.M + BM - 1) / BM, 2 * pr.p);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
   const bool x3 = pr.nparts == 4;
 #define QTP_TC_LAUNCH(AMN, BMN)                                                            \
-  if (split) return launch_kind<AMN, BMN, 4, 128, 16, true>(args, grid, st);               \
+  if (acc == ACC_SPLIT) return launch_kind<AMN, BMN, 4, 128, 16, ACC_SPLIT>(args, grid, st); \
+  if (acc == ACC_PROMOTE) return launch_kind<AMN, BMN, 4, 128, 16, ACC_PROMOTE>(args, grid, st); \
   return x3 ? (bn == 256 ? launch_kind<AMN, BMN, 4, 256, 16>(args, grid, st)              \
                          : launch_kind<AMN, BMN, 4, 128, 16>(args, grid, st))             \
             : (bn == 256 ? launch_kind<AMN, BMN, 2, 256, 16>(args, grid, st)              \

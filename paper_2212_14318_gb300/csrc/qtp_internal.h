@@ -129,6 +129,24 @@ cudaError_t launch_fft_fwd_fixed(const FftFwdJob* jobs, int njobs, int fmt, int 
                                  cudaStream_t st);
 cudaError_t launch_fft_inv_fixed(const FftInvJob* jobs, int njobs, int p, const float2* tw, cudaStream_t st);
 
+// Long tubes (qtp_fft_split.cu): the two-pass ("four-step") transforms
+// through an FP32 intermediate, p = N1 N2.  fft_split_dims picks N2, the
+// largest divisor <= sqrt(p), and returns false when it is below 4 (p prime
+// or twice a prime, ...).  fft_split_eligible: whether the forward (inv =
+// false) or inverse transform of length p takes the two-pass form by default
+// (forward from p = 2048 up without a compile-time transform, where it
+// measured faster); environment QTP_FFT_SPLIT=0: never, =1: both directions
+// for every splittable length above 128.  Scratch: fft_split_scratch_bytes
+// per tensor transformed in the same launch (the first tensor's intermediate
+// first).
+bool fft_split_dims(int p, int* n1, int* n2);
+bool fft_split_eligible(int p, bool inv);
+size_t fft_split_scratch_bytes(int p, long long rows, long long cols);
+cudaError_t launch_fft_fwd_split(const FftFwdJob* jobs, int njobs, int fmt, int p, const float2* tw, float2* scratch,
+                                 cudaStream_t st);
+cudaError_t launch_fft_inv_split(const FftInvJob* jobs, int njobs, int p, const float2* tw, float2* scratch,
+                                 cudaStream_t st);
+
 cudaError_t launch_twiddles(float2* tw, int p, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdJob* jobs, int njobs, int fmt, const RadixPlan& rp,
                            const float2* tw, cudaStream_t st);
@@ -188,8 +206,24 @@ enum TcKind : int {
 };
 
 // Tensor-core tile choice: 0 = heuristic (256 wide for N > 160; split
-// accumulators for K > 384), else one of these.
-enum TcTile : int { TILE_AUTO = 0, TILE_256 = 1, TILE_128 = 2, TILE_128_SPLIT = 3 };
+// accumulators for K > kTcSingleMaxK, promoted ones for K > kTcSplitMaxK),
+// else one of these.
+enum TcTile : int { TILE_AUTO = 0, TILE_256 = 1, TILE_128 = 2, TILE_128_SPLIT = 3, TILE_128_PROMOTE = 4 };
+
+// Reduction lengths (K per half of the m x 2n x 2s complex product) up to which
+// each split-BF16 accumulator mode keeps the relative error within 1e-5 on
+// N(0,1) data, and the segment length of the promoted mode (K steps of 16).
+constexpr int kTcSingleMaxK = 384;   // one accumulator pair (5.6e-6 at 256)
+constexpr int kTcSplitMaxK = 1024;   // split accumulators (6.2e-6 at 1024, 1.0e-5 at 2048)
+constexpr int kTcPromoteSteps = 32;  // promoted: at most 32 K steps per TMEM accumulation
+
+// Failure-path testing: the environment variables QTP_INJECT_WITHHOLD (a K
+// step index) and QTP_INJECT_WAIT_NS (nanoseconds) make the next tensor-core
+// launches never load that K step's operands and bound every wait by that
+// many nanoseconds, so the bounded waits expire and the kernels unwind
+// (recording QTP_DEVERR_* in the error word) without touching any memory
+// outside their buffers.  Unset: *withhold = -1, *wait_ns = the default bound.
+void fault_injection(int* withhold, unsigned long long* wait_ns);
 
 struct TcProblem {
   int kind;
@@ -248,6 +282,10 @@ size_t c32_bytes_of(long long p, long long rows, long long cols);
 
 cudaError_t launch_gemm_tc(const TcProblem& pr, int* d_err, cudaStream_t st, char* msg, size_t msglen,
                            int dep_mode = 0);
+// The forward product's tensor-core problem (Thm 5.1 in the plain-transform
+// form) over bf16 spectra sa (A, [plane][part][f][m][ld]), sb (B) written by
+// the forward FFT, output C_hat sc ([plane][f][m][s], complex FP32).
+TcProblem make_tc_fwd(int m, int n, int s, int p, int nparts, int tile, const void* sa, const void* sb, float2* sc);
 
 }  // namespace qtp
 
@@ -260,6 +298,8 @@ struct qtp_plan {
   float2* d_tw;      // w^e = exp(-2 pi i e / p), e in [0, p)
   int* d_err;        // device error word written by bounded waits
   qtp::RadixPlan rp;
+  int fft_split_fwd;  // forward / inverse tube transforms in two passes through a
+  int fft_split_inv;  // workspace intermediate (long p)
   int tracing;
   cudaEvent_t ev[4];  // stage boundaries of the last traced call
   // streams and events of qtp_forward_host_many, created on its first call

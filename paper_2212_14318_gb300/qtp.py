@@ -342,6 +342,18 @@ class BatchPlan:
         return int(v.value)
 
     def forward(self, As, Bs, Cs=None, workspace=None, stream=None):
+        """C_i = A_i * B_i for every product (qtp_forward_batched); returns the Cs.
+        Validates and marshals every tensor on each call; for a batch whose
+        tensors stay the same across calls, bind() does that once."""
+        bound = self.bind(As, Bs, Cs, workspace)
+        bound.forward(stream)
+        return bound.Cs
+
+    def bind(self, As, Bs, Cs=None, workspace=None):
+        """Validate the batch's tensors once and keep their device pointers:
+        the returned object's forward() is one qtp_forward_batched call.  It
+        holds references to the tensors and the workspace, so their memory
+        stays valid; their contents may change between calls."""
         import torch
         n = len(self.shapes)
         if len(As) != n or len(Bs) != n:
@@ -349,23 +361,18 @@ class BatchPlan:
         if Cs is None:
             Cs = [torch.empty((2, m, s, p, 2), dtype=torch.float32, device=As[0].device)
                   for (m, _, s, p) in self.shapes]
+        if len(Cs) != n:
+            raise ValueError("one C per product")
         for i, (m, k, s, p) in enumerate(self.shapes):
             _check_tensor(As[i], (2, m, k, p, 2), f"A[{i}]")
             _check_tensor(Bs[i], (2, k, s, p, 2), f"B[{i}]")
             _check_tensor(Cs[i], (2, m, s, p, 2), f"C[{i}]")
-        pa = (ctypes.c_void_p * n)(*[t.data_ptr() for t in As])
-        pb = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Bs])
-        pc = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Cs])
         if workspace is None:
             need = self.workspace_size()
             if self._ws is None or self._ws.numel() < need:
                 self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=As[0].device)
             workspace = self._ws
-        _check(lib().qtp_forward_batched(self._h, ctypes.cast(pa, ctypes.c_void_p), ctypes.cast(pb, ctypes.c_void_p),
-                                         ctypes.cast(pc, ctypes.c_void_p), _ptr(workspace),
-                                         workspace.numel() * workspace.element_size(), _stream(stream)),
-               "qtp_forward_batched")
-        return Cs
+        return BoundBatch(self, list(As), list(Bs), list(Cs), workspace)
 
     def set_tracing(self, enable: bool = True):
         _check(lib().qtp_batch_plan_set_tracing(self._h, 1 if enable else 0), "qtp_batch_plan_set_tracing")
@@ -388,6 +395,26 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+class BoundBatch:
+    """A batch plan with its tensors validated and their pointers marshalled
+    (BatchPlan.bind)."""
+
+    def __init__(self, plan, As, Bs, Cs, workspace):
+        n = len(plan.shapes)
+        self.plan, self.As, self.Bs, self.Cs, self.workspace = plan, As, Bs, Cs, workspace
+        self._pa = (ctypes.c_void_p * n)(*[t.data_ptr() for t in As])
+        self._pb = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Bs])
+        self._pc = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Cs])
+        self._ws_bytes = workspace.numel() * workspace.element_size()
+
+    def forward(self, stream=None):
+        _check(lib().qtp_forward_batched(self.plan._h, ctypes.cast(self._pa, ctypes.c_void_p),
+                                         ctypes.cast(self._pb, ctypes.c_void_p), ctypes.cast(self._pc, ctypes.c_void_p),
+                                         _ptr(self.workspace), self._ws_bytes, _stream(stream)),
+               "qtp_forward_batched")
+        return self.Cs
 
 
 _plan_cache = {}

@@ -304,3 +304,62 @@ def test_backward_from_saved_spectra(precision, shape):
     torch.cuda.synchronize()
     assert only_b[0] is None
     np.testing.assert_array_equal(to_host(only_b[1]), to_host(gB_ref))
+
+
+# Both transform forms at long tube lengths: the two-pass (four-step) transform
+# through the workspace intermediate (QTP_FFT_SPLIT=1 forces it also for the
+# lengths that have a one-kernel transform) and the one-kernel transforms
+# (QTP_FFT_SPLIT=0), each against the oracle's FP64 Algorithm 5.1 and sampled
+# definition entries; the plan fixes its form at creation.
+@pytest.mark.parametrize("split", ["1", "0"])
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("m,n,s,p", [(5, 6, 7, 256), (3, 4, 5, 1000), (9, 7, 40, 1024), (2, 3, 2, 4096),
+                                     (7, 5, 6, 243)])
+def test_forward_large_p_both_transforms(split, precision, m, n, s, p):
+    import os
+    qtp = _qtp()
+    A, B = _inputs(m, n, s, p, seed=p + 3 * m)
+    os.environ["QTP_FFT_SPLIT"] = split
+    try:
+        plan = qtp.Plan(m, n, s, p, precision)
+    finally:
+        del os.environ["QTP_FFT_SPLIT"]
+    assert plan.launch_count()[0] == (5 if split == "1" else 3)
+    C = to_host(plan.forward(to_dev(A), to_dev(B)))
+    plan.sync()
+    Aq, Bq = planes_to_comp(A), planes_to_comp(B)
+    assert_close(C, Q.alg51(Aq, Bq), REL_TOL, ELEM_TOL, f"p={p} split={split} vs Alg. 5.1 (FP64)")
+    ii, tt, kk = synth.sample_positions(m, s, p, 32)
+    ref = Q.tprod_def_entries(Aq, Bq, ii, tt, kk)
+    got = planes_to_comp(C)[:, ii, tt, kk]
+    assert np.linalg.norm(got - ref) <= REL_TOL * np.linalg.norm(ref), f"p={p} split={split} sampled entries"
+
+
+@pytest.mark.parametrize("split", ["1", None])
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("m,n,s,p", [(5, 6, 7, 1000), (4, 3, 5, 4096)])
+def test_backward_large_p(split, precision, m, n, s, p):
+    """dA = dC * B^H and dB = A^H * dC at long tube lengths, with the two-pass
+    transforms forced in both directions (forward of A, B and dC, inverse of
+    dA and dB through the workspace intermediate) and with the default choice
+    (two-pass forward from p = 2048, one-kernel inverse), against the
+    oracle's FP64 Algorithm 5.1 on the conjugate transposes."""
+    import os
+    qtp = _qtp()
+    A, B = _inputs(m, n, s, p, seed=p + 1)
+    G = synth.quat_normal(m, s, p, seed=p + 2)
+    if split is not None:
+        os.environ["QTP_FFT_SPLIT"] = split
+    try:
+        plan = qtp.Plan(m, n, s, p, precision)
+    finally:
+        os.environ.pop("QTP_FFT_SPLIT", None)
+    if split == "1":
+        assert plan.launch_count() == (5, 8)
+    else:
+        assert plan.launch_count() == ((4, 7) if p >= 2048 else (3, 5))
+    dA, dB = plan.backward(to_dev(G), to_dev(A), to_dev(B))
+    plan.sync()
+    Aq, Bq, Gq = planes_to_comp(A), planes_to_comp(B), planes_to_comp(G)
+    assert_close(to_host(dA), Q.alg51(Gq, Q.conj_transpose(Bq)), REL_TOL, ELEM_TOL, f"dA p={p}")
+    assert_close(to_host(dB), Q.alg51(Q.conj_transpose(Aq), Gq), REL_TOL, ELEM_TOL, f"dB p={p}")

@@ -1,4 +1,4 @@
-"""qtp_forward_noalloc against qtp_forward.
+"""qtp_forward_noalloc against the FP64 oracle and against qtp_forward.
 
 qtp_forward_noalloc serves callers that may not allocate device memory (their
 memory belongs to another allocator, or cudaMalloc's synchronisation is too
@@ -10,6 +10,7 @@ passes alone in a fresh process.
 import numpy as np
 import pytest
 
+import oracle as Q
 from paper_2212_14318_gb300 import synth
 from tests._gpu import assert_close, to_dev, to_host
 from tests._qlayout import planes_to_comp
@@ -38,9 +39,13 @@ def test_noalloc_matches_forward_on_two_calls_in_a_row(precision):
         B = synth.quat_normal(n, s, p, seed=600 + call)
         dA, dB = to_dev(A), to_dev(B)
         ref = qtp.Plan(m, n, s, p, precision).forward(dA, dB)
-        got = qtp.forward_noalloc(dA, dB, precision=precision)
-        assert_close(to_host(got), planes_to_comp(to_host(ref)), REL_TOL, ELEM_TOL,
-                     f"noalloc call {call} {precision}")
+        got = to_host(qtp.forward_noalloc(dA, dB, precision=precision))
+        # the definition (Definition 2.3, FP64), as every parity test
+        assert_close(got, Q.tprod_def(planes_to_comp(A), planes_to_comp(B)), REL_TOL, ELEM_TOL,
+                     f"noalloc call {call} {precision} vs oracle")
+        # and the entry point that allocates, on the same device inputs
+        assert_close(got, planes_to_comp(to_host(ref)), REL_TOL, ELEM_TOL,
+                     f"noalloc call {call} {precision} vs qtp_forward")
 
 
 def test_noalloc_rejects_products_beyond_the_static_array():
