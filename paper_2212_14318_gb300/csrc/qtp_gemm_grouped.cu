@@ -202,25 +202,31 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // The issuing thread is this kernel's critical path (narrow MMAs): stage,
+    // phase and descriptor words are counters, one asm statement per half.
     if (lane == 0) {
-      // base descriptors of the three slots of stage 0, K-major and MN-major
+      // descriptor words of the three slots of stage 0, K-major and MN-major
       const uint64_t dsh_k = part_desc<false, GBK>(base, 0);
       const uint64_t dh0_mn = part_desc<true, GBK>(base + NP * G_SLOT, 0);
-      const uint64_t dh1_mn = part_desc<true, GBK>(base + 2 * NP * G_SLOT, 0);
-      const uint32_t step = (uint32_t)(G_SLOT >> 4);
-      long long it = 0;
+      const uint32_t k_hi = (uint32_t)(dsh_k >> 32), mn_hi = (uint32_t)(dh0_mn >> 32);
+      const uint32_t sh0 = (uint32_t)dsh_k, h00 = (uint32_t)dh0_mn;
+      constexpr uint32_t PART = (uint32_t)(G_SLOT >> 4);    // part-to-part step
+      constexpr uint32_t HALF = (uint32_t)(NP * G_SLOT) >> 4; // half 0 -> half 1 slot
+      constexpr uint32_t STG = (uint32_t)STAGE >> 4;         // stage-to-stage step
+      uint32_t so = 0;  // stage offset (descriptor units)
+      int s = 0;
+      uint32_t ph = 0;
       int lt = 0, cur = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++lt) {
         const GTile T = decode_tile(probs, nprobs, t, cur);
         const GroupProblem& P = probs[T.g];
-        const int K = P.K;
         const bool tr = P.trans != 0;
         const int ncols = tr ? P.M : P.N;
         const int nw = (min(GBN, ncols - T.nt * GBN) + 15) & ~15;
         const uint32_t idesc = make_idesc(tr, !tr, nw);
         const uint32_t nmask = tr ? V.negmask_t : V.negmask;
-        const int nkb = (K + GBK - 1) / GBK;
+        const int nkb = (P.K + GBK - 1) / GBK;
         const int buf = lt & 1;
         const uint32_t uph = (uint32_t)(lt >> 1) & 1u;
         if (!mbar_wait(acc_empty + 8 * buf, uph ^ 1u, wait_ns)) {
@@ -231,33 +237,40 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
         fence_after();
         const uint32_t d0 = tmem + (uint32_t)(buf * 4 * GBN);  // C1 re, C1 im, C2 re, C2 im
-        uint32_t a0r = 0, a0i = 0, a1r = 0, a1i = 0;
-        for (int kk = 0; kk < 2 * nkb; ++kk, ++it) {
-          const int kh = kk / nkb;
-          const int s = (int)(it % GSTAGES);
-          const uint32_t ph = (uint32_t)(it / GSTAGES) & 1u;
-          if (!mbar_wait(full + 8 * s, ph, wait_ns)) {
-            atomicExch(err, QTP_DEVERR_TIMEOUT_FULL);
-            atomicExch(&abort_flag, 1);
-            ok = false;
-            break;
+        uint32_t acc = 0;
+        for (int kh = 0; kh < 2 && ok; ++kh) {
+          uint32_t p0, p1, p2, p3, q0, q1, q2, q3;
+          signed_idescs(idesc, nmask >> (4 * kh), p0, p1, p2, p3);
+          signed_idescs(idesc, nmask >> (4 * (2 + kh)), q0, q1, q2, q3);
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(full + 8 * s, ph, wait_ns)) {
+              atomicExch(err, QTP_DEVERR_TIMEOUT_FULL);
+              atomicExch(&abort_flag, 1);
+              ok = false;
+              break;
+            }
+            fence_after();
+            if (tr) {  // A operands: B's spectra per half (MN-major); B operand: A's spectra (K-major, shared)
+              complex_kstep_issue<NP, false>(h00 + so, mn_hi, sh0 + so, k_hi, PART, PART, p0, p1, p2, p3, d0,
+                                             d0 + GBN, d0, d0 + GBN, acc);
+              complex_kstep_issue<NP, false>(h00 + HALF + so, mn_hi, sh0 + so, k_hi, PART, PART, q0, q1, q2, q3,
+                                             d0 + 2 * GBN, d0 + 3 * GBN, d0 + 2 * GBN, d0 + 3 * GBN, acc);
+            } else {   // A operand: A's spectra (K-major, shared); B operands: B's spectra per half (MN-major)
+              complex_kstep_issue<NP, false>(sh0 + so, k_hi, h00 + so, mn_hi, PART, PART, p0, p1, p2, p3, d0,
+                                             d0 + GBN, d0, d0 + GBN, acc);
+              complex_kstep_issue<NP, false>(sh0 + so, k_hi, h00 + HALF + so, mn_hi, PART, PART, q0, q1, q2, q3,
+                                             d0 + 2 * GBN, d0 + 3 * GBN, d0 + 2 * GBN, d0 + 3 * GBN, acc);
+            }
+            acc = 1u;
+            mma_commit(empty + 8 * s);
+            if (++s == GSTAGES) {
+              s = 0;
+              ph ^= 1u;
+              so = 0;
+            } else {
+              so += STG;
+            }
           }
-          fence_after();
-          const uint32_t neg0 = nmask >> (4 * kh), neg1 = nmask >> (4 * (2 + kh));
-          const uint64_t so = (uint64_t)((uint32_t)(s * STAGE) >> 4);  // stage offset in descriptor units
-          if (tr) {  // A operands: B's spectra per half (MN-major); B operand: A's spectra (K-major, shared)
-            complex_kstep<NP, false>(dh0_mn + so, dsh_k + so, step, step, idesc, neg0, d0, d0 + GBN, d0, d0 + GBN,
-                                     a0r, a0i, a0r, a0i);
-            complex_kstep<NP, false>(dh1_mn + so, dsh_k + so, step, step, idesc, neg1, d0 + 2 * GBN, d0 + 3 * GBN,
-                                     d0 + 2 * GBN, d0 + 3 * GBN, a1r, a1i, a1r, a1i);
-          } else {   // A operand: A's spectra (K-major, shared); B operands: B's spectra per half (MN-major)
-            const uint64_t db1 = dh1_mn + so;
-            complex_kstep<NP, false>(dsh_k + so, dh0_mn + so, step, step, idesc, neg0, d0, d0 + GBN, d0, d0 + GBN,
-                                     a0r, a0i, a0r, a0i);
-            complex_kstep<NP, false>(dsh_k + so, db1, step, step, idesc, neg1, d0 + 2 * GBN, d0 + 3 * GBN,
-                                     d0 + 2 * GBN, d0 + 3 * GBN, a1r, a1i, a1r, a1i);
-          }
-          mma_commit(empty + 8 * s);
         }
         if (!ok) break;
         mma_commit(acc_full + 8 * buf);

@@ -177,104 +177,123 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       // the spectra come from the previous kernel (launched with PDL); mode 2
       // reads spectra that were complete before that kernel let it start
       if (args.dep_mode != 2) grid_dep_wait();
-      for (int it = 0; it < total; ++it) {
-        const int kh = it / nkb;
-        const int kb = it - kh * nkb;
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(S.empty + 8 * s, ph ^ 1u, wait_ns)) {
-          atomicExch(args.err, QTP_DEVERR_TIMEOUT_EMPTY);
-          atomicExch(&abort_flag, 1);
-          break;
-        }
-        if (*(volatile int*)&abort_flag) break;
-        if (it == args.withhold) {  // failure-path test: this stage never arrives
+      const int fneg = f == 0 ? 0 : p - f;
+      int s = 0, it = 0;
+      uint32_t ph = 0;
+      bool run = true;
+      for (int kh = 0; kh < 2 && run; ++kh) {
+        const int ga = args.a_fneg[h][kh] ? fneg : f;
+        const int gb = args.b_fneg[h][kh] ? fneg : f;
+        const int pa = args.a_plane[h][kh] * NP, pb = args.b_plane[h][kh] * NP;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const uint32_t full_s = S.full + 8 * s;
+          if (!mbar_wait(S.empty + 8 * s, ph ^ 1u, wait_ns)) {
+            atomicExch(args.err, QTP_DEVERR_TIMEOUT_EMPTY);
+            atomicExch(&abort_flag, 1);
+            run = false;
+            break;
+          }
+          if (*(volatile int*)&abort_flag) {
+            run = false;
+            break;
+          }
+          if (it != args.withhold) {  // (failure-path test: a withheld stage never arrives)
+            mbar_expect_tx(full_s, (uint32_t)(NP * (A_TILE + B_TILE)));
+            const int k0 = kb * BK;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              const uint32_t ta = S.a + (uint32_t)(s * NP + q) * A_TILE;
+              const uint32_t tb = S.b + (uint32_t)(s * NP + q) * B_TILE;
+              if (A_MN) {
+                tma_load_4d(ta, &args.tmA, full_s, mt * BM, k0, ga, pa + q);
+                tma_load_4d(ta + 128u * BK, &args.tmA, full_s, mt * BM + 64, k0, ga, pa + q);
+              } else {
+                tma_load_4d(ta, &args.tmA, full_s, k0, mt * BM, ga, pa + q);
+              }
+              if (B_MN) {
+#pragma unroll
+                for (int c = 0; c < BN / 64; ++c)
+                  tma_load_4d(tb + 128u * BK * c, &args.tmB, full_s, nt * BN + 64 * c, k0, gb, pb + q);
+              } else {
+                tma_load_4d(tb, &args.tmB, full_s, k0, nt * BN, gb, pb + q);
+              }
+            }
+          }
           issued = it + 1;
-          continue;
-        }
-        mbar_expect_tx(S.full + 8 * s, (uint32_t)(NP * (A_TILE + B_TILE)));
-        const int ga = args.a_fneg[h][kh] ? (p - f) % p : f;
-        const int gb = args.b_fneg[h][kh] ? (p - f) % p : f;
-        const int k0 = kb * BK;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          const uint32_t ta = S.a + (uint32_t)(s * NP + q) * A_TILE;
-          const uint32_t tb = S.b + (uint32_t)(s * NP + q) * B_TILE;
-          const int ca = args.a_plane[h][kh] * NP + q;
-          const int cb = args.b_plane[h][kh] * NP + q;
-          if (A_MN) {
-            tma_load_4d(ta, &args.tmA, S.full + 8 * s, mt * BM, k0, ga, ca);
-            tma_load_4d(ta + 128u * BK, &args.tmA, S.full + 8 * s, mt * BM + 64, k0, ga, ca);
-          } else {
-            tma_load_4d(ta, &args.tmA, S.full + 8 * s, k0, mt * BM, ga, ca);
-          }
-          if (B_MN) {
-#pragma unroll
-            for (int c = 0; c < BN / 64; ++c)
-              tma_load_4d(tb + 128u * BK * c, &args.tmB, S.full + 8 * s, nt * BN + 64 * c, k0, gb, cb);
-          } else {
-            tma_load_4d(tb, &args.tmB, S.full + 8 * s, k0, nt * BN, gb, cb);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
           }
         }
-        issued = it + 1;
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // The issuing thread is the critical path of narrow tiles: no division
+    // in the loop (stage, phase, segment and descriptor words are counters),
+    // one asm statement per K step.
     if (lane == 0) {
+      static_assert(BK == 16, "one 16-deep MMA step per stage");
       // MMA width: this tile's valid columns rounded up to 16 (<= BN)
       int nw = args.N - nt * BN;
       nw = nw > BN ? BN : ((nw + 15) & ~15);
       const uint32_t idesc = make_idesc(A_MN, B_MN, nw);
       const uint64_t da0 = part_desc<A_MN, BK>(S.a, 0);
       const uint64_t db0 = part_desc<B_MN, BK>(S.b, 0);
+      const uint32_t a_hi = (uint32_t)(da0 >> 32), b_hi = (uint32_t)(db0 >> 32);
+      constexpr uint32_t A_PART = (uint32_t)A_TILE >> 4, B_PART = (uint32_t)B_TILE >> 4;
+      constexpr uint32_t A_STAGE = (uint32_t)(NP * A_TILE) >> 4, B_STAGE = (uint32_t)(NP * B_TILE) >> 4;
       const uint32_t d_re = tmem;
       const uint32_t d_im = tmem + (uint32_t)BN;
       const uint32_t c_re = SPLIT ? tmem + 2u * BN : d_re;  // correction accumulators
       const uint32_t c_im = SPLIT ? tmem + 3u * BN : d_im;
-      uint32_t acc_re = 0, acc_im = 0, acc_cre = 0, acc_cim = 0;
+      uint32_t acc = 0;
+      uint32_t a_lo = (uint32_t)da0, b_lo = (uint32_t)db0;  // descriptor words of stage s
+      int s = 0;
+      uint32_t ph = 0;
+      int segleft = seg, j = 0;
       bool ok = true;
-      for (int it = 0; it < total; ++it) {
-        const int kh = it / nkb;
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (PROMOTE && it > 0 && it % seg == 0) {
-          // a new segment: wait until the epilogue has folded the previous
-          // one into the running sum, then restart the accumulators at zero
-          const int j = it / seg - 1;
-          if (!mbar_wait(S.acc_empty, (uint32_t)j & 1u, wait_ns)) {
-            atomicExch(args.err, QTP_DEVERR_TIMEOUT_ACC);
+      for (int kh = 0; kh < 2 && ok; ++kh) {
+        uint32_t i0, i1, i2, i3;
+        signed_idescs(idesc, args.negmask[h][kh], i0, i1, i2, i3);
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (PROMOTE && segleft == 0) {
+            // a new segment: wait until the epilogue has folded the previous
+            // one into the running sum, then restart the accumulators at zero
+            if (!mbar_wait(S.acc_empty, (uint32_t)j & 1u, wait_ns)) {
+              atomicExch(args.err, QTP_DEVERR_TIMEOUT_ACC);
+              atomicExch(&abort_flag, 1);
+              ok = false;
+              break;
+            }
+            fence_after();
+            ++j;
+            acc = 0u;
+            segleft = seg;
+          }
+          if (!mbar_wait(S.full + 8 * s, ph, wait_ns)) {
+            atomicExch(args.err, QTP_DEVERR_TIMEOUT_FULL);
             atomicExch(&abort_flag, 1);
             ok = false;
             break;
           }
           fence_after();
-          acc_re = 0u;
-          acc_im = 0u;
+          complex_kstep_issue<NP, SPLIT>(a_lo, a_hi, b_lo, b_hi, A_PART, B_PART, i0, i1, i2, i3, d_re, d_im, c_re,
+                                         c_im, acc);
+          acc = 1u;
+          mma_commit(S.empty + 8 * s);  // frees the stage when these MMAs complete
+          // end of a segment other than the last: hand the accumulators over
+          if (PROMOTE && --segleft == 0 && !(kh == 1 && kb + 1 == nkb)) mma_commit(S.acc_full);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+            a_lo = (uint32_t)da0;
+            b_lo = (uint32_t)db0;
+          } else {
+            a_lo += A_STAGE;
+            b_lo += B_STAGE;
+          }
         }
-        if (!mbar_wait(S.full + 8 * s, ph, wait_ns)) {
-          atomicExch(args.err, QTP_DEVERR_TIMEOUT_FULL);
-          atomicExch(&abort_flag, 1);
-          ok = false;
-          break;
-        }
-        fence_after();
-        const uint32_t neg = args.negmask[h][kh];
-        // descriptors of this stage's part tiles: the base descriptor advanced by
-        // (byte offset >> 4) in its start-address field (no carry: smem < 256 KB)
-        const uint64_t da = da0 + (uint64_t)((uint32_t)(s * NP * A_TILE) >> 4);
-        const uint64_t db = db0 + (uint64_t)((uint32_t)(s * NP * B_TILE) >> 4);
-#pragma unroll
-        for (int k16 = 0; k16 < BK / 16; ++k16) {
-          // part tiles: NP == 4: re_hi, re_lo, im_hi, im_lo; NP == 2: re, im
-          const uint32_t ka = (uint32_t)k16 * (A_MN ? 2048u : 32u) >> 4;
-          const uint32_t kb = (uint32_t)k16 * (B_MN ? 2048u : 32u) >> 4;
-          complex_kstep<NP, SPLIT>(da + ka, db + kb, (uint32_t)(A_TILE >> 4), (uint32_t)(B_TILE >> 4), idesc, neg,
-                                   d_re, d_im, c_re, c_im, acc_re, acc_im, acc_cre, acc_cim);
-        }
-        mma_commit(S.empty + 8 * s);  // frees the stage when these MMAs complete
-        // end of a segment other than the last: hand the accumulators over
-        if (PROMOTE && (it + 1) % seg == 0 && it + 1 < total) mma_commit(S.acc_full);
       }
       if (ok) {
         mma_commit(S.acc_full);

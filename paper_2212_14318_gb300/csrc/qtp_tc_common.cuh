@@ -270,6 +270,95 @@ __device__ __forceinline__ void complex_kstep(uint64_t da, uint64_t db, uint32_t
   acc_im = 1u;
 }
 
+// The same K step with every MMA issued from one asm statement.  The MMA
+// warp's single issuing thread is the critical path for 128-wide and
+// narrower tiles (a 16-deep step of 12 MMAs takes ~1100 cycles at N = 128,
+// and every dependent instruction of the issue loop adds to it), so the
+// descriptors travel as 32-bit low words (start address >> 4 and the leading
+// byte offset: a part or stage offset never carries out of the 14-bit
+// address field, shared memory being < 256 KB) with one shared high word per
+// operand, are packed with mov.b64 inside the asm, and the accumulate
+// predicates are set once.  a_lo / b_lo: low words of part 0 of the A / B
+// tiles; a_step / b_step: part-to-part increments; i0..i3: instruction
+// descriptors of the four real products (negate-B bit per sign, see
+// complex_kstep); acc: 0 for the first K step into the accumulators.
+template <int NP, bool SPLIT>
+__device__ __forceinline__ void complex_kstep_issue(uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi,
+                                                    uint32_t a_step, uint32_t b_step, uint32_t i0, uint32_t i1,
+                                                    uint32_t i2, uint32_t i3, uint32_t d_re, uint32_t d_im,
+                                                    uint32_t c_re, uint32_t c_im, uint32_t acc) {
+  if constexpr (NP == 4) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred pa, pc, pt;\n\t"
+        ".reg .b32 t1, t2, t3;\n\t"
+        ".reg .b64 arh, arl, aih, ail, brh, brl, bih, bil;\n\t"
+        "setp.ne.b32 pa, %14, 0;\n\t"
+        "setp.eq.b32 pt, %14, %14;\n\t"
+        "setp.ne.b32 pc, %15, 0;\n\t"
+        "add.u32 t1, %0, %4;\n\t"
+        "add.u32 t2, t1, %4;\n\t"
+        "add.u32 t3, t2, %4;\n\t"
+        "mov.b64 arh, {%0, %1};\n\t"
+        "mov.b64 arl, {t1, %1};\n\t"
+        "mov.b64 aih, {t2, %1};\n\t"
+        "mov.b64 ail, {t3, %1};\n\t"
+        "add.u32 t1, %2, %5;\n\t"
+        "add.u32 t2, t1, %5;\n\t"
+        "add.u32 t3, t2, %5;\n\t"
+        "mov.b64 brh, {%2, %3};\n\t"
+        "mov.b64 brl, {t1, %3};\n\t"
+        "mov.b64 bih, {t2, %3};\n\t"
+        "mov.b64 bil, {t3, %3};\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%10], arh, brh, %6, pa;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%12], arh, brl, %6, pc;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%11], arh, bih, %8, pa;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%13], arh, bil, %8, pc;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%12], arl, brh, %6, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%13], arl, bih, %8, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%10], aih, bih, %7, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%12], aih, bil, %7, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%11], aih, brh, %9, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%13], aih, brl, %9, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%12], ail, bih, %7, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%13], ail, brh, %9, pt;\n\t"
+        "}" ::"r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(a_step), "r"(b_step), "r"(i0), "r"(i1), "r"(i2),
+        "r"(i3), "r"(d_re), "r"(d_im), "r"(c_re), "r"(c_im), "r"(acc), "r"(SPLIT ? acc : 1u)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred pa, pt;\n\t"
+        ".reg .b32 t1;\n\t"
+        ".reg .b64 ar, ai, br, bi;\n\t"
+        "setp.ne.b32 pa, %10, 0;\n\t"
+        "setp.eq.b32 pt, %10, %10;\n\t"
+        "add.u32 t1, %0, %4;\n\t"
+        "mov.b64 ar, {%0, %1};\n\t"
+        "mov.b64 ai, {t1, %1};\n\t"
+        "add.u32 t1, %2, %5;\n\t"
+        "mov.b64 br, {%2, %3};\n\t"
+        "mov.b64 bi, {t1, %3};\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%11], ar, br, %6, pa;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%12], ar, bi, %8, pa;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%11], ai, bi, %7, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%12], ai, br, %9, pt;\n\t"
+        "}" ::"r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(a_step), "r"(b_step), "r"(i0), "r"(i1), "r"(i2),
+        "r"(i3), "r"(acc), "r"(d_re), "r"(d_im)
+        : "memory");
+  }
+}
+
+// Instruction descriptors of the four real products of a complex product:
+// bit q of neg subtracts product q (ar.br, ai.bi, ar.bi, ai.br).
+__device__ __forceinline__ void signed_idescs(uint32_t idesc, uint32_t neg, uint32_t& i0, uint32_t& i1,
+                                              uint32_t& i2, uint32_t& i3) {
+  i0 = (neg & 1u) ? idesc | kNegB : idesc;
+  i1 = (neg & 2u) ? idesc | kNegB : idesc;
+  i2 = (neg & 4u) ? idesc | kNegB : idesc;
+  i3 = (neg & 8u) ? idesc | kNegB : idesc;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
