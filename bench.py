@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--workload", default="video",
-                    choices=["video", "precision", "small", "diff", "batch", "tsvd", "long1000", "long4096"])
+                    choices=["video", "precision", "small", "diff", "batch", "tsvd", "long1000", "long1024", "long4096"])
     ap.add_argument("--batch-count", type=int, default=4096, help="products in the batch workload")
     return ap.parse_args()
 
@@ -595,7 +595,9 @@ def run_batch(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def leg(precision, steps, warmup):
-        plan = qtp.BatchPlan(shapes, precision)
+        # split-BF16: the plan times the products' routing (grouped kernel vs
+        # single-product kernel from a size threshold) at creation
+        plan = qtp.BatchPlan(shapes, precision, autotune=precision != "fp32")
         plan.set_tracing(True)
         # the batch's tensors are validated and marshalled once (BatchPlan.bind):
         # a step is one qtp_forward_batched call
@@ -624,6 +626,14 @@ def run_batch(args):
     sampler.start()
     plan, Cs, ms, st = leg(args.precision, args.steps, args.warmup)
     clocks = sampler.stop()
+    route_min, tuned = plan.route()
+    cands = [2**31 - 1, 192, 128, 96, 64, 48]
+    routing = {"route_min": None if route_min == 2**31 - 1 else route_min,
+               "what": "products with min(m, s) >= route_min run in the single-product kernel (wide tiles), the "
+                       "rest in the grouped kernel; chosen at plan creation by timing the products for each "
+                       "threshold on a zeroed scratch workspace (null: grouped only)",
+               "products_ms_by_threshold": {("grouped only" if c == 2**31 - 1 else str(c)): t
+                                            for c, t in zip(cands, tuned)}}
 
     def sampled_err(Cs):
         rng = np.random.default_rng(7)
@@ -652,7 +662,7 @@ def run_batch(args):
     hB = [b.cpu().pin_memory() for b in Bs]
     hC = [torch.empty((2, m, s, p, 2), dtype=torch.float32).pin_memory() for (m, _, s, p) in shapes]
     dC = [torch.empty((2, m, s, p, 2), dtype=torch.float32, device=dev) for (m, _, s, p) in shapes]
-    eplan = qtp.BatchPlan(shapes, args.precision)
+    eplan = qtp.BatchPlan(shapes, args.precision, autotune=args.precision != "fp32")
     ebound = eplan.bind(As, Bs, dC)
     ebound.forward()
     eplan.sync()
@@ -703,7 +713,7 @@ def run_batch(args):
                                "p in {8,12,16,31,32,64,100,128}, N(0,1), transforms one launch per tube length, "
                                "products one persistent launch, CUDA graph",
                    "precision": args.precision, "l2": "inputs larger than L2; 256 MB flush before every step"},
-        "rel_err": rel, "roofline": roof, "stages": stages, "fp32_path": fp32,
+        "rel_err": rel, "roofline": roof, "stages": stages, "fp32_path": fp32, "routing": routing,
         "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(sum(a.numel() * 4 for a in As) + sum(b.numel() * 4 for b in Bs)),
                 "d2h_bytes_per_step": int(sum(c.numel() * 4 for c in dC))},

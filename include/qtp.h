@@ -66,7 +66,8 @@ typedef enum {
   QTP_ERR_WORKSPACE = 3,    /* workspace missing or smaller than required */
   QTP_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed          */
   QTP_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up         */
-  QTP_ERR_INTERNAL = 6
+  QTP_ERR_INTERNAL = 6,
+  QTP_ERR_NOT_CONVERGED = 7 /* an iteration stopped at its limit (T-SVD)  */
 } qtp_status;
 
 /* Arithmetic of the per-frequency products (Alg. 5.1 Step 2).  The tube FFTs
@@ -92,13 +93,16 @@ typedef struct qtp_plan qtp_plan;
  * each below 2^31 complex entries per plane.  Allocates the twiddle table
  * w^e = exp(-2 pi i e / p), e in [0, p) (eq. DFT, generated in FP64 and
  * rounded to FP32) and synchronises the current device.  flags: 0 or
- * QTP_PLAN_AUTOTUNE.  With QTP_PLAN_AUTOTUNE (BF16 precisions) the plan
- * times, for the forward and both backward product kinds, every tensor-core
- * tile shape that keeps the split-BF16 accuracy bound for that kind's
- * reduction length on scratch spectra it allocates and frees, and keeps the
- * fastest; choices are cached per (device, shape, precision) in the process
- * and appended to the file named by the environment variable
- * QTP_AUTOTUNE_CACHE, if set, which later processes read. */
+ * QTP_PLAN_AUTOTUNE.  With QTP_PLAN_AUTOTUNE the plan times, on scratch
+ * buffers it allocates and frees, (BF16 precisions) for the forward and both
+ * backward product kinds every tensor-core tile shape that keeps the
+ * split-BF16 accuracy bound for that kind's reduction length, and (p > 128)
+ * every form of the forward and of the inverse tube transform (one kernel,
+ * two passes with runtime-radix sub-transforms, two passes with compile-time
+ * ones), and keeps the fastest of each; choices are cached per (device,
+ * shape, precision) in the process and appended to the file named by the
+ * environment variable QTP_AUTOTUNE_CACHE, if set, which later processes
+ * read. */
 QTP_API qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p,
                            int precision, unsigned flags);
 QTP_API qtp_status qtp_plan_destroy(qtp_plan* plan);
@@ -117,9 +121,10 @@ QTP_API qtp_status qtp_plan_get_tiles(const qtp_plan* plan, int* tiles3);
  * (Steps 1, 2, 3 of Algorithm 5.1; the backward transforms A and B, then dC,
  * forms dA and dB, and transforms both back in one launch), or 1 forward
  * launch for products small enough to run whole in one CTA.  Long tubes
- * (p > 128 without a one-kernel transform, and with a factor between 4 and
- * sqrt(p)) transform in two launches each (through an intermediate in the
- * workspace): 5 and 8.  The training pair issues *forward
+ * (p > 128 without a one-kernel compile-time transform that factor as
+ * p = N1 N2 with N2 in {256, 128, 100, 64} and N1 <= 32, or from p = 2048 with
+ * any factor between 4 and sqrt(p)) transform in two launches per transform
+ * step (through an intermediate in the workspace): up to 5 and 8.  The training pair issues *forward
  * (qtp_forward_saving, never the one-CTA route) and *backward minus the
  * transform launches of A and B (qtp_backward_saved).  Library extension
  * with no counterpart in the paper; for launch accounting.
@@ -238,6 +243,16 @@ QTP_API qtp_status qtp_tsvd_workspace_size(int m, int n, int p, size_t* bytes);
 QTP_API qtp_status qtp_tsvd(int m, int n, int p, const float* A, float* U, float* S, float* V, float* sigma,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* Synchronise stream after a qtp_tsvd call of this shape on this workspace
+ * and report whether every frequency pair's Jacobi sweeps converged: each of
+ * the two sweep phases stops after a sweep without rotations or after 40
+ * sweeps; a pair that still rotated in its 40th sweep gets factors that are
+ * written as usual but may miss the orthogonality bound, and this call then
+ * returns QTP_ERR_NOT_CONVERGED (else QTP_OK; QTP_ERR_CUDA if the stream
+ * reports an error).  The status lives in the workspace and is cleared by the
+ * next qtp_tsvd on it. */
+QTP_API qtp_status qtp_tsvd_sync(int m, int n, int p, const void* workspace, void* stream);
+
 /* Gradients of a real loss L(C), C = A * B, with each quaternion entry taken
  * as four independent reals (not in the paper; a training-style use of it):
  *     dA = dC * B^H,   dB = A^H * dC,
@@ -263,6 +278,7 @@ typedef struct qtp_batch_plan qtp_batch_plan;
 
 /* Flags of qtp_batch_plan_create. */
 #define QTP_BATCH_NO_GRAPH 1u  /* launch the kernels directly instead of replaying a CUDA graph */
+#define QTP_BATCH_AUTOTUNE 2u  /* time the products' routing at plan creation (BF16 precisions) */
 
 /* Plan a batch of `count` products C_i = A_i * B_i (Definition 2.3, each by
  * Algorithm 5.1).  Shapes are copied; each must satisfy the limits of
@@ -288,6 +304,23 @@ QTP_API qtp_status qtp_batch_workspace_size(const qtp_batch_plan* plan, size_t* 
  * Asynchronous on stream. */
 QTP_API qtp_status qtp_forward_batched(qtp_batch_plan* plan, const float* const* A, const float* const* B,
                                        float* const* C, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Routing of a batch's tensor-core products (library extension; the paper has
+ * no counterpart).  Step 2 runs every product either in the grouped kernel
+ * (128 x 64 tiles that compute both output halves) or in the single-product
+ * kernel (128 x 256 / 128 x 128 tiles per output half, one launch each,
+ * spread over four streams of the plan inside the graph): products whose
+ * split-BF16 reduction exceeds 384 per half always take the latter, and so do
+ * products with min(m, s) >= *route_min.  Without QTP_BATCH_AUTOTUNE
+ * *route_min is INT_MAX (every other product grouped; the environment
+ * variable QTP_BATCH_ROUTE_MIN overrides it).  With QTP_BATCH_AUTOTUNE the
+ * plan times the products on a zeroed scratch workspace it allocates and
+ * frees for the thresholds INT_MAX, 192, 128, 96, 64, 48 and keeps the
+ * fastest (cached per device, precision and shapes for the process);
+ * tuned_ms[i] (i < *tuned_count <= 8) receives those times in that order.
+ * Any output pointer may be NULL. */
+QTP_API qtp_status qtp_batch_plan_route(const qtp_batch_plan* plan, int* route_min, float* tuned_ms,
+                                        int* tuned_count);
 
 /* Tracing of batched calls: four events around the three stages (forward
  * transforms, products, inverse transforms); ms3 receives their durations for

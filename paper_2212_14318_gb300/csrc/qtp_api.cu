@@ -58,7 +58,7 @@ size_t c32_bytes(long long p, long long rows, long long cols) {
 // Intermediate of the two-pass long-tube transforms: the largest set of
 // tensors transformed in one launch (A with B, dC alone, C alone, dA with dB).
 size_t split_scratch_bytes(const qtp_plan* pl) {
-  if (!pl->fft_split_fwd && !pl->fft_split_inv) return 0;
+  if (pl->fft_split_fwd == FFT_ONE && pl->fft_split_inv == FFT_ONE) return 0;
   const size_t a = align256(fft_split_scratch_bytes(pl->p, pl->m, pl->n));
   const size_t b = align256(fft_split_scratch_bytes(pl->p, pl->n, pl->s));
   const size_t c = align256(fft_split_scratch_bytes(pl->p, pl->m, pl->s));
@@ -101,13 +101,31 @@ BwdLayout bwd_layout(const qtp_plan* pl) {
 // long tubes (scratch: the layout's intermediate).
 cudaError_t plan_fft_fwd(const qtp_plan* pl, const FftFwdJob* jobs, int njobs, int fmt, char* scratch,
                          cudaStream_t st) {
-  if (pl->fft_split_fwd) return launch_fft_fwd_split(jobs, njobs, fmt, pl->p, pl->d_tw, (float2*)scratch, st);
+  if (pl->fft_split_fwd == FFT_LONG) return launch_fft_fwd_long(jobs, njobs, fmt, pl->p, pl->d_tw, (float2*)scratch, st);
+  if (pl->fft_split_fwd == FFT_SPLIT)
+    return launch_fft_fwd_split(jobs, njobs, fmt, pl->p, pl->d_tw, (float2*)scratch, st);
   return launch_fft_fwd(jobs, njobs, fmt, pl->rp, pl->d_tw, st);
 }
 
 cudaError_t plan_fft_inv(const qtp_plan* pl, const FftInvJob* jobs, int njobs, char* scratch, cudaStream_t st) {
-  if (pl->fft_split_inv) return launch_fft_inv_split(jobs, njobs, pl->p, pl->d_tw, (float2*)scratch, st);
+  if (pl->fft_split_inv == FFT_LONG) return launch_fft_inv_long(jobs, njobs, pl->p, pl->d_tw, (float2*)scratch, st);
+  if (pl->fft_split_inv == FFT_SPLIT) return launch_fft_inv_split(jobs, njobs, pl->p, pl->d_tw, (float2*)scratch, st);
   return launch_fft_inv(jobs, njobs, pl->rp, pl->d_tw, st);
+}
+
+// Twiddle entries of a plan: w_p^e (e < p), followed for the long transform
+// form by w_N2^e (e < N2).
+int plan_twiddle_count(const qtp_plan* pl) {
+  int n2 = 0;
+  if (pl->p > 128 && fft_long_dims(pl->p, nullptr, &n2)) return pl->p + n2;  // any form may be chosen
+  return pl->p;
+}
+
+cudaError_t plan_twiddles(const qtp_plan* pl, cudaStream_t st) {
+  cudaError_t e = launch_twiddles(pl->d_tw, pl->p, st);
+  const int n = plan_twiddle_count(pl);
+  if (e == cudaSuccess && n > pl->p) e = launch_twiddles(pl->d_tw + pl->p, n - pl->p, st);
+  return e;
 }
 
 qtp_status check_plan(const qtp_plan* pl) {
@@ -371,7 +389,10 @@ qtp_status run_products_bwd(const qtp_plan* pl, const void* sa, const void* sb, 
 // process and, when QTP_AUTOTUNE_CACHE names a file, across processes.
 // ----------------------------------------------------------------------------
 std::mutex g_tune_mu;
-std::map<std::string, std::array<int, 3>> g_tune_cache;
+// per (device, shape, precision): tiles of the forward, dA, dB products and
+// the forms of the forward and inverse tube transforms
+using TuneRecord = std::array<int, 5>;
+std::map<std::string, TuneRecord> g_tune_cache;
 bool g_tune_file_loaded = false;
 
 std::string tune_key(const qtp_plan* pl) {
@@ -392,69 +413,60 @@ void tune_cache_load() {
   if (!path) return;
   FILE* f = fopen(path, "r");
   if (!f) return;
-  char key[256];
-  int a, b, c;
-  while (fscanf(f, "%255s %d %d %d", key, &a, &b, &c) == 4) g_tune_cache[key] = {a, b, c};
+  char line[512], key[256];
+  while (fgets(line, sizeof(line), f)) {
+    TuneRecord r;
+    if (sscanf(line, "%255s %d %d %d %d %d", key, &r[0], &r[1], &r[2], &r[3], &r[4]) == 6) g_tune_cache[key] = r;
+  }
   fclose(f);
 }
 
-void tune_cache_store(const std::string& key, const std::array<int, 3>& t) {
+void tune_cache_store(const std::string& key, const TuneRecord& t) {
   g_tune_cache[key] = t;
   const char* path = getenv("QTP_AUTOTUNE_CACHE");
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d\n", key.c_str(), t[0], t[1], t[2]);
+  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), t[0], t[1], t[2], t[3], t[4]);
   fclose(f);
 }
 
-// Mean time (ms) of `reps` launches of one tensor-core problem, after a warm-up.
-float time_tc(const TcProblem& pr, int* d_err, cudaEvent_t e0, cudaEvent_t e1, int reps) {
-  char msg[256];
-  if (launch_gemm_tc(pr, d_err, 0, msg, sizeof(msg)) != cudaSuccess) return 1e30f;
+// Mean time (ms) of `reps` runs of fn on the legacy stream, after a warm-up.
+template <class F>
+float time_ms(F fn, cudaEvent_t e0, cudaEvent_t e1, int reps) {
+  if (fn() != cudaSuccess) return 1e30f;
   cudaEventRecord(e0, 0);
-  for (int i = 0; i < reps; ++i) launch_gemm_tc(pr, d_err, 0, msg, sizeof(msg));
+  for (int i = 0; i < reps; ++i) fn();
   cudaEventRecord(e1, 0);
-  if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+  if (cudaEventSynchronize(e1) != cudaSuccess) {
+    cudaGetLastError();
+    return 1e30f;
+  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   return ms / reps;
 }
 
-qtp_status autotune(qtp_plan* pl) {
-  if (pl->precision == QTP_PREC_FP32) return QTP_OK;  // one FP32 kernel: nothing to choose
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  tune_cache_load();
-  const std::string key = tune_key(pl);
-  auto hit = g_tune_cache.find(key);
-  if (hit != g_tune_cache.end()) {
-    for (int k = 0; k < 3; ++k) pl->tile[k] = hit->second[k];
-    return QTP_OK;
-  }
+// Tile of each product kind: the candidates that keep split-BF16 within 1e-5
+// at that kind's reduction length, timed on scratch spectra.
+cudaError_t tune_tiles(qtp_plan* pl, TuneRecord& best, cudaEvent_t e0, cudaEvent_t e1) {
   const int fmt = spec_format(pl->precision);
   const size_t bA = spec_bytes(fmt, pl->p, pl->m, pl->n), bB = spec_bytes(fmt, pl->p, pl->n, pl->s),
                bG = spec_bytes(fmt, pl->p, pl->m, pl->s);
   const size_t bOut = c32_bytes(pl->p, std::max(pl->m, pl->n), std::max(pl->s, pl->n));
   char* scratch = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaMalloc(&scratch, bA + bB + bG + bOut);
   if (e == cudaSuccess) e = cudaMemset(scratch, 0, bA + bB + bG);
-  if (e == cudaSuccess) e = cudaEventCreate(&e0);
-  if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) {
     cudaFree(scratch);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    return cuda_fail(e, "autotune scratch");
+    return e;
   }
   char* sa = scratch;
   char* sb = sa + bA;
   char* sg = sb + bB;
   float2* out = (float2*)(sg + bG);
-  std::array<int, 3> best = {TILE_AUTO, TILE_AUTO, TILE_AUTO};
   for (int kind = 0; kind < 3; ++kind) {
     TcProblem pr = kind == 0 ? tc_fwd(pl, sa, sb, out) : kind == 1 ? tc_bwd_a(pl, sb, sg, out) : tc_bwd_b(pl, sa, sg, out);
-    // candidates that keep split-BF16 within 1e-5 at this reduction length
     std::vector<int> cands = {TILE_128_PROMOTE};
     if (pr.nparts == 2 || pr.K <= kTcSplitMaxK) cands.push_back(TILE_128_SPLIT);
     if (pr.nparts == 2 || pr.K <= kTcSingleMaxK) {
@@ -464,17 +476,104 @@ qtp_status autotune(qtp_plan* pl) {
     float best_ms = 1e30f;
     for (int c : cands) {
       pr.tile = c;
-      const float ms = time_tc(pr, pl->d_err, e0, e1, 3);
+      char msg[256];
+      const float ms = time_ms([&] { return launch_gemm_tc(pr, pl->d_err, 0, msg, sizeof(msg)); }, e0, e1, 3);
       if (ms < best_ms) {
         best_ms = ms;
         best[kind] = c;
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(scratch);
   e = cudaDeviceSynchronize();
+  cudaFree(scratch);
+  return e;
+}
+
+// Form of the forward and of the inverse tube transform (one kernel, runtime
+// two-pass, compile-time long two-pass), timed on scratch tensors of the
+// plan's shapes: the forward transforms A and B, the inverse C.
+cudaError_t tune_forms(qtp_plan* pl, TuneRecord& best, cudaEvent_t e0, cudaEvent_t e1) {
+  std::vector<int> cands = {FFT_ONE};
+  if (fft_split_dims(pl->p, nullptr, nullptr)) cands.push_back(FFT_SPLIT);
+  if (fft_long_dims(pl->p, nullptr, nullptr)) cands.push_back(FFT_LONG);
+  best[3] = pl->fft_split_fwd;
+  best[4] = pl->fft_split_inv;
+  if (cands.size() == 1) return cudaSuccess;
+  const int fmt = spec_format(pl->precision);
+  const size_t iA = c32_bytes(pl->p, pl->m, pl->n), iB = c32_bytes(pl->p, pl->n, pl->s),
+               iC = c32_bytes(pl->p, pl->m, pl->s);
+  const size_t sA = spec_bytes(fmt, pl->p, pl->m, pl->n), sB = spec_bytes(fmt, pl->p, pl->n, pl->s);
+  const size_t zs = std::max(align256(fft_split_scratch_bytes(pl->p, pl->m, pl->n)) +
+                                 align256(fft_split_scratch_bytes(pl->p, pl->n, pl->s)),
+                             align256(fft_split_scratch_bytes(pl->p, pl->m, pl->s)));
+  char* scratch = nullptr;
+  const size_t total = iA + iB + 2 * iC + sA + sB + zs;
+  cudaError_t e = cudaMalloc(&scratch, total);
+  if (e == cudaSuccess) e = cudaMemset(scratch, 0, total);
+  if (e != cudaSuccess) {
+    cudaFree(scratch);
+    return e;
+  }
+  char* A = scratch;
+  char* B = A + iA;
+  char* Chat = B + iB;
+  char* C = Chat + iC;
+  char* spA = C + iC;
+  char* spB = spA + sA;
+  char* z = spB + sB;
+  FftFwdJob jobs[2];
+  jobs[0].in = (const float2*)A;
+  jobs[0].out = spA;
+  jobs[0].rows = pl->m; jobs[0].cols = pl->n; jobs[0].ld = (int)spec_ld(fmt, pl->n);
+  jobs[0].nblocks = nblocks_fwd(pl->m, pl->n, pl->p, fmt);
+  jobs[1].in = (const float2*)B;
+  jobs[1].out = spB;
+  jobs[1].rows = pl->n; jobs[1].cols = pl->s; jobs[1].ld = (int)spec_ld(fmt, pl->s);
+  jobs[1].nblocks = nblocks_fwd(pl->n, pl->s, pl->p, fmt);
+  FftInvJob ij;
+  ij.in = (const float2*)Chat;
+  ij.out = (float2*)C;
+  ij.rows = pl->m; ij.cols = pl->s;
+  ij.nblocks = nblocks_for(pl->m, pl->s, pl->p, true);
+  const int fwd0 = pl->fft_split_fwd, inv0 = pl->fft_split_inv;
+  float bf = 1e30f, bi = 1e30f;
+  for (int c : cands) {
+    pl->fft_split_fwd = c;
+    pl->fft_split_inv = c;
+    const float tf = time_ms([&] { return plan_fft_fwd(pl, jobs, 2, fmt, z, 0); }, e0, e1, 3);
+    const float ti = time_ms([&] { return plan_fft_inv(pl, &ij, 1, z, 0); }, e0, e1, 3);
+    if (tf < bf) { bf = tf; best[3] = c; }
+    if (ti < bi) { bi = ti; best[4] = c; }
+  }
+  pl->fft_split_fwd = fwd0;
+  pl->fft_split_inv = inv0;
+  e = cudaDeviceSynchronize();
+  cudaFree(scratch);
+  return e;
+}
+
+qtp_status autotune(qtp_plan* pl) {
+  const bool tiles = pl->precision != QTP_PREC_FP32;  // one FP32 products kernel: no tile to choose
+  const bool forms = pl->p > 128;                     // one transform form below
+  if (!tiles && !forms) return QTP_OK;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_cache_load();
+  const std::string key = tune_key(pl);
+  auto hit = g_tune_cache.find(key);
+  if (hit != g_tune_cache.end()) {
+    for (int k = 0; k < 3; ++k) pl->tile[k] = hit->second[k];
+    pl->fft_split_fwd = hit->second[3];
+    pl->fft_split_inv = hit->second[4];
+    return QTP_OK;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  TuneRecord best = {TILE_AUTO, TILE_AUTO, TILE_AUTO, pl->fft_split_fwd, pl->fft_split_inv};
+  if (e == cudaSuccess && tiles) e = tune_tiles(pl, best, e0, e1);
+  if (e == cudaSuccess && forms) e = tune_forms(pl, best, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(e, "autotune");
   int v = 0;
   cudaMemcpy(&v, pl->d_err, sizeof(int), cudaMemcpyDeviceToHost);
@@ -483,6 +582,8 @@ qtp_status autotune(qtp_plan* pl) {
     return fail(QTP_ERR_TIMEOUT, "autotune: a device-side wait gave up (code %d)", v);
   }
   for (int k = 0; k < 3; ++k) pl->tile[k] = best[k];
+  pl->fft_split_fwd = best[3];
+  pl->fft_split_inv = best[4];
   tune_cache_store(key, best);
   return QTP_OK;
 }
@@ -574,16 +675,16 @@ qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int preci
   pl->m = m; pl->n = n; pl->s = s; pl->p = p;
   pl->precision = precision;
   pl->rp = make_radix_plan(p);
-  pl->fft_split_fwd = fft_split_eligible(p, false) ? 1 : 0;
-  pl->fft_split_inv = fft_split_eligible(p, true) ? 1 : 0;
+  pl->fft_split_fwd = fft_form(p, false);
+  pl->fft_split_inv = fft_form(p, true);
   pl->d_tw = nullptr;
   pl->d_err = nullptr;
   pl->tracing = 0;
   cudaError_t e = cudaGetDevice(&pl->device);
-  if (e == cudaSuccess) e = cudaMalloc(&pl->d_tw, sizeof(float2) * p);
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_tw, sizeof(float2) * plan_twiddle_count(pl));
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(pl->d_err, 0, sizeof(int));
-  if (e == cudaSuccess) e = launch_twiddles(pl->d_tw, p, 0);
+  if (e == cudaSuccess) e = plan_twiddles(pl, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     if (pl->d_tw) cudaFree(pl->d_tw);
@@ -618,7 +719,7 @@ qtp_status qtp_plan_launch_count(const qtp_plan* pl, int* forward, int* backward
   if ((r = check_plan(pl)) != QTP_OK) return r;
   if (!forward || !backward) return fail(QTP_ERR_INVALID_ARG, "output pointer is NULL");
   // each transform step takes two launches in its two-pass form
-  const int sf = pl->fft_split_fwd, si = pl->fft_split_inv;
+  const int sf = pl->fft_split_fwd != FFT_ONE, si = pl->fft_split_inv != FFT_ONE;
   *forward = fused_small_eligible(pl->m, pl->n, pl->s, pl->p) ? 1 : 3 + sf + si;
   *backward = 5 + 2 * sf + si;
   return QTP_OK;
@@ -821,7 +922,7 @@ qtp_status qtp_forward_host_many(const qtp_plan* pl, int count, const float* con
 // ---------------------------------------------------------------------------
 
 struct TsvdLayout {
-  size_t tw, h, uh, vh, sh, scratch, total;
+  size_t tw, h, uh, vh, sh, scratch, status, total;
 };
 
 static TsvdLayout tsvd_layout(int m, int n, int p) {
@@ -833,7 +934,8 @@ static TsvdLayout tsvd_layout(int m, int n, int p) {
   L.vh = L.uh + c32_bytes(p, m, k);
   L.sh = L.vh + c32_bytes(p, n, k);
   L.scratch = L.sh + c32_bytes(p, k, k);
-  L.total = L.scratch + align256(tsvd_scratch_bytes(m, n, p));
+  L.status = L.scratch + align256(tsvd_scratch_bytes(m, n, p));
+  L.total = L.status + 256;
   return L;
 }
 
@@ -891,7 +993,9 @@ qtp_status qtp_tsvd(int m, int n, int p, const float* A, float* U, float* S, flo
   fj.nblocks = nblocks_fwd(m, n, p, FMT_C32);
   QTP_CUDA(launch_fft_fwd(&fj, 1, FMT_C32, rp, tw, st), "T-SVD forward FFT");
   QTP_CUDA(cudaMemsetAsync(Sh, 0, c32_bytes(p, k, k), st), "T-SVD clear S");
-  QTP_CUDA(launch_tsvd_pairs(H, m, n, p, Uh, Vh, Sh, sigma, scratch, st), "T-SVD per-frequency SVDs");
+  int* status = (int*)(ws + L.status);
+  QTP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st), "T-SVD clear status");
+  QTP_CUDA(launch_tsvd_pairs(H, m, n, p, Uh, Vh, Sh, sigma, scratch, status, st), "T-SVD per-frequency SVDs");
   FftInvJob ij[2];
   ij[0].in = Uh;
   ij[0].out = (float2*)U;
@@ -911,6 +1015,19 @@ qtp_status qtp_tsvd(int m, int n, int p, const float* A, float* U, float* S, flo
   sj.cols = k;
   sj.nblocks = nblocks_for(k, k, p, true);
   QTP_CUDA(launch_fft_inv(&sj, 1, rp, tw, st), "T-SVD inverse FFT of S");
+  return QTP_OK;
+}
+
+qtp_status qtp_tsvd_sync(int m, int n, int p, const void* workspace, void* stream) {
+  g_err[0] = 0;
+  qtp_status r;
+  if ((r = check_tsvd_shape(m, n, p)) != QTP_OK) return r;
+  if ((r = check_dev_ptr(workspace, "workspace")) != QTP_OK) return r;
+  QTP_CUDA(cudaStreamSynchronize(as_stream(stream)), "stream synchronize");
+  int v = 0;
+  QTP_CUDA(cudaMemcpy(&v, (const char*)workspace + tsvd_layout(m, n, p).status, sizeof(int), cudaMemcpyDeviceToHost),
+           "read T-SVD status");
+  if (v != 0) return fail(QTP_ERR_NOT_CONVERGED, "T-SVD: Jacobi sweeps reached their limit still rotating");
   return QTP_OK;
 }
 
@@ -1107,10 +1224,10 @@ extern "C" qtp_status qtp_forward_noalloc(int m, int n, int s, int p, int precis
   pl.m = m; pl.n = n; pl.s = s; pl.p = p;
   pl.precision = precision;
   pl.rp = make_radix_plan(p);
-  pl.fft_split_fwd = fft_split_eligible(p, false) ? 1 : 0;
-  pl.fft_split_inv = fft_split_eligible(p, true) ? 1 : 0;
+  pl.fft_split_fwd = fft_form(p, false);
+  pl.fft_split_inv = fft_form(p, true);
   // static scratch: [twiddles][error word][forward workspace]
-  const size_t tw_bytes = align256((size_t)p * sizeof(float2));
+  const size_t tw_bytes = align256((size_t)plan_twiddle_count(&pl) * sizeof(float2));
   const size_t ws_off = tw_bytes + 256;
   const size_t need = ws_off + fwd_layout(&pl).total;
   if (need > (size_t)QTP_NOALLOC_SCRATCH_BYTES)
@@ -1133,6 +1250,6 @@ extern "C" qtp_status qtp_forward_noalloc(int m, int n, int s, int p, int precis
   // The array keeps the previous call's contents: the error word must start at
   // zero and the twiddles may belong to another p, so both are rewritten here.
   QTP_CUDA(cudaMemsetAsync(pl.d_err, 0, sizeof(int), st), "clear the error word");
-  QTP_CUDA(launch_twiddles(pl.d_tw, p, st), "twiddles");
+  QTP_CUDA(plan_twiddles(&pl, st), "twiddles");
   return forward_impl(&pl, A, B, C, base + ws_off, st);
 }

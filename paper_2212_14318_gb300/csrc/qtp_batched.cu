@@ -12,10 +12,15 @@
 // The plan buckets the products by tube length p, then by size, so that CTAs
 // working at the same time share a kernel specialisation and their
 // products' spectra stay in L2; the pointer table keeps the caller's order.
-// A split-BF16 product whose reduction (n per half) is longer than the grouped
-// kernel's single accumulator keeps within 1e-5 (kTcSingleMaxK) runs its
-// products through the single-product kernel instead, whose accumulator mode
-// follows K (one launch each, after the grouped launch, in the same graph).
+// Tensor-core products can leave the grouped kernel (128 x 64 tiles, both
+// output halves per tile) for the single-product kernel (128 x 256 or
+// 128 x 128 tiles per output half, accumulator mode by K): a split-BF16
+// product whose reduction (n per half) is longer than the grouped kernel's
+// single accumulator keeps within 1e-5 (kTcSingleMaxK) always does, and with
+// QTP_BATCH_AUTOTUNE every product with min(m, s) at or above a threshold the
+// plan picks by timing (its wide MMAs cost less per column than the grouped
+// kernel's narrow ones).  Those run one launch each after the grouped launch,
+// spread over the plan's auxiliary streams, inside the same graph.
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -24,6 +29,7 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "qtp_internal.h"
@@ -63,12 +69,21 @@ struct qtp_batch_plan {
   // host copies needed to encode tensor maps
   std::vector<GroupProblem> h_probs;
   std::vector<int> prod_of_prob;  // product index of each GroupProblem
-  // products that take the single-product tensor-core kernel (long reductions)
+  // every product in walk order with its workspace offsets, and those that
+  // take the single-product tensor-core kernel (long reductions, wide routing)
   struct LongProduct {
-    int m, n, s, p;
+    int idx, m, n, s, p;
     size_t sa, sb, sc;  // workspace offsets of the spectra of A, B and C_hat
   };
+  std::vector<LongProduct> prods;
   std::vector<LongProduct> long_probs;
+  int route_min = 0x7fffffff;  // min(m, s) from which products take the single-product kernel
+  static constexpr int kAux = 4;
+  cudaStream_t aux[kAux] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kAux] = {nullptr, nullptr, nullptr, nullptr};
+  float tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // products time per candidate threshold (autotune)
+  int tune_n = 0;
   void* h_tmaps = nullptr;        // pinned
   char* tmaps_for_ws = nullptr;   // workspace base the device tensor maps point into
   // per-call pointer staging (pinned, 2 slots) and stream plumbing
@@ -105,6 +120,11 @@ void free_plan(qtp_batch_plan* b) {
   }
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (int i = 0; i < qtp_batch_plan::kAux; ++i) {
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+    if (b->aux[i]) cudaStreamDestroy(b->aux[i]);
+  }
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->h_tmaps) cudaFreeHost(b->h_tmaps);
   cudaFree(b->d_tw);
@@ -128,6 +148,32 @@ void trace(qtp_batch_plan* b, int i, cudaStream_t st, bool capturing) {
   else cudaEventRecord(b->ev[i], st);
 }
 
+// Step 2 on the tensor cores: the grouped launch, then the products that
+// take the single-product kernel, dealt round-robin over the auxiliary
+// streams (forked from st after the grouped launch and joined back).
+qtp_status enqueue_tc_products(qtp_batch_plan* b, char* ws, cudaStream_t st) {
+  const int np = b->fmt == FMT_BF16X3 ? 4 : 2;
+  BP_CUDA(launch_gemm_tc_grouped(b->d_probs, b->n_probs, b->total_tiles, np, ws, b->d_err, b->num_sms, st),
+          "batched products (tensor cores)");
+  if (b->long_probs.empty()) return QTP_OK;
+  const int na = (int)std::min<size_t>(qtp_batch_plan::kAux, b->long_probs.size());
+  BP_CUDA(cudaEventRecord(b->ev_fork, st), "fork");
+  for (int a = 0; a < na; ++a) BP_CUDA(cudaStreamWaitEvent(b->aux[a], b->ev_fork, 0), "fork");
+  for (size_t i = 0; i < b->long_probs.size(); ++i) {
+    const auto& L = b->long_probs[i];
+    const TcProblem pr = make_tc_fwd(L.m, L.n, L.s, L.p, np, TILE_AUTO, ws + L.sa, ws + L.sb, (float2*)(ws + L.sc));
+    char msg[256] = "";
+    cudaError_t e = launch_gemm_tc(pr, b->d_err, b->aux[i % na], msg, sizeof(msg));
+    if (e != cudaSuccess)
+      return set_error(QTP_ERR_CUDA, "batched products (single-product kernel): %s %s", cudaGetErrorString(e), msg);
+  }
+  for (int a = 0; a < na; ++a) {
+    BP_CUDA(cudaEventRecord(b->ev_join[a], b->aux[a]), "join");
+    BP_CUDA(cudaStreamWaitEvent(st, b->ev_join[a], 0), "join");
+  }
+  return QTP_OK;
+}
+
 // The grouped launches of one forward call, on stream st.
 qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing) {
   trace(b, 0, st, capturing);
@@ -139,16 +185,8 @@ qtp_status enqueue(qtp_batch_plan* b, char* ws, cudaStream_t st, bool capturing)
   if (b->precision == QTP_PREC_FP32) {
     BP_CUDA(launch_gemm_simt_grouped(b->d_probs, b->d_prob_tile, b->total_tiles, ws, st), "batched products (fp32)");
   } else {
-    const int np = b->fmt == FMT_BF16X3 ? 4 : 2;
-    BP_CUDA(launch_gemm_tc_grouped(b->d_probs, b->n_probs, b->total_tiles, np, ws, b->d_err, b->num_sms, st),
-            "batched products (tensor cores)");
-    for (const auto& L : b->long_probs) {
-      const TcProblem pr = make_tc_fwd(L.m, L.n, L.s, L.p, np, TILE_AUTO, ws + L.sa, ws + L.sb, (float2*)(ws + L.sc));
-      char msg[256] = "";
-      cudaError_t e = launch_gemm_tc(pr, b->d_err, st, msg, sizeof(msg));
-      if (e != cudaSuccess)
-        return set_error(QTP_ERR_CUDA, "batched products (long reduction): %s %s", cudaGetErrorString(e), msg);
-    }
+    qtp_status r = enqueue_tc_products(b, ws, st);
+    if (r != QTP_OK) return r;
   }
   trace(b, 2, st, capturing);
   for (const FftRange& r : b->inv_ranges)
@@ -177,9 +215,188 @@ qtp_status encode_tmaps(qtp_batch_plan* b, char* ws, cudaStream_t st) {
   return QTP_OK;
 }
 
+// The products' tile space for a routing threshold: products with a long
+// reduction (split-BF16) or with min(m, s) >= route_min take the
+// single-product kernel (long_probs), the others get their grouped tiles.
+void layout_products(qtp_batch_plan* b, int route_min) {
+  const bool tc = b->precision != QTP_PREC_FP32;
+  const int fmt = b->fmt;
+  const int BMt = tc ? kGroupTcBM : kGroupSimtBM;
+  const int BNt = tc ? kGroupTcBN : kGroupSimtBN;
+  b->h_probs.clear();
+  b->prod_of_prob.clear();
+  b->long_probs.clear();
+  long long tiles = 0;
+  for (const auto& L : b->prods) {
+    if (tc && ((fmt == FMT_BF16X3 && L.n > kTcSingleMaxK) || std::min(L.m, L.s) >= route_min)) {
+      b->long_probs.push_back(L);
+      continue;
+    }
+    GroupProblem P;
+    memset(&P, 0, sizeof(P));
+    P.tile_begin = tiles;
+    P.sa_off = (long long)L.sa;
+    P.sb_off = (long long)L.sb;
+    P.out_off = (long long)L.sc;
+    P.M = L.m;
+    P.N = L.s;
+    P.K = L.n;
+    P.p = L.p;
+    // Tensor cores: 128-row tiles, MMA width the tile's columns rounded up to
+    // 16; computing C^T = B^T A^T instead when that pads less (the larger of
+    // m and s then fills the 128 rows).
+    P.bn = BNt;
+    P.trans = 0;
+    if (tc) {
+      auto padded = [](long long rows, long long cols) {
+        return (rows + 127) / 128 * 128 * ((cols + 15) / 16 * 16);
+      };
+      P.trans = padded(L.s, L.m) < padded(L.m, L.s) ? 1 : 0;
+    }
+    const int trows = P.trans ? L.s : L.m, tcols = P.trans ? L.m : L.s;
+    P.tiles_m = (trows + BMt - 1) / BMt;
+    P.tiles_n = (tcols + BNt - 1) / BNt;
+    P.lda = (int)spec_ld_of(fmt, L.n);
+    P.ldb = (int)spec_ld_of(fmt, L.s);
+    // tensor cores: a tile computes both output halves; FP32: one tile per half
+    tiles += (long long)P.tiles_m * P.tiles_n * (tc ? 1 : 2) * L.p;
+    b->h_probs.push_back(P);
+    b->prod_of_prob.push_back(L.idx);
+  }
+  b->n_probs = (int)b->h_probs.size();
+  b->total_tiles = tiles;
+  b->route_min = route_min;
+  b->tmaps_for_ws = nullptr;  // the tensor maps follow the grouped products
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+// Tensor maps live in d_tmaps: grouped product i's pair at 256 i.
+void set_tmap_slots(qtp_batch_plan* b) {
+  if (b->precision == QTP_PREC_FP32) return;
+  for (int i = 0; i < b->n_probs; ++i) {
+    b->h_probs[i].tmA = (char*)b->d_tmaps + (size_t)i * 256;
+    b->h_probs[i].tmB = (char*)b->d_tmaps + (size_t)i * 256 + 128;
+  }
+}
+
+// Products time (ms, mean of reps after one warm-up) of the current layout on
+// workspace ws, on the plan's stream.
+qtp_status time_tc_products(qtp_batch_plan* b, char* ws, int reps, float* ms) {
+  qtp_status r = encode_tmaps(b, ws, b->cap);
+  if (r != QTP_OK) return r;
+  BP_CUDA(cudaMemcpyAsync(b->d_probs, b->h_probs.data(), sizeof(GroupProblem) * std::max(b->n_probs, 1),
+                          cudaMemcpyHostToDevice, b->cap),
+          "upload products");
+  if ((r = enqueue_tc_products(b, ws, b->cap)) != QTP_OK) return r;
+  BP_CUDA(cudaEventRecord(b->ev[0], b->cap), "time products");
+  for (int i = 0; i < reps; ++i)
+    if ((r = enqueue_tc_products(b, ws, b->cap)) != QTP_OK) return r;
+  BP_CUDA(cudaEventRecord(b->ev[1], b->cap), "time products");
+  BP_CUDA(cudaEventSynchronize(b->ev[1]), "time products");
+  BP_CUDA(cudaEventElapsedTime(ms, b->ev[0], b->ev[1]), "time products");
+  *ms /= reps;
+  return QTP_OK;
+}
+
+// Autotuner of the routing threshold (QTP_BATCH_AUTOTUNE): the products of
+// this batch are timed, on a zeroed scratch workspace, for every candidate
+// threshold (grouped kernel only, then min(m, s) >= 192, 128, 96, 64, 48 to
+// the single-product kernel); the fastest is kept and cached per (device,
+// precision, shapes) for the process.
+std::mutex g_route_mu;
+std::map<std::string, int> g_route_cache;
+
+std::string route_key(const qtp_batch_plan* b) {
+  unsigned long long h = 1469598103934665603ull;  // FNV-1a over the shapes
+  for (const qtp_shape& q : b->shapes)
+    for (int v : {q.m, q.n, q.s, q.p}) {
+      h ^= (unsigned)v;
+      h *= 1099511628211ull;
+    }
+  cudaDeviceProp prop;
+  std::string dev = "dev";
+  if (cudaGetDeviceProperties(&prop, b->device) == cudaSuccess) dev = prop.name;
+  char buf[320];
+  snprintf(buf, sizeof(buf), "%s:%d:%d:%016llx", dev.c_str(), b->precision, b->count, h);
+  return buf;
+}
+
+qtp_status autotune_routing(qtp_batch_plan* b) {
+  std::lock_guard<std::mutex> lock(g_route_mu);
+  const std::string key = route_key(b);
+  auto hit = g_route_cache.find(key);
+  if (hit != g_route_cache.end()) {
+    layout_products(b, hit->second);
+    set_tmap_slots(b);
+    BP_CUDA(cudaMemcpy(b->d_probs, b->h_probs.data(), sizeof(GroupProblem) * std::max(b->n_probs, 1),
+                       cudaMemcpyHostToDevice),
+            "upload products");
+    return QTP_OK;
+  }
+  const int cands[] = {0x7fffffff, 192, 128, 96, 64, 48};
+  char* ws = nullptr;
+  cudaError_t e = cudaMalloc(&ws, std::max(b->ws_bytes, (size_t)256));
+  if (e == cudaSuccess) e = cudaMemset(ws, 0, b->ws_bytes);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    if (!b->ev[i]) e = cudaEventCreate(&b->ev[i]);
+  if (e != cudaSuccess) {
+    cudaFree(ws);
+    return set_error(QTP_ERR_CUDA, "batch autotune scratch: %s", cudaGetErrorString(e));
+  }
+  int best = cands[0];
+  float best_ms = 1e30f;
+  qtp_status r = QTP_OK;
+  b->tune_n = 0;
+  for (int c : cands) {
+    layout_products(b, c);
+    set_tmap_slots(b);
+    float ms = 0.f;
+    r = time_tc_products(b, ws, 2, &ms);
+    if (r != QTP_OK) break;
+    b->tune_ms[b->tune_n++] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaStreamSynchronize(b->cap);
+  cudaFree(ws);
+  if (!b->tracing)  // the events were only borrowed for the timing
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(b->ev[i]);
+      b->ev[i] = nullptr;
+    }
+  if (r != QTP_OK) return r;
+  int v = 0;
+  BP_CUDA(cudaMemcpy(&v, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+  if (v != 0) {
+    cudaMemset(b->d_err, 0, sizeof(int));
+    return set_error(QTP_ERR_TIMEOUT, "batch autotune: a device-side wait gave up (code %d)", v);
+  }
+  layout_products(b, best);
+  set_tmap_slots(b);
+  BP_CUDA(cudaMemcpy(b->d_probs, b->h_probs.data(), sizeof(GroupProblem) * std::max(b->n_probs, 1),
+                     cudaMemcpyHostToDevice),
+          "upload products");
+  g_route_cache[key] = best;
+  return QTP_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+qtp_status qtp_batch_plan_route(const qtp_batch_plan* b, int* route_min, float* tuned_ms, int* tuned_count) {
+  if (!b) return set_error(QTP_ERR_INVALID_ARG, "plan is NULL");
+  if (route_min) *route_min = b->route_min;
+  if (tuned_count) *tuned_count = b->tune_n;
+  if (tuned_ms)
+    for (int i = 0; i < b->tune_n; ++i) tuned_ms[i] = b->tune_ms[i];
+  return QTP_OK;
+}
 
 qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, int count, int precision,
                                  unsigned flags) {
@@ -190,7 +407,7 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   if (count > (1 << 20)) return set_error(QTP_ERR_INVALID_ARG, "at most 2^20 products per batch");
   if (precision != QTP_PREC_FP32 && precision != QTP_PREC_BF16X3 && precision != QTP_PREC_BF16)
     return set_error(QTP_ERR_INVALID_ARG, "unknown precision %d", precision);
-  if (flags & ~QTP_BATCH_NO_GRAPH) return set_error(QTP_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(QTP_BATCH_NO_GRAPH | QTP_BATCH_AUTOTUNE)) return set_error(QTP_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
   const long long lim = 1LL << 31;
   for (int i = 0; i < count; ++i) {
     const qtp_shape& q = shapes[i];
@@ -213,8 +430,6 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   b->shapes.assign(shapes, shapes + count);
   const int fmt = b->fmt;
   const bool tc = precision != QTP_PREC_FP32;
-  const int BMt = tc ? kGroupTcBM : kGroupSimtBM;
-  const int BNt = tc ? kGroupTcBN : kGroupSimtBN;
 
   // bucket by p, then by work (largest first)
   std::vector<int> order(count);
@@ -238,7 +453,7 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   // workspace layout, FFT jobs, product tiles
   std::vector<FftGroupJob> fwd, inv;
   size_t off = 0;
-  long long fb = 0, ib = 0, tiles = 0;
+  long long fb = 0, ib = 0;
   for (int idx : order) {
     const qtp_shape& q = shapes[idx];
     const int Tf = fft_tubes_per_block(q.p, false), Ti = fft_tubes_per_block(q.p, true);
@@ -271,41 +486,11 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
     fwd.push_back(job(0, q.m, q.n, sa, fb));
     fwd.push_back(job(1, q.n, q.s, sb, fb));
     inv.push_back(job(2, q.m, q.s, sc, ib));
-    if (tc && fmt == FMT_BF16X3 && q.n > kTcSingleMaxK) {
-      b->long_probs.push_back({q.m, q.n, q.s, q.p, sa, sb, sc});
-      continue;
-    }
-    GroupProblem P;
-    memset(&P, 0, sizeof(P));
-    P.tile_begin = tiles;
-    P.sa_off = (long long)sa;
-    P.sb_off = (long long)sb;
-    P.out_off = (long long)sc;
-    P.M = q.m;
-    P.N = q.s;
-    P.K = q.n;
-    P.p = q.p;
-    // Tensor cores: 128-row tiles, MMA width the tile's columns rounded up to
-    // 16; computing C^T = B^T A^T instead when that pads less (the larger of
-    // m and s then fills the 128 rows).
-    P.bn = BNt;
-    P.trans = 0;
-    if (tc) {
-      auto padded = [](long long rows, long long cols) {
-        return (rows + 127) / 128 * 128 * ((cols + 15) / 16 * 16);
-      };
-      P.trans = padded(q.s, q.m) < padded(q.m, q.s) ? 1 : 0;
-    }
-    const int trows = P.trans ? q.s : q.m, tcols = P.trans ? q.m : q.s;
-    P.tiles_m = (trows + BMt - 1) / BMt;
-    P.tiles_n = (tcols + BNt - 1) / BNt;
-    P.lda = (int)spec_ld_of(fmt, q.n);
-    P.ldb = (int)spec_ld_of(fmt, q.s);
-    // tensor cores: a tile computes both output halves; FP32: one tile per half
-    tiles += (long long)P.tiles_m * P.tiles_n * (tc ? 1 : 2) * q.p;
-    b->h_probs.push_back(P);
-    b->prod_of_prob.push_back(idx);
+    b->prods.push_back({idx, q.m, q.n, q.s, q.p, sa, sb, sc});
   }
+  const char* route_env = getenv("QTP_BATCH_ROUTE_MIN");
+  layout_products(b, route_env ? atoi(route_env) : 0x7fffffff);
+  const long long tiles = b->total_tiles;
   if (fb > 0x7fffffffLL || ib > 0x7fffffffLL || (!tc && tiles > 0x7fffffffLL)) {
     free_plan(b);
     return set_error(QTP_ERR_UNSUPPORTED, "batch too large for one grouped launch");
@@ -313,10 +498,8 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   b->ws_bytes = off;
   b->n_fwd = (int)fwd.size();
   b->n_inv = (int)inv.size();
-  b->n_probs = (int)b->h_probs.size();
   b->fwd_blocks = fb;
   b->inv_blocks = ib;
-  b->total_tiles = tiles;
   // launch ranges: jobs are ordered by p, so each p's CTAs are contiguous
   auto ranges = [](const std::vector<FftGroupJob>& jobs, long long total, bool inv) {
     std::vector<FftRange> r;
@@ -337,8 +520,8 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tw, sizeof(float2) * tw_total);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_fwd, sizeof(FftGroupJob) * fwd.size());
   if (e == cudaSuccess) e = cudaMalloc(&b->d_inv, sizeof(FftGroupJob) * inv.size());
-  // (every table at least one entry: a batch of long-reduction products only has no grouped tiles)
-  const size_t nprob_alloc = (size_t)std::max(b->n_probs, 1);
+  // product tables sized for every product (the routing may change which are grouped)
+  const size_t nprob_alloc = (size_t)count;
   if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, sizeof(GroupProblem) * nprob_alloc);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(float2*) * 3 * count);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
@@ -352,15 +535,16 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int i = 0; i < qtp_batch_plan::kAux && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->aux[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     free_plan(b);
     return set_error(QTP_ERR_CUDA, "batch plan allocation: %s", cudaGetErrorString(e));
   }
-  if (tc)  // tensor maps live in d_tmaps: product i's pair at 256 i
-    for (int i = 0; i < b->n_probs; ++i) {
-      b->h_probs[i].tmA = (char*)b->d_tmaps + (size_t)i * 256;
-      b->h_probs[i].tmB = (char*)b->d_tmaps + (size_t)i * 256 + 128;
-    }
+  set_tmap_slots(b);
   for (auto& kv : tw_off) {
     e = launch_twiddles(b->d_tw + kv.second, kv.first, 0);
     if (e != cudaSuccess) break;
@@ -391,12 +575,19 @@ qtp_status qtp_batch_plan_create(qtp_batch_plan** out, const qtp_shape* shapes, 
     e = cudaMemcpy(b->d_prob_tile, prob_tile.data(), sizeof(int) * prob_tile.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_fwd, fwd.data(), sizeof(FftGroupJob) * fwd.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_inv, inv.data(), sizeof(FftGroupJob) * inv.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && b->n_probs > 0)
     e = cudaMemcpy(b->d_probs, b->h_probs.data(), sizeof(GroupProblem) * b->n_probs, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_plan(b);
     return set_error(QTP_ERR_CUDA, "batch plan set-up: %s", cudaGetErrorString(e));
+  }
+  if (tc && (flags & QTP_BATCH_AUTOTUNE) && !route_env) {
+    qtp_status r = autotune_routing(b);
+    if (r != QTP_OK) {
+      free_plan(b);
+      return r;
+    }
   }
   *out = b;
   return QTP_OK;

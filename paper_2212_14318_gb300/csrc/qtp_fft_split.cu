@@ -22,11 +22,28 @@
 // (twice the one-kernel transform's bytes), all in long coalesced runs.  The
 // sub-DFTs are the Stockham stages of the one-kernel transforms, reading the
 // length-p twiddle table with stride N2 (w_N1^e = w_p^(e N2)) or N1.
+//
+// Compile-time form ("long" transforms, fft_long_*): when p = N1 N2 with N2 a
+// length that has a tuned two-pass transform (64, 100, 128, 256) and N1 <= 32,
+// the N1-point DFTs run in registers and the N2-point ones are that two-pass
+// transform (qtp_fft_twopass.cuh) with its frequencies remapped:
+//   forward pass 1: thread (tube, n2 or n2 pair) loads x[N2 n1 + n2] for all
+//                   n1 (16-byte loads, coalesced across n2), DFT-N1 in
+//                   registers, twiddle w_p^(n2 k1), stores Z[k1][tube][n2];
+//   forward pass 2: for each k1, the two-pass N2 transform of the Z rows
+//                   (tubes of length N2), storing frequency k1 + N1 k2;
+//   inverse pass 1: for each k1, the inverse two-pass N2 transform gathering
+//                   frequencies k1 + N1 k2, its output sample n2 multiplied by
+//                   w_p^(-k1 n2), stored Z[k1][tube][n2];
+//   inverse pass 2: thread (tube, n2 pair) loads Z[k1][tube][n2] for all k1,
+//                   inverse DFT-N1, stores x[N2 n1 + n2] / N1.
+// The N2 table w_N2^e sits after the length-p table (plan twiddles p + N2).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdlib.h>
 
 #include "qtp_fft_common.cuh"
+#include "qtp_fft_twopass.cuh"
 #include "qtp_internal.h"
 
 namespace qtp {
@@ -304,7 +321,282 @@ cudaError_t launch_fwd2(const FftFwdJob* jobs, int njobs, const SplitArgs& a, co
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------- long form
+
+constexpr int kLongThreads = 256;
+constexpr int kLongN2[] = {256, 128, 100, 64};
+
+// Register pass of the forward transform (PAIR: two neighbouring n2 per
+// thread, 16-byte accesses).  Items over [job 0 tubes x N2 / W][job 1 ...].
+template <int N1, bool PAIR>
+__global__ void __launch_bounds__(kLongThreads) fft_long_fwd1(const float2* __restrict__ x0,
+                                                              const float2* __restrict__ x1, long long items0,
+                                                              long long items, long long nt0, long long nt1, int n2,
+                                                              int p, const float2* __restrict__ tw, float2* z0,
+                                                              float2* z1) {
+  constexpr int W = PAIR ? 2 : 1;
+  const long long it = (long long)blockIdx.x * kLongThreads + threadIdx.x;
+  if (it >= items) return;
+  const bool second = it >= items0;
+  const long long li = second ? it - items0 : it;
+  const float2* __restrict__ x = second ? x1 : x0;
+  float2* z = second ? z1 : z0;
+  const long long nt = second ? nt1 : nt0;
+  const int per = n2 / W;
+  const long long g = li / per;
+  const int m2 = (int)(li - g * per) * W;
+  const float2* src = x + g * p + m2;
+  float2 a[N1], c[N1];
+#pragma unroll
+  for (int k = 0; k < N1; ++k) {
+    if (PAIR) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src + (long long)k * n2));
+      a[k] = make_float2(v.x, v.y);
+      c[k] = make_float2(v.z, v.w);
+    } else {
+      a[k] = __ldg(src + (long long)k * n2);
+    }
+  }
+  Dft<N1, false>::run(a);
+  if (PAIR) Dft<N1, false>::run(c);
+  float2* dst = z + g * n2 + m2;
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    float2 u = a[k1];
+    if (k1 > 0 && m2 > 0) u = cmul(u, twid<false>(tw, m2 * k1));
+    float2* o = dst + (long long)k1 * nt * n2;
+    if (PAIR) {
+      float2 w = c[k1];
+      if (k1 > 0) w = cmul(w, twid<false>(tw, (m2 + 1) * k1));
+      *reinterpret_cast<float4*>(o) = make_float4(u.x, u.y, w.x, w.y);
+    } else {
+      *o = u;
+    }
+  }
+}
+
+// Register pass of the inverse transform: x[N2 n1 + n2] = 1/N1 sum_k1 Z[k1][g][n2] w_N1^(-k1 n1).
+template <int N1, bool PAIR>
+__global__ void __launch_bounds__(kLongThreads) fft_long_inv2(const float2* __restrict__ z0,
+                                                              const float2* __restrict__ z1, long long items0,
+                                                              long long items, long long nt0, long long nt1, int n2,
+                                                              int p, float2* x0, float2* x1) {
+  constexpr int W = PAIR ? 2 : 1;
+  const long long it = (long long)blockIdx.x * kLongThreads + threadIdx.x;
+  if (it >= items) return;
+  const bool second = it >= items0;
+  const long long li = second ? it - items0 : it;
+  const float2* __restrict__ z = second ? z1 : z0;
+  float2* x = second ? x1 : x0;
+  const long long nt = second ? nt1 : nt0;
+  const int per = n2 / W;
+  const long long g = li / per;
+  const int m2 = (int)(li - g * per) * W;
+  const float2* src = z + g * n2 + m2;
+  float2 a[N1], c[N1];
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    if (PAIR) {
+      const float4 v = *reinterpret_cast<const float4*>(src + (long long)k1 * nt * n2);
+      a[k1] = make_float2(v.x, v.y);
+      c[k1] = make_float2(v.z, v.w);
+    } else {
+      a[k1] = src[(long long)k1 * nt * n2];
+    }
+  }
+  Dft<N1, true>::run(a);
+  if (PAIR) Dft<N1, true>::run(c);
+  const float sc = 1.0f / (float)N1;
+  float2* dst = x + g * p + m2;
+#pragma unroll
+  for (int n1 = 0; n1 < N1; ++n1) {
+    float2* o = dst + (long long)n1 * n2;
+    if (PAIR) *reinterpret_cast<float4*>(o) = make_float4(a[n1].x * sc, a[n1].y * sc, c[n1].x * sc, c[n1].y * sc);
+    else *o = make_float2(a[n1].x * sc, a[n1].y * sc);
+  }
+}
+
+// Two-pass pass of the forward transform for every k1: blocks [0, n1 nbk0)
+// belong to the first tensor (k1 = b / nbk0), the rest to the second.
+template <int N2, int FMT>
+__global__ void __launch_bounds__(kThreads, min_blocks<N2, false>()) fft_long_fwd2(FftFwdJob j0, FftFwdJob j1,
+                                                                               long long nbk0, long long nbk1, int n1,
+                                                                               int p, const float2* __restrict__ tw_n2,
+                                                                               const float2* z0, const float2* z1) {
+  extern __shared__ float4 smem_f4[];
+  long long b = blockIdx.x;
+  const bool second = b >= (long long)n1 * nbk0;
+  if (second) b -= (long long)n1 * nbk0;
+  const long long nbk = second ? nbk1 : nbk0;
+  const int k1 = (int)(b / nbk);
+  FftFwdJob job = second ? j1 : j0;
+  job.in = (second ? z1 : z0) + (long long)k1 * ntubes_of(job.rows, job.cols) * N2;
+  const LongMap L{n1, k1, p, nullptr};
+  fs_fwd_body<N2, FMT, true>(job, b - k1 * nbk, tw_n2, reinterpret_cast<float2*>(smem_f4), L);
+}
+
+template <int N2>
+__global__ void __launch_bounds__(kThreads, min_blocks<N2, true>()) fft_long_inv1(FftInvJob j0, FftInvJob j1,
+                                                                              long long nbk0, long long nbk1, int n1,
+                                                                              int p, const float2* __restrict__ tw_n2,
+                                                                              const float2* __restrict__ tw_p,
+                                                                              float2* z0, float2* z1) {
+  extern __shared__ float4 smem_f4[];
+  long long b = blockIdx.x;
+  const bool second = b >= (long long)n1 * nbk0;
+  if (second) b -= (long long)n1 * nbk0;
+  const long long nbk = second ? nbk1 : nbk0;
+  const int k1 = (int)(b / nbk);
+  FftInvJob job = second ? j1 : j0;
+  job.out = (second ? z1 : z0) + (long long)k1 * ntubes_of(job.rows, job.cols) * N2;
+  const LongMap L{n1, k1, p, tw_p};
+  fs_inv_body<N2, true>(job, b - k1 * nbk, tw_n2, reinterpret_cast<float2*>(smem_f4), L);
+}
+
+template <int N2, bool INV>
+constexpr size_t long_smem() {
+  return (size_t)N2 * fs_pitch(N2, INV) * sizeof(float2);
+}
+
+// Runs of the two-pass N2 transform over one k1's rows: the padded run space
+// of the bf16 forward (odd rows get a phantom tube) or the plain one.
+long long long_runs(int rows, int cols, int n2, bool inv, int fmt) {
+  const int cp = (!inv && fmt != FMT_C32 && (cols & 1)) ? cols + 1 : cols;
+  return div_up(2LL * rows * cp, tubes_for(n2, inv));
+}
+
+template <int N1>
+cudaError_t launch_reg(bool inv, const float2* a0, const float2* a1, long long nt0, long long nt1, int n2, int p,
+                       const float2* tw, float2* b0, float2* b1, cudaStream_t st) {
+  constexpr bool PAIR = N1 <= 16;  // two n2 per thread while the registers allow
+  const long long items0 = nt0 * n2 / (PAIR ? 2 : 1), items = items0 + nt1 * n2 / (PAIR ? 2 : 1);
+  if (items == 0) return cudaSuccess;
+  const long long blocks = div_up(items, kLongThreads);
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (!inv)
+    fft_long_fwd1<N1, PAIR><<<(unsigned)blocks, kLongThreads, 0, st>>>(a0, a1, items0, items, nt0, nt1, n2, p, tw, b0,
+                                                                      b1);
+  else
+    fft_long_inv2<N1, PAIR><<<(unsigned)blocks, kLongThreads, 0, st>>>(a0, a1, items0, items, nt0, nt1, n2, p, b0, b1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reg_n1(int n1, bool inv, const float2* a0, const float2* a1, long long nt0, long long nt1, int n2,
+                          int p, const float2* tw, float2* b0, float2* b1, cudaStream_t st) {
+#define QTP_LONG_N1(N) \
+  case N: return launch_reg<N>(inv, a0, a1, nt0, nt1, n2, p, tw, b0, b1, st);
+  switch (n1) {
+    QTP_LONG_N1(2) QTP_LONG_N1(3) QTP_LONG_N1(4) QTP_LONG_N1(5) QTP_LONG_N1(6) QTP_LONG_N1(8) QTP_LONG_N1(10)
+    QTP_LONG_N1(12) QTP_LONG_N1(16) QTP_LONG_N1(20) QTP_LONG_N1(24) QTP_LONG_N1(25) QTP_LONG_N1(30) QTP_LONG_N1(32)
+    default: return cudaErrorInvalidValue;
+  }
+#undef QTP_LONG_N1
+}
+
+template <int N2, int FMT>
+cudaError_t launch_fwd2_long(const FftFwdJob* jobs, int njobs, int n1, int p, const float2* tw_n2, const float2* z0,
+                             const float2* z1, cudaStream_t st) {
+  constexpr size_t smem = long_smem<N2, false>();
+  static std::atomic<unsigned long long> attr_set{0};
+  cudaError_t e = ensure_smem_attr(attr_set, fft_long_fwd2<N2, FMT>, smem);
+  if (e != cudaSuccess) return e;
+  const long long nbk0 = long_runs(jobs[0].rows, jobs[0].cols, N2, false, FMT);
+  const long long nbk1 = njobs > 1 ? long_runs(jobs[1].rows, jobs[1].cols, N2, false, FMT) : 0;
+  const long long blocks = (long long)n1 * (nbk0 + nbk1);
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  fft_long_fwd2<N2, FMT><<<(unsigned)blocks, kThreads, smem, st>>>(jobs[0], njobs > 1 ? jobs[1] : jobs[0], nbk0, nbk1,
+                                                                    n1, p, tw_n2, z0, z1);
+  return cudaGetLastError();
+}
+
+template <int N2>
+cudaError_t launch_fwd2_fmt(const FftFwdJob* jobs, int njobs, int fmt, int n1, int p, const float2* tw_n2,
+                            const float2* z0, const float2* z1, cudaStream_t st) {
+  switch (fmt) {
+    case FMT_C32: return launch_fwd2_long<N2, FMT_C32>(jobs, njobs, n1, p, tw_n2, z0, z1, st);
+    case FMT_BF16X3: return launch_fwd2_long<N2, FMT_BF16X3>(jobs, njobs, n1, p, tw_n2, z0, z1, st);
+    case FMT_BF16: return launch_fwd2_long<N2, FMT_BF16>(jobs, njobs, n1, p, tw_n2, z0, z1, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N2>
+cudaError_t launch_inv1_long(const FftInvJob* jobs, int njobs, int n1, int p, const float2* tw_n2, const float2* tw_p,
+                             float2* z0, float2* z1, cudaStream_t st) {
+  constexpr size_t smem = long_smem<N2, true>();
+  static std::atomic<unsigned long long> attr_set{0};
+  cudaError_t e = ensure_smem_attr(attr_set, fft_long_inv1<N2>, smem);
+  if (e != cudaSuccess) return e;
+  const long long nbk0 = long_runs(jobs[0].rows, jobs[0].cols, N2, true, FMT_C32);
+  const long long nbk1 = njobs > 1 ? long_runs(jobs[1].rows, jobs[1].cols, N2, true, FMT_C32) : 0;
+  const long long blocks = (long long)n1 * (nbk0 + nbk1);
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  fft_long_inv1<N2><<<(unsigned)blocks, kThreads, smem, st>>>(jobs[0], njobs > 1 ? jobs[1] : jobs[0], nbk0, nbk1, n1,
+                                                              p, tw_n2, tw_p, z0, z1);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool fft_long_dims(int p, int* n1, int* n2) {
+  static const int n1s[] = {2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 25, 30, 32};
+  for (int N2 : kLongN2) {
+    if (p % N2) continue;
+    const int N1 = p / N2;
+    for (int c : n1s)
+      if (c == N1) {
+        if (n1) *n1 = N1;
+        if (n2) *n2 = N2;
+        return true;
+      }
+  }
+  return false;
+}
+
+cudaError_t launch_fft_fwd_long(const FftFwdJob* jobs, int njobs, int fmt, int p, const float2* tw, float2* scratch,
+                                cudaStream_t st) {
+  int n1 = 0, n2 = 0;
+  if (njobs < 1 || njobs > 2 || !fft_long_dims(p, &n1, &n2)) return cudaErrorInvalidValue;
+  const long long nt0 = ntubes_of(jobs[0].rows, jobs[0].cols);
+  const long long nt1 = njobs > 1 ? ntubes_of(jobs[1].rows, jobs[1].cols) : 0;
+  float2* z0 = scratch;
+  float2* z1 = scratch + nt0 * p;
+  cudaError_t e = launch_reg_n1(n1, false, jobs[0].in, njobs > 1 ? jobs[1].in : jobs[0].in, nt0, nt1, n2, p, tw, z0,
+                                z1, st);
+  if (e != cudaSuccess) return e;
+  const float2* tw_n2 = tw + p;
+  switch (n2) {
+    case 256: return launch_fwd2_fmt<256>(jobs, njobs, fmt, n1, p, tw_n2, z0, z1, st);
+    case 128: return launch_fwd2_fmt<128>(jobs, njobs, fmt, n1, p, tw_n2, z0, z1, st);
+    case 100: return launch_fwd2_fmt<100>(jobs, njobs, fmt, n1, p, tw_n2, z0, z1, st);
+    case 64: return launch_fwd2_fmt<64>(jobs, njobs, fmt, n1, p, tw_n2, z0, z1, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fft_inv_long(const FftInvJob* jobs, int njobs, int p, const float2* tw, float2* scratch,
+                                cudaStream_t st) {
+  int n1 = 0, n2 = 0;
+  if (njobs < 1 || njobs > 2 || !fft_long_dims(p, &n1, &n2)) return cudaErrorInvalidValue;
+  const long long nt0 = ntubes_of(jobs[0].rows, jobs[0].cols);
+  const long long nt1 = njobs > 1 ? ntubes_of(jobs[1].rows, jobs[1].cols) : 0;
+  float2* z0 = scratch;
+  float2* z1 = scratch + nt0 * p;
+  const float2* tw_n2 = tw + p;
+  cudaError_t e;
+  switch (n2) {
+    case 256: e = launch_inv1_long<256>(jobs, njobs, n1, p, tw_n2, tw, z0, z1, st); break;
+    case 128: e = launch_inv1_long<128>(jobs, njobs, n1, p, tw_n2, tw, z0, z1, st); break;
+    case 100: e = launch_inv1_long<100>(jobs, njobs, n1, p, tw_n2, tw, z0, z1, st); break;
+    case 64: e = launch_inv1_long<64>(jobs, njobs, n1, p, tw_n2, tw, z0, z1, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  return launch_reg_n1(n1, true, z0, z1, nt0, nt1, n2, p, nullptr, jobs[0].out, njobs > 1 ? jobs[1].out : jobs[0].out,
+                       st);
+}
 
 bool fft_split_dims(int p, int* n1, int* n2) {
   // the largest divisor N2 <= sqrt(p), and N1 = p / N2 >= N2
@@ -327,6 +619,16 @@ bool fft_split_eligible(int p, bool inv) {
   // 1.14 against 2.65 ms), not at p = 1000 (0.30 against 0.23 ms); the
   // inverse two-pass form is slower at both (0.65 against 0.51 ms at 4096).
   return !inv && p >= 2048 && fft_fixed_tubes(p, false) == 0;
+}
+
+int fft_form(int p, bool inv) {
+  if (const char* env = getenv("QTP_FFT_SPLIT")) {
+    if (p <= 128 || env[0] == '0') return FFT_ONE;
+    if (env[0] == '2' && fft_long_dims(p, nullptr, nullptr)) return FFT_LONG;
+    if (env[0] == '1' || env[0] == '2') return fft_split_dims(p, nullptr, nullptr) ? FFT_SPLIT : FFT_ONE;
+  }
+  if (p > 128 && fft_fixed_tubes(p, false) == 0 && fft_long_dims(p, nullptr, nullptr)) return FFT_LONG;
+  return fft_split_eligible(p, inv) ? FFT_SPLIT : FFT_ONE;
 }
 
 size_t fft_split_scratch_bytes(int p, long long rows, long long cols) {

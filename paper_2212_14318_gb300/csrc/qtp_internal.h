@@ -141,6 +141,23 @@ cudaError_t launch_fft_inv_fixed(const FftInvJob* jobs, int njobs, int p, const 
 // first).
 bool fft_split_dims(int p, int* n1, int* n2);
 bool fft_split_eligible(int p, bool inv);
+// Compile-time long form: p = N1 N2 with N2 in {256, 128, 100, 64} (a tuned
+// two-pass length) and N1 <= 32 (registers).  Its twiddles are the length-p
+// table followed by the length-N2 one (fft_long_extra_twiddles(p) = N2
+// entries after the first p).
+bool fft_long_dims(int p, int* n1, int* n2);
+cudaError_t launch_fft_fwd_long(const FftFwdJob* jobs, int njobs, int fmt, int p, const float2* tw, float2* scratch,
+                                cudaStream_t st);
+cudaError_t launch_fft_inv_long(const FftInvJob* jobs, int njobs, int p, const float2* tw, float2* scratch,
+                                cudaStream_t st);
+// Transform form of a tube length, per direction: one kernel, the two-pass
+// form with runtime-radix sub-DFTs, or the compile-time long form.  Default:
+// the long form where fft_long_dims splits p (above 128, no one-kernel
+// compile-time transform), else the runtime two-pass forward from p = 2048,
+// else one kernel.  Environment QTP_FFT_SPLIT: 0 one kernel, 1 runtime
+// two-pass, 2 long form (where p splits), for every length above 128.
+enum FftForm : int { FFT_ONE = 0, FFT_SPLIT = 1, FFT_LONG = 2 };
+int fft_form(int p, bool inv);
 size_t fft_split_scratch_bytes(int p, long long rows, long long cols);
 cudaError_t launch_fft_fwd_split(const FftFwdJob* jobs, int njobs, int fmt, int p, const float2* tw, float2* scratch,
                                  cudaStream_t st);
@@ -158,10 +175,11 @@ cudaError_t launch_fft_inv(const FftInvJob* jobs, int njobs, const RadixPlan& rp
 // ([plane][f][m][k]), V ([plane][f][n][k]) and S ([plane][f][k][k], zeroed by
 // the caller) and sigma ([f][k]); k = min(m, n) <= 64.  scratch: global
 // buffers of tsvd_scratch_bytes(m, n, p) bytes when one pair's matrices do not
-// fit in shared memory (0 bytes otherwise).
+// fit in shared memory (0 bytes otherwise); *status is set to 1 (never
+// cleared) when a pair's Jacobi sweeps stop at their limit still rotating.
 size_t tsvd_scratch_bytes(int m, int n, int p);
 cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, float2* Vh, float2* Sh,
-                              float* sigma, float2* scratch, cudaStream_t st);
+                              float* sigma, float2* scratch, int* status, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // Per-frequency complex products (Alg. 5.1 Step 2), generic operand views.
@@ -298,8 +316,8 @@ struct qtp_plan {
   float2* d_tw;      // w^e = exp(-2 pi i e / p), e in [0, p)
   int* d_err;        // device error word written by bounded waits
   qtp::RadixPlan rp;
-  int fft_split_fwd;  // forward / inverse tube transforms in two passes through a
-  int fft_split_inv;  // workspace intermediate (long p)
+  int fft_split_fwd;  // FftForm of the forward / inverse tube transforms (two-pass
+  int fft_split_inv;  // forms go through a workspace intermediate)
   int tracing;
   cudaEvent_t ev[4];  // stage boundaries of the last traced call
   // streams and events of qtp_forward_host_many, created on its first call

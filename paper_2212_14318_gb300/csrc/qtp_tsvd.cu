@@ -306,6 +306,7 @@ struct TsvdArgs {
   int m, n, p, k;
   int R, C;          // rows and columns of the matrix the Jacobi sweeps work on
   int tall;          // 1: the sweeps work on M_f (m >= n); 0: on M_f^H
+  int* status;       // set to 1 when a phase's sweeps end at kTsvdMaxSweeps still rotating
 };
 
 // Round-robin schedule: pair t of round rr over C (even) columns; column 0
@@ -328,7 +329,8 @@ __device__ __forceinline__ void rr_pair(int C, int rr, int t, int& a, int& b) {
 // buffers alternate between two sets, so the one cluster barrier per round
 // orders both the hand-over and the reuse of a set two rounds later.  The
 // rotations and their order are those of the sweeps from memory.
-__device__ __forceinline__ void ring_sweeps(float2* X, float2* V, int R, int C, float tol, int nc, int rank,
+// Returns whether a sweep without rotations ended the loop (cluster-uniform).
+__device__ __forceinline__ bool ring_sweeps(float2* X, float2* V, int R, int C, float tol, int nc, int rank,
                                             int warp, int lane, int tid, int* rotations, float4* slots) {
   cg::cluster_group cl = cg::this_cluster();
   const int R2 = R >> 1, C2 = C >> 1, L = R2 + C2;
@@ -350,6 +352,7 @@ __device__ __forceinline__ void ring_sweeps(float2* X, float2* V, int R, int C, 
     return cl.map_shared_rank(local_slot(s, kind, u % kTsvdWarps), u / kTsvdWarps);
   };
   int set = 0;
+  bool converged = false;
   for (int sweep = 0; sweep < kTsvdMaxSweeps; ++sweep) {
     if (tid == 0) *rotations = 0;
     cl.sync();
@@ -397,7 +400,10 @@ __device__ __forceinline__ void ring_sweeps(float2* X, float2* V, int R, int C, 
     for (int j = 0; j < nc; ++j) total += *cl.map_shared_rank(rotations, j);
     const bool done = total == 0;
     cl.sync();
-    if (done) break;
+    if (done) {
+      converged = true;
+      break;
+    }
   }
   if (active) {
     rr_pair(C, 0, t, ca, cb);
@@ -407,6 +413,7 @@ __device__ __forceinline__ void ring_sweeps(float2* X, float2* V, int R, int C, 
     store_col<true>(vb, reinterpret_cast<float4*>(V + (long long)cb * C), C2, lane);
   }
   cl.sync();
+  return converged;
 }
 
 // G = false: one CTA per pair, buffers in dynamic shared memory.  G = true:
@@ -515,9 +522,12 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
     }
   }
   if constexpr (RING) {
-    ring_sweeps(X, V, R, C, tol, nc, rank, warp, lane, tid, &rotations, reinterpret_cast<float4*>(tsvd_smem));
+    if (!ring_sweeps(X, V, R, C, tol, nc, rank, warp, lane, tid, &rotations, reinterpret_cast<float4*>(tsvd_smem)) &&
+        rank == 0 && tid == 0)
+      atomicExch(a.status, 1);
     continue;
   }
+  bool converged = false;
   for (int sweep = 0; sweep < kTsvdMaxSweeps; ++sweep) {
     if (tid == 0) rotations = 0;
     pair_sync<G>();
@@ -580,8 +590,12 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
     }
     const bool done = total == 0;
     pair_sync<G>();
-    if (done) break;
+    if (done) {
+      converged = true;
+      break;
+    }
   }
+  if (!converged && rank == 0 && tid == 0) atomicExch(a.status, 1);
   }
   // the rest (sorting, completion, scatter) is the first CTA's alone; the
   // others leave after the last barrier, with no access to their shared
@@ -745,10 +759,11 @@ size_t tsvd_scratch_bytes(int m, int n, int p) {
 }
 
 cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, float2* Vh, float2* Sh,
-                              float* sigma, float2* scratch, cudaStream_t st) {
+                              float* sigma, float2* scratch, int* status, cudaStream_t st) {
   const int k = m < n ? m : n;
   if (2 * k > kTsvdMaxCols) return cudaErrorInvalidValue;
   TsvdArgs a;
+  a.status = status;
   a.H = H;
   a.Uh = Uh;
   a.Vh = Vh;

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(PKG, "_lib", "libqtp.so")
 
 QTP_OK = 0
 STATUS_NAMES = {0: "QTP_OK", 1: "QTP_ERR_INVALID_ARG", 2: "QTP_ERR_UNSUPPORTED", 3: "QTP_ERR_WORKSPACE",
-                4: "QTP_ERR_CUDA", 5: "QTP_ERR_TIMEOUT", 6: "QTP_ERR_INTERNAL"}
+                4: "QTP_ERR_CUDA", 5: "QTP_ERR_TIMEOUT", 6: "QTP_ERR_INTERNAL", 7: "QTP_ERR_NOT_CONVERGED"}
 PRECISIONS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
 PLAN_AUTOTUNE = 1
 
@@ -42,6 +42,7 @@ SIGNATURES = {
     "qtp_forward_saving": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qtp_backward_saved": (_i, [_vp, _vp, _vp, _sz, _vp, _vp, _vp, _sz, _vp]),
     "qtp_tsvd": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "qtp_tsvd_sync": (_i, [_i, _i, _i, _vp, _vp]),
     "qtp_forward_host_many": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _sz,
                                    _vp]),
     "qtp_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -56,6 +57,8 @@ SIGNATURES = {
     "qtp_batch_plan_set_tracing": (_i, [_vp, _i]),
     "qtp_batch_stage_times": (_i, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "qtp_batch_plan_sync": (_i, [_vp, _vp]),
+    "qtp_batch_plan_route": (_i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ctypes.c_int)]),
     "qtp_last_error": (ctypes.c_char_p, []),
     "qtp_version": (_i, []),
 }
@@ -126,10 +129,12 @@ def _check_host_tensor(t, shape, name):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
-def tsvd(A, workspace=None, stream=None):
+def tsvd(A, workspace=None, stream=None, check=False):
     """T-SVD A = U * S * V^H of a CUDA tensor A (2, m, n, p, 2) (qtp_tsvd):
     returns U (2, m, k, p, 2), S (2, k, k, p, 2), V (2, n, k, p, 2) and sigma
-    (p, k), k = min(m, n)."""
+    (p, k), k = min(m, n).  check: synchronise and raise QtpError
+    (QTP_ERR_NOT_CONVERGED) if a frequency pair's sweeps did not converge
+    (qtp_tsvd_sync)."""
     import torch
     if not isinstance(A, torch.Tensor) or A.dim() != 5 or A.shape[0] != 2 or A.shape[4] != 2:
         raise ValueError("A must have shape (2, m, n, p, 2)")
@@ -146,6 +151,8 @@ def tsvd(A, workspace=None, stream=None):
     ws = workspace if workspace is not None else torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=dev)
     _check(lib().qtp_tsvd(m, n, p, _ptr(A), _ptr(U), _ptr(S), _ptr(V), _ptr(sigma), _ptr(ws),
                           ws.numel() * ws.element_size(), _stream(stream)), "qtp_tsvd")
+    if check:
+        _check(lib().qtp_tsvd_sync(m, n, p, _ptr(ws), _stream(stream)), "qtp_tsvd_sync")
     return U, S, V, sigma
 
 
@@ -318,20 +325,22 @@ class Shape(ctypes.Structure):
 
 
 BATCH_NO_GRAPH = 1
+BATCH_AUTOTUNE = 2
 
 
 class BatchPlan:
     """A qtp_batch_plan: many independent products C_i = A_i * B_i of uneven shapes."""
 
-    def __init__(self, shapes, precision: str = "bf16x3", graph: bool = True):
+    def __init__(self, shapes, precision: str = "bf16x3", graph: bool = True, autotune: bool = False):
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {list(PRECISIONS)}")
         self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
         self.precision = precision
         arr = (Shape * len(self.shapes))(*[Shape(*sh) for sh in self.shapes])
         h = ctypes.c_void_p()
+        flags = (0 if graph else BATCH_NO_GRAPH) | (BATCH_AUTOTUNE if autotune else 0)
         _check(lib().qtp_batch_plan_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(self.shapes),
-                                           PRECISIONS[precision], 0 if graph else BATCH_NO_GRAPH),
+                                           PRECISIONS[precision], flags),
                "qtp_batch_plan_create")
         self._h = h
         self._ws = None
@@ -373,6 +382,14 @@ class BatchPlan:
                 self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=As[0].device)
             workspace = self._ws
         return BoundBatch(self, list(As), list(Bs), list(Cs), workspace)
+
+    def route(self):
+        """(route_min, tuned times in ms per candidate threshold) of qtp_batch_plan_route."""
+        r = ctypes.c_int()
+        n = ctypes.c_int()
+        ms = (ctypes.c_float * 8)()
+        _check(lib().qtp_batch_plan_route(self._h, ctypes.byref(r), ms, ctypes.byref(n)), "qtp_batch_plan_route")
+        return int(r.value), [float(ms[i]) for i in range(n.value)]
 
     def set_tracing(self, enable: bool = True):
         _check(lib().qtp_batch_plan_set_tracing(self._h, 1 if enable else 0), "qtp_batch_plan_set_tracing")

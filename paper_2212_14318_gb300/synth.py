@@ -19,7 +19,7 @@ motivation, Sec. 1, is mirrored by a pixel-like pure-quaternion A):
 * batch      4096 problems, m, n, s = round(exp(U(ln 16, ln 256))),
              p uniform over {8, 12, 16, 31, 32, 64, 100, 128}
 * diff       A 128x64x32, B 64x128x32, target T 128x128x32, N(0,1)
-* long1000, long4096  A, B 64x64x1000 / 64x64x4096 N(0,1): long tubes (long
+* long1000, long1024, long4096  A, B 64x64xp N(0,1): long tubes (long
              videos), the two-pass transforms
 
 Seeds: 0 for A, 1 for B, 2 for T, 3 for sampled output positions, 4 for the
@@ -37,6 +37,7 @@ WORKLOADS = {
     "precision": dict(m=1024, n=1024, s=1024, p=128, a_kind="normal"),
     "diff": dict(m=128, n=64, s=128, p=32, a_kind="normal"),
     "long1000": dict(m=64, n=64, s=64, p=1000, a_kind="normal"),
+    "long1024": dict(m=64, n=64, s=64, p=1024, a_kind="normal"),
     "long4096": dict(m=64, n=64, s=64, p=4096, a_kind="normal"),
 }
 

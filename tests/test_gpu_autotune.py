@@ -41,3 +41,28 @@ def test_autotuned_plan_is_accurate_and_respects_the_accuracy_rule(m, n, s, p, t
     if os.path.exists(cache):
         lines = cache.read_text().split("\n")
         assert any(f":{m}:{n}:{s}:{p}:1 " in ln for ln in lines)
+
+
+@pytest.mark.parametrize("m,n,s,p", [(6, 5, 7, 1024), (4, 6, 5, 1000)])
+def test_autotuned_transform_forms(m, n, s, p, tmp_path, monkeypatch):
+    """With p > 128 the autotuner also times the tube transform forms (one
+    kernel, runtime two-pass, compile-time two-pass) per direction; the plan
+    with its choice matches the oracle's FP64 Algorithm 5.1, forward and
+    backward."""
+    monkeypatch.setenv("QTP_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    from paper_2212_14318_gb300 import qtp
+    A = synth.quat_normal(m, n, p, 13)
+    B = synth.quat_normal(n, s, p, 14)
+    G = synth.quat_normal(m, s, p, 15)
+    for precision in ("bf16x3", "fp32"):
+        plan = qtp.Plan(m, n, s, p, precision, autotune=True)
+        fwd, bwd = plan.launch_count()
+        assert fwd in (3, 4, 5) and bwd in (5, 6, 7, 8), (fwd, bwd)
+        C = to_host(plan.forward(to_dev(A), to_dev(B)))
+        plan.sync()
+        Aq, Bq, Gq = planes_to_comp(A), planes_to_comp(B), planes_to_comp(G)
+        assert_close(C, Q.alg51(Aq, Bq), 1e-5, 1e-4, f"autotuned forms {precision} p={p}")
+        dA, dB = plan.backward(to_dev(G), to_dev(A), to_dev(B))
+        plan.sync()
+        assert_close(to_host(dA), Q.alg51(Gq, Q.conj_transpose(Bq)), 1e-5, 1e-4, f"autotuned forms dA {precision}")
+        assert_close(to_host(dB), Q.alg51(Q.conj_transpose(Aq), Gq), 1e-5, 1e-4, f"autotuned forms dB {precision}")

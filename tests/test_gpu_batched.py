@@ -151,3 +151,50 @@ def test_bound_batch_repeats_with_new_contents():
     bound.forward()
     plan.sync()
     _check_all(shapes, As2, Bs, bound.Cs, "bound, new contents")
+
+
+# products of the batch routing tests: narrow, wide (min(m, s) >= 64 / 128),
+# transposed, and one with a long reduction
+ROUTE_SHAPES = [(8, 8, 8, 16), (150, 40, 300, 4), (70, 33, 90, 12), (130, 64, 140, 8), (20, 30, 200, 8),
+                (64, 500, 72, 4), (16, 16, 16, 31), (96, 48, 96, 32)]
+
+
+@pytest.mark.parametrize("route_min", ["0", "64", "128"])
+def test_routed_products_match_oracle(route_min, monkeypatch):
+    """Products routed to the single-product kernel (all of them at 0; those
+    with min(m, s) >= 64 or 128), launched over the plan's auxiliary streams
+    inside the graph, against the oracle; a second replay repeats them."""
+    from paper_2212_14318_gb300 import qtp
+    monkeypatch.setenv("QTP_BATCH_ROUTE_MIN", route_min)
+    As = [synth.quat_normal(m, n, p, 610 + i) for i, (m, n, s, p) in enumerate(ROUTE_SHAPES)]
+    Bs = [synth.quat_normal(n, s, p, 620 + i) for i, (m, n, s, p) in enumerate(ROUTE_SHAPES)]
+    plan = qtp.BatchPlan(ROUTE_SHAPES, "bf16x3")
+    assert plan.route()[0] == int(route_min)
+    dA, dB = [to_dev(a) for a in As], [to_dev(b) for b in Bs]
+    Cs = plan.forward(dA, dB)
+    plan.sync()
+    _check_all(ROUTE_SHAPES, As, Bs, Cs, f"route_min={route_min}")
+    first = [to_host(c) for c in Cs]
+    plan.forward(dA, dB, Cs)
+    plan.sync()
+    for c, f in zip(Cs, first):
+        np.testing.assert_array_equal(to_host(c), f)
+
+
+def test_autotuned_batch_routing():
+    """QTP_BATCH_AUTOTUNE times the products for each candidate threshold and
+    keeps the fastest; the tuned plan matches the oracle and a second plan of
+    the same shapes reuses the choice."""
+    from paper_2212_14318_gb300 import qtp
+    shapes = ROUTE_SHAPES * 3
+    As = [synth.quat_normal(m, n, p, 630 + i) for i, (m, n, s, p) in enumerate(shapes)]
+    Bs = [synth.quat_normal(n, s, p, 660 + i) for i, (m, n, s, p) in enumerate(shapes)]
+    plan = qtp.BatchPlan(shapes, "bf16x3", autotune=True)
+    route_min, times = plan.route()
+    assert len(times) == 6 and all(t > 0 for t in times), times
+    assert route_min in (2**31 - 1, 192, 128, 96, 64, 48)
+    assert times[[2**31 - 1, 192, 128, 96, 64, 48].index(route_min)] == min(times)
+    Cs = plan.forward([to_dev(a) for a in As], [to_dev(b) for b in Bs])
+    plan.sync()
+    _check_all(shapes, As, Bs, Cs, "autotuned routing")
+    assert qtp.BatchPlan(shapes, "bf16x3", autotune=True).route()[0] == route_min

@@ -306,12 +306,14 @@ def test_backward_from_saved_spectra(precision, shape):
     np.testing.assert_array_equal(to_host(only_b[1]), to_host(gB_ref))
 
 
-# Both transform forms at long tube lengths: the two-pass (four-step) transform
-# through the workspace intermediate (QTP_FFT_SPLIT=1 forces it also for the
-# lengths that have a one-kernel transform) and the one-kernel transforms
-# (QTP_FFT_SPLIT=0), each against the oracle's FP64 Algorithm 5.1 and sampled
-# definition entries; the plan fixes its form at creation.
-@pytest.mark.parametrize("split", ["1", "0"])
+# Every transform form at long tube lengths: the compile-time two-pass form
+# (QTP_FFT_SPLIT=2: register DFT-N1 and a tuned two-pass N2 transform; lengths
+# it cannot split take the runtime form), the runtime-radix two-pass
+# (four-step) form (=1), both through the workspace intermediate and forced
+# also for the lengths that have a one-kernel transform, and the one-kernel
+# transforms (=0); each against the oracle's FP64 Algorithm 5.1 and sampled
+# definition entries.  The plan fixes its form at creation.
+@pytest.mark.parametrize("split", ["2", "1", "0"])
 @pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("m,n,s,p", [(5, 6, 7, 256), (3, 4, 5, 1000), (9, 7, 40, 1024), (2, 3, 2, 4096),
                                      (7, 5, 6, 243)])
@@ -324,7 +326,7 @@ def test_forward_large_p_both_transforms(split, precision, m, n, s, p):
         plan = qtp.Plan(m, n, s, p, precision)
     finally:
         del os.environ["QTP_FFT_SPLIT"]
-    assert plan.launch_count()[0] == (5 if split == "1" else 3)
+    assert plan.launch_count()[0] == (3 if split == "0" else 5)
     C = to_host(plan.forward(to_dev(A), to_dev(B)))
     plan.sync()
     Aq, Bq = planes_to_comp(A), planes_to_comp(B)
@@ -337,13 +339,15 @@ def test_forward_large_p_both_transforms(split, precision, m, n, s, p):
 
 @pytest.mark.parametrize("split", ["1", None])
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("m,n,s,p", [(5, 6, 7, 1000), (4, 3, 5, 4096)])
+@pytest.mark.parametrize("m,n,s,p", [(5, 6, 7, 1000), (4, 3, 5, 4096), (3, 4, 5, 2187)])
 def test_backward_large_p(split, precision, m, n, s, p):
-    """dA = dC * B^H and dB = A^H * dC at long tube lengths, with the two-pass
-    transforms forced in both directions (forward of A, B and dC, inverse of
-    dA and dB through the workspace intermediate) and with the default choice
-    (two-pass forward from p = 2048, one-kernel inverse), against the
-    oracle's FP64 Algorithm 5.1 on the conjugate transposes."""
+    """dA = dC * B^H and dB = A^H * dC at long tube lengths, with the runtime
+    two-pass transforms forced in both directions (forward of A, B and dC,
+    inverse of dA and dB through the workspace intermediate) and with the
+    default choice (the compile-time two-pass form for 1000 = 10 x 100 and
+    4096 = 16 x 256; for 2187 = 3^7, which it cannot split, the runtime
+    two-pass forward and the one-kernel inverse), against the oracle's FP64
+    Algorithm 5.1 on the conjugate transposes."""
     import os
     qtp = _qtp()
     A, B = _inputs(m, n, s, p, seed=p + 1)
@@ -354,10 +358,10 @@ def test_backward_large_p(split, precision, m, n, s, p):
         plan = qtp.Plan(m, n, s, p, precision)
     finally:
         os.environ.pop("QTP_FFT_SPLIT", None)
-    if split == "1":
+    if split == "1" or p in (1000, 4096):
         assert plan.launch_count() == (5, 8)
     else:
-        assert plan.launch_count() == ((4, 7) if p >= 2048 else (3, 5))
+        assert plan.launch_count() == (4, 7)
     dA, dB = plan.backward(to_dev(G), to_dev(A), to_dev(B))
     plan.sync()
     Aq, Bq, Gq = planes_to_comp(A), planes_to_comp(B), planes_to_comp(G)

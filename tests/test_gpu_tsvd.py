@@ -23,7 +23,13 @@ pytestmark = pytest.mark.gpu
 # frequencies (p = 1, even p); odd and prime p; k = 64 (the maximum, global
 # scratch); a tall shape whose pair matrices still fit in shared memory.
 SHAPES = [(1, 1, 1), (5, 3, 1), (3, 5, 2), (8, 8, 8), (16, 12, 16), (12, 16, 12), (40, 24, 31), (24, 40, 7),
-          (64, 64, 32), (200, 16, 8), (16, 300, 5), (130, 20, 100)]
+          (64, 64, 32), (200, 16, 8), (16, 300, 5), (130, 20, 100),
+          # columns in registers handed over between warps (2 max(m, n) <= 256 with the buffers in the
+          # global scratch): a 2-CTA cluster; a 3-CTA cluster whose last CTA has idle warps (C/2 not a
+          # multiple of 16); the wide input (sweeps on M_f^H)
+          (128, 32, 4), (120, 40, 6), (40, 120, 9),
+          # sweeps from L2 with the register pair step (256 < 2 max(m, n) <= 512, buffers above 200 KB)
+          (200, 64, 8)]
 SIGMA_TOL = 2e-5     # relative to the largest singular value
 REC_TOL = 1e-5       # relative Frobenius error of U * S * V^H
 ORTH_TOL = 2e-5      # max |U^H * U - I| entry
@@ -37,7 +43,7 @@ def tp(X, Y):
 def factors(m, n, p, seed):
     from paper_2212_14318_gb300 import qtp
     A = synth.quat_normal(m, n, p, seed)
-    U, S, V, sigma = qtp.tsvd(to_dev(A))
+    U, S, V, sigma = qtp.tsvd(to_dev(A), check=True)  # every pair's sweeps converged (qtp_tsvd_sync)
     return (planes_to_comp(A), planes_to_comp(to_host(U)), planes_to_comp(to_host(S)),
             planes_to_comp(to_host(V)), to_host(sigma).astype(np.float64))
 
@@ -89,7 +95,7 @@ def test_tsvd_rank_deficient(p):
     x, y = rng.standard_normal((4, m, 1, p)), rng.standard_normal((4, n, 1, p))
     for Aq in (np.zeros((4, m, n, p)), Q.tprod_def(x, Q.conj_transpose(y))):
         A = comp_to_planes(Aq).astype(np.float32)
-        U, S, V, sigma = qtp.tsvd(to_dev(A))
+        U, S, V, sigma = qtp.tsvd(to_dev(A), check=True)  # every pair's sweeps converged (qtp_tsvd_sync)
         torch.cuda.synchronize()
         U, S, V = (planes_to_comp(to_host(t)) for t in (U, S, V))
         sigma = to_host(sigma).astype(np.float64)
