@@ -99,7 +99,8 @@ typedef struct qtp_plan qtp_plan;
  * split-BF16 accuracy bound for that kind's reduction length, and (p > 128)
  * every form of the forward and of the inverse tube transform (one kernel,
  * two passes with runtime-radix sub-transforms, two passes with compile-time
- * ones), and keeps the fastest of each; choices are cached per (device,
+ * ones for every split p = N1 N2 they allow), and keeps the fastest of each;
+ * choices are cached per (device,
  * shape, precision) in the process and appended to the file named by the
  * environment variable QTP_AUTOTUNE_CACHE, if set, which later processes
  * read. */
@@ -122,7 +123,7 @@ QTP_API qtp_status qtp_plan_get_tiles(const qtp_plan* plan, int* tiles3);
  * forms dA and dB, and transforms both back in one launch), or 1 forward
  * launch for products small enough to run whole in one CTA.  Long tubes
  * (p > 128 without a one-kernel compile-time transform that factor as
- * p = N1 N2 with N2 in {256, 128, 100, 64} and N1 <= 32, or from p = 2048 with
+ * p = N1 N2 with N2 in {128, 256, 100, 64} and N1 <= 32, or from p = 2048 with
  * any factor between 4 and sqrt(p)) transform in two launches per transform
  * step (through an intermediate in the workspace): up to 5 and 8.  The training pair issues *forward
  * (qtp_forward_saving, never the one-CTA route) and *backward minus the

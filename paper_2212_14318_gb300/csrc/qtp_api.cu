@@ -101,30 +101,38 @@ BwdLayout bwd_layout(const qtp_plan* pl) {
 // long tubes (scratch: the layout's intermediate).
 cudaError_t plan_fft_fwd(const qtp_plan* pl, const FftFwdJob* jobs, int njobs, int fmt, char* scratch,
                          cudaStream_t st) {
-  if (pl->fft_split_fwd == FFT_LONG) return launch_fft_fwd_long(jobs, njobs, fmt, pl->p, pl->d_tw, (float2*)scratch, st);
+  if (pl->fft_split_fwd == FFT_LONG)
+    return launch_fft_fwd_long(jobs, njobs, fmt, pl->p, pl->long_n2, pl->d_tw, (float2*)scratch, st);
   if (pl->fft_split_fwd == FFT_SPLIT)
     return launch_fft_fwd_split(jobs, njobs, fmt, pl->p, pl->d_tw, (float2*)scratch, st);
   return launch_fft_fwd(jobs, njobs, fmt, pl->rp, pl->d_tw, st);
 }
 
 cudaError_t plan_fft_inv(const qtp_plan* pl, const FftInvJob* jobs, int njobs, char* scratch, cudaStream_t st) {
-  if (pl->fft_split_inv == FFT_LONG) return launch_fft_inv_long(jobs, njobs, pl->p, pl->d_tw, (float2*)scratch, st);
+  if (pl->fft_split_inv == FFT_LONG)
+    return launch_fft_inv_long(jobs, njobs, pl->p, pl->long_n2, pl->d_tw, (float2*)scratch, st);
   if (pl->fft_split_inv == FFT_SPLIT) return launch_fft_inv_split(jobs, njobs, pl->p, pl->d_tw, (float2*)scratch, st);
   return launch_fft_inv(jobs, njobs, pl->rp, pl->d_tw, st);
 }
 
-// Twiddle entries of a plan: w_p^e (e < p), followed for the long transform
-// form by w_N2^e (e < N2).
-int plan_twiddle_count(const qtp_plan* pl) {
+// N2 of a plan's compile-time long form (0 when p has none).
+int plan_long_n2(const qtp_plan* pl) {
   int n2 = 0;
-  if (pl->p > 128 && fft_long_dims(pl->p, nullptr, &n2)) return pl->p + n2;  // any form may be chosen
-  return pl->p;
+  if (pl->p <= 128 || !fft_long_dims(pl->p, nullptr, &n2)) return 0;
+  return pl->long_n2 ? pl->long_n2 : n2;
 }
 
+// Twiddle entries of a plan: w_p^e (e < p), followed, where p has a long
+// form (any form may be chosen), by room for the largest N2 table (256).
+int plan_twiddle_count(const qtp_plan* pl) {
+  return plan_long_n2(pl) ? pl->p + 256 : pl->p;
+}
+
+// w_p^e, then w_N2^e (e < N2) of the plan's long form.
 cudaError_t plan_twiddles(const qtp_plan* pl, cudaStream_t st) {
   cudaError_t e = launch_twiddles(pl->d_tw, pl->p, st);
-  const int n = plan_twiddle_count(pl);
-  if (e == cudaSuccess && n > pl->p) e = launch_twiddles(pl->d_tw + pl->p, n - pl->p, st);
+  const int n2 = plan_long_n2(pl);
+  if (e == cudaSuccess && n2) e = launch_twiddles(pl->d_tw + pl->p, n2, st);
   return e;
 }
 
@@ -389,9 +397,9 @@ qtp_status run_products_bwd(const qtp_plan* pl, const void* sa, const void* sb, 
 // process and, when QTP_AUTOTUNE_CACHE names a file, across processes.
 // ----------------------------------------------------------------------------
 std::mutex g_tune_mu;
-// per (device, shape, precision): tiles of the forward, dA, dB products and
-// the forms of the forward and inverse tube transforms
-using TuneRecord = std::array<int, 5>;
+// per (device, shape, precision): tiles of the forward, dA, dB products, the
+// forms of the forward and inverse tube transforms and the long form's N2
+using TuneRecord = std::array<int, 6>;
 std::map<std::string, TuneRecord> g_tune_cache;
 bool g_tune_file_loaded = false;
 
@@ -416,7 +424,8 @@ void tune_cache_load() {
   char line[512], key[256];
   while (fgets(line, sizeof(line), f)) {
     TuneRecord r;
-    if (sscanf(line, "%255s %d %d %d %d %d", key, &r[0], &r[1], &r[2], &r[3], &r[4]) == 6) g_tune_cache[key] = r;
+    if (sscanf(line, "%255s %d %d %d %d %d %d", key, &r[0], &r[1], &r[2], &r[3], &r[4], &r[5]) == 7)
+      g_tune_cache[key] = r;
   }
   fclose(f);
 }
@@ -427,7 +436,7 @@ void tune_cache_store(const std::string& key, const TuneRecord& t) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), t[0], t[1], t[2], t[3], t[4]);
+  fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), t[0], t[1], t[2], t[3], t[4], t[5]);
   fclose(f);
 }
 
@@ -490,14 +499,21 @@ cudaError_t tune_tiles(qtp_plan* pl, TuneRecord& best, cudaEvent_t e0, cudaEvent
 }
 
 // Form of the forward and of the inverse tube transform (one kernel, runtime
-// two-pass, compile-time long two-pass), timed on scratch tensors of the
-// plan's shapes: the forward transforms A and B, the inverse C.
+// two-pass, compile-time long two-pass with each N2 p splits into), timed on
+// scratch tensors of the plan's shapes: the forward transforms A and B, the
+// inverse C.  Both directions share one N2 (one second twiddle table).
 cudaError_t tune_forms(qtp_plan* pl, TuneRecord& best, cudaEvent_t e0, cudaEvent_t e1) {
-  std::vector<int> cands = {FFT_ONE};
-  if (fft_split_dims(pl->p, nullptr, nullptr)) cands.push_back(FFT_SPLIT);
-  if (fft_long_dims(pl->p, nullptr, nullptr)) cands.push_back(FFT_LONG);
+  struct Cand {
+    int form, n2;
+  };
+  std::vector<Cand> cands = {{FFT_ONE, 0}};
+  if (fft_split_dims(pl->p, nullptr, nullptr)) cands.push_back({FFT_SPLIT, 0});
+  int n2s[4];
+  const int nl = fft_long_splits(pl->p, n2s);
+  for (int i = 0; i < nl; ++i) cands.push_back({FFT_LONG, n2s[i]});
   best[3] = pl->fft_split_fwd;
   best[4] = pl->fft_split_inv;
+  best[5] = pl->long_n2;
   if (cands.size() == 1) return cudaSuccess;
   const int fmt = spec_format(pl->precision);
   const size_t iA = c32_bytes(pl->p, pl->m, pl->n), iB = c32_bytes(pl->p, pl->n, pl->s),
@@ -535,19 +551,39 @@ cudaError_t tune_forms(qtp_plan* pl, TuneRecord& best, cudaEvent_t e0, cudaEvent
   ij.out = (float2*)C;
   ij.rows = pl->m; ij.cols = pl->s;
   ij.nblocks = nblocks_for(pl->m, pl->s, pl->p, true);
-  const int fwd0 = pl->fft_split_fwd, inv0 = pl->fft_split_inv;
-  float bf = 1e30f, bi = 1e30f;
-  for (int c : cands) {
-    pl->fft_split_fwd = c;
-    pl->fft_split_inv = c;
-    const float tf = time_ms([&] { return plan_fft_fwd(pl, jobs, 2, fmt, z, 0); }, e0, e1, 3);
-    const float ti = time_ms([&] { return plan_fft_inv(pl, &ij, 1, z, 0); }, e0, e1, 3);
-    if (tf < bf) { bf = tf; best[3] = c; }
-    if (ti < bi) { bi = ti; best[4] = c; }
+  const int fwd0 = pl->fft_split_fwd, inv0 = pl->fft_split_inv, n20 = pl->long_n2;
+  std::vector<float> tf(cands.size()), ti(cands.size());
+  for (size_t c = 0; c < cands.size() && e == cudaSuccess; ++c) {
+    pl->fft_split_fwd = pl->fft_split_inv = cands[c].form;
+    if (cands[c].form == FFT_LONG) {
+      pl->long_n2 = cands[c].n2;
+      e = plan_twiddles(pl, 0);  // the N2 table of this split
+    }
+    tf[c] = time_ms([&] { return plan_fft_fwd(pl, jobs, 2, fmt, z, 0); }, e0, e1, 3);
+    ti[c] = time_ms([&] { return plan_fft_inv(pl, &ij, 1, z, 0); }, e0, e1, 3);
   }
+  // the fastest form per direction; when both are long forms, one N2 for both
+  size_t bf = 0, bi = 0;
+  for (size_t c = 1; c < cands.size(); ++c) {
+    if (tf[c] < tf[bf]) bf = c;
+    if (ti[c] < ti[bi]) bi = c;
+  }
+  int n2 = 0;
+  if (cands[bf].form == FFT_LONG && cands[bi].form == FFT_LONG && cands[bf].n2 != cands[bi].n2) {
+    size_t bb = bf;
+    for (size_t c = 0; c < cands.size(); ++c)
+      if (cands[c].form == FFT_LONG && tf[c] + ti[c] < tf[bb] + ti[bb]) bb = c;
+    bf = bi = bb;
+  }
+  if (cands[bf].form == FFT_LONG) n2 = cands[bf].n2;
+  else if (cands[bi].form == FFT_LONG) n2 = cands[bi].n2;
+  best[3] = cands[bf].form;
+  best[4] = cands[bi].form;
+  best[5] = n2;
   pl->fft_split_fwd = fwd0;
   pl->fft_split_inv = inv0;
-  e = cudaDeviceSynchronize();
+  pl->long_n2 = n20;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(scratch);
   return e;
 }
@@ -564,12 +600,16 @@ qtp_status autotune(qtp_plan* pl) {
     for (int k = 0; k < 3; ++k) pl->tile[k] = hit->second[k];
     pl->fft_split_fwd = hit->second[3];
     pl->fft_split_inv = hit->second[4];
+    pl->long_n2 = hit->second[5];
+    cudaError_t e = plan_twiddles(pl, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "autotune twiddles");
     return QTP_OK;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  TuneRecord best = {TILE_AUTO, TILE_AUTO, TILE_AUTO, pl->fft_split_fwd, pl->fft_split_inv};
+  TuneRecord best = {TILE_AUTO, TILE_AUTO, TILE_AUTO, pl->fft_split_fwd, pl->fft_split_inv, pl->long_n2};
   if (e == cudaSuccess && tiles) e = tune_tiles(pl, best, e0, e1);
   if (e == cudaSuccess && forms) e = tune_forms(pl, best, e0, e1);
   if (e0) cudaEventDestroy(e0);
@@ -584,6 +624,10 @@ qtp_status autotune(qtp_plan* pl) {
   for (int k = 0; k < 3; ++k) pl->tile[k] = best[k];
   pl->fft_split_fwd = best[3];
   pl->fft_split_inv = best[4];
+  pl->long_n2 = best[5];
+  e = plan_twiddles(pl, 0);  // the N2 table of the chosen split
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "autotune twiddles");
   tune_cache_store(key, best);
   return QTP_OK;
 }
@@ -677,6 +721,12 @@ qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int preci
   pl->rp = make_radix_plan(p);
   pl->fft_split_fwd = fft_form(p, false);
   pl->fft_split_inv = fft_form(p, true);
+  if (const char* env = getenv("QTP_FFT_LONG_N2")) {  // the long form's N2, if p splits with it
+    int n2s[4];
+    const int k = fft_long_splits(p, n2s), want = atoi(env);
+    for (int i = 0; i < k; ++i)
+      if (n2s[i] == want) pl->long_n2 = want;
+  }
   pl->d_tw = nullptr;
   pl->d_err = nullptr;
   pl->tracing = 0;

@@ -141,14 +141,17 @@ cudaError_t launch_fft_inv_fixed(const FftInvJob* jobs, int njobs, int p, const 
 // first).
 bool fft_split_dims(int p, int* n1, int* n2);
 bool fft_split_eligible(int p, bool inv);
-// Compile-time long form: p = N1 N2 with N2 in {256, 128, 100, 64} (a tuned
-// two-pass length) and N1 <= 32 (registers).  Its twiddles are the length-p
-// table followed by the length-N2 one (fft_long_extra_twiddles(p) = N2
-// entries after the first p).
+// Compile-time long form: p = N1 N2 with N2 in {128, 256, 100, 64} (a tuned
+// two-pass length) and N1 <= 32 (registers).  fft_long_splits writes every
+// such N2 of p (at most 4, in that order of preference) and returns their
+// count; fft_long_dims gives the default (the first).  The launches take the
+// N2 to use (0: the default); their twiddles are the length-p table followed
+// by the length-N2 one.
+int fft_long_splits(int p, int* n2s);
 bool fft_long_dims(int p, int* n1, int* n2);
-cudaError_t launch_fft_fwd_long(const FftFwdJob* jobs, int njobs, int fmt, int p, const float2* tw, float2* scratch,
-                                cudaStream_t st);
-cudaError_t launch_fft_inv_long(const FftInvJob* jobs, int njobs, int p, const float2* tw, float2* scratch,
+cudaError_t launch_fft_fwd_long(const FftFwdJob* jobs, int njobs, int fmt, int p, int n2, const float2* tw,
+                                float2* scratch, cudaStream_t st);
+cudaError_t launch_fft_inv_long(const FftInvJob* jobs, int njobs, int p, int n2, const float2* tw, float2* scratch,
                                 cudaStream_t st);
 // Transform form of a tube length, per direction: one kernel, the two-pass
 // form with runtime-radix sub-DFTs, or the compile-time long form.  Default:
@@ -318,6 +321,7 @@ struct qtp_plan {
   qtp::RadixPlan rp;
   int fft_split_fwd;  // FftForm of the forward / inverse tube transforms (two-pass
   int fft_split_inv;  // forms go through a workspace intermediate)
+  int long_n2;        // N2 of the compile-time long form (0: its default split)
   int tracing;
   cudaEvent_t ev[4];  // stage boundaries of the last traced call
   // streams and events of qtp_forward_host_many, created on its first call
