@@ -91,8 +91,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   __shared__ int abort_flag;
 
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const uint32_t stg_base = base + GSTAGES * STAGE;  // 4 epilogue staging areas
-  const uint32_t bars = stg_base + 4 * kStgBytes;
+  const uint32_t bars = base + GSTAGES * STAGE;
   const uint32_t full = bars, empty = bars + 8 * GSTAGES;
   const uint32_t acc_full = bars + 16 * GSTAGES;      // 2 barriers
   const uint32_t acc_empty = acc_full + 16;           // 2 barriers
@@ -284,7 +283,6 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    float2* stg = reinterpret_cast<float2*>(smem_raw + (stg_base - smem_u32(smem_raw)) + q * kStgBytes);
     int lt = 0, cur = 0;
     for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
       const GTile T = decode_tile(probs, nprobs, t, cur);
@@ -307,13 +305,16 @@ __global__ void __launch_bounds__(kGThreads, 1)
         float2* out = reinterpret_cast<float2*>(ws + P.out_off) + (long long)h * P.p * P.M * P.N +
                       (long long)T.f * P.M * P.N;
         const uint32_t tb = tmem + (uint32_t)(buf * 4 * GBN + h * 2 * GBN) + lane_off;
+        const bool vec = ((reinterpret_cast<uintptr_t>(out) | (uintptr_t)(P.N & 1) * 8u) & 15u) == 0;
 #pragma unroll 1
         for (int c0 = 0; c0 < nw; c0 += 32) {
-          uint32_t re[32], im[32];
-          tmem_ld32(tb + (uint32_t)c0, re);
-          tmem_ld32(tb + (uint32_t)(GBN + c0), im);
           const int col0 = T.nt * GBN + c0;
-          if (P.trans) {
+          if (!P.trans) {
+            store_chunk<false>(tb + (uint32_t)c0, GBN, 0, out + (long long)row0 * P.N + col0, P.N, P.M - row0,
+                               P.N - col0, lane, vec);
+          } else {
+            uint32_t re[32], im[32];
+            tmem_ld32x2(tb + (uint32_t)c0, tb + (uint32_t)(GBN + c0), re, im);
             // accumulator row = column of C (index into s), column = row of C
             // (index into m): lane-consecutive stores along C's rows
             const int cs = row0 + lane;
@@ -323,8 +324,6 @@ __global__ void __launch_bounds__(kGThreads, 1)
               for (int j = 0; j < 32; ++j)
                 if (j < nj) out[(long long)(col0 + j) * P.N + cs] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
             }
-          } else {
-            store_chunk(stg, re, im, out + (long long)row0 * P.N + col0, P.N, P.M - row0, P.N - col0, lane);
           }
         }
       }
@@ -405,7 +404,7 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
                                    char* ws, int* d_err, int num_ctas, cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;
   const int np = nparts == 4 ? 4 : 2;
-  const size_t smem = (size_t)GSTAGES * 3 * np * G_SLOT + 4 * kStgBytes + 1024 + 256;
+  const size_t smem = (size_t)GSTAGES * 3 * np * G_SLOT + 1024 + 256;
   const int grid = (int)(total_tiles < num_ctas ? total_tiles : num_ctas);
   // Forward product (Thm 5.1): C1 = A1 B1 - A2 conj(B2(-f)), C2 = A1 B2 + A2 conj(B1(-f)).
   // (tau ar + i tau ai)(br + i sb bi): re += tau ar.br - tau sb ai.bi, im += tau sb ar.bi + tau ai.br

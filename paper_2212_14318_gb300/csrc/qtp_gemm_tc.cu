@@ -350,34 +350,19 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       }
     } else {
       fence_after();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // ring: async-proxy use -> generic writes
       float2* out = args.out + (long long)h * args.out_hstride + (long long)f * args.out_fstride;
-      // The operand ring is idle once the accumulators are final (every TMA
-      // load was consumed and every MMA has completed): it holds the staging
-      // areas of the epilogue warps.
-      static_assert(STAGES * NP * (A_TILE + B_TILE) >= kEpiWarps * kStgBytes,
-                    "staging areas must fit in the operand ring");
-      float2* stg = reinterpret_cast<float2*>(smem_raw + (S.a - raw) + (warp - 2) * kStgBytes);
       const int row0 = mt * BM + q * 32;
+      const bool vec = ((reinterpret_cast<uintptr_t>(out) | (uintptr_t)(args.out_rstride & 1) * 8u) & 15u) == 0;
 #pragma unroll 1
       for (int c0 = c_begin; c0 < c_begin + BN / 2; c0 += 32) {
         const uint32_t t = tmem + lane_off + (uint32_t)c0;
-        uint32_t re[32], im[32];
-        if (SPLIT || (PROMOTE && nseg > 1)) {  // plus the correction pair, or the running sum
-          uint32_t cre[32], cim[32];
-          tmem_ld32x4(t, t + BN, t + 2 * BN, t + 3 * BN, re, im, cre, cim);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            re[i] = __float_as_uint(__uint_as_float(re[i]) + __uint_as_float(cre[i]));
-            im[i] = __float_as_uint(__uint_as_float(im[i]) + __uint_as_float(cim[i]));
-          }
-        } else {
-          tmem_ld32x2(t, t + BN, re, im);
-        }
         const int col0 = nt * BN + c0;
-        if (col0 < args.N)
-          store_chunk(stg, re, im, out + (long long)row0 * args.out_rstride + col0, args.out_rstride, args.M - row0,
-                      args.N - col0, lane);
+        if (col0 >= args.N) break;  // warp-uniform
+        float2* o = out + (long long)row0 * args.out_rstride + col0;
+        if (SPLIT || (PROMOTE && nseg > 1))  // plus the correction pair, or the running sum
+          store_chunk<true>(t, BN, 2 * BN, o, args.out_rstride, args.M - row0, args.N - col0, lane, vec);
+        else
+          store_chunk<false>(t, BN, 2 * BN, o, args.out_rstride, args.M - row0, args.N - col0, lane, vec);
       }
     }
     fence_before();

@@ -168,6 +168,46 @@ __device__ __forceinline__ void tmem_ld32x4(uint32_t a0, uint32_t a1, uint32_t a
       : "memory");
 }
 
+// tcgen05.ld 16x256b: at TMEM address (lane L, column C), repetition j of .x4
+// hands thread t the words (lane L + t/4, columns C + 8j + 2(t%4) and +1) in
+// registers 4j, 4j+1 and (lane L + 8 + t/4, the same columns) in 4j+2, 4j+3
+// (checked on the GPU against words written in the 32x32b layout).  Two (four)
+// loads of 32 columns each behind one tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld16x256x2(uint32_t a0, uint32_t a1, uint32_t (&r)[16], uint32_t (&s)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      :
+        "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]),
+        "=r"(s[8]), "=r"(s[9]), "=r"(s[10]), "=r"(s[11]), "=r"(s[12]), "=r"(s[13]), "=r"(s[14]), "=r"(s[15])
+      : "r"(a0), "r"(a1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16x256x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t (&r)[16],
+                                                uint32_t (&s)[16], uint32_t (&t)[16], uint32_t (&u)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      :
+        "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]),
+        "=r"(s[8]), "=r"(s[9]), "=r"(s[10]), "=r"(s[11]), "=r"(s[12]), "=r"(s[13]), "=r"(s[14]), "=r"(s[15]),
+        "=r"(t[0]), "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]), "=r"(t[7]),
+        "=r"(t[8]), "=r"(t[9]), "=r"(t[10]), "=r"(t[11]), "=r"(t[12]), "=r"(t[13]), "=r"(t[14]), "=r"(t[15]),
+        "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+      : "memory");
+}
+
 // Write 32 consecutive TMEM columns of this thread's lane (the inverse of
 // tmem_ld32); tmem_st_wait() makes the stores complete before a thread
 // signals that the columns may be overwritten.
@@ -369,33 +409,54 @@ __device__ __forceinline__ void tensormap_acquire(const void* tm) {
                : "memory");
 }
 
-// Epilogue store of one warp's 32 x 32 complex chunk of an accumulator tile.
-// tcgen05.ld 32x32b hands lane l row l (re[j], im[j] = column j); storing that
-// directly would put the 32 lanes of every store on 32 different rows.  The
-// chunk is instead transposed through this warp's staging area stg, 16
-// columns at a time (32 rows of kStgPitch float2; the odd pitch keeps both
-// phases free of bank conflicts), and written with lane = column: each store
-// covers 128 contiguous bytes of two rows.  out points at (row0, col0) of a
-// row-major matrix with row stride ld (float2); rows_valid / cols_valid clip
-// the chunk at the matrix edge.
-constexpr int kStgPitch = 17;
-constexpr int kStgBytes = 32 * kStgPitch * 8;  // per epilogue warp
-
-__device__ __forceinline__ void store_chunk(float2* stg, const uint32_t (&re)[32], const uint32_t (&im)[32],
-                                            float2* out, long long ld, int rows_valid, int cols_valid, int lane) {
-  const int nr = rows_valid < 32 ? rows_valid : 32;
-  const int c = lane & 15, rr = lane >> 4;
+// Epilogue store of one warp's 32 x 32 complex chunk of an accumulator tile,
+// straight from the 16x256b register layout: a thread holds two neighbouring
+// columns of two rows of the real and of the imaginary accumulator, so it
+// writes 16 contiguous bytes (two complex values) and four neighbouring
+// threads fill 64 contiguous bytes of a row (whole 32-byte sectors), with no
+// shared-memory transpose.  t: TMEM address of the warp's first lane and the
+// chunk's first column of the real accumulator; the imaginary one at
+// t + im_off; CORR adds the pair at t + corr_off (split correction or promoted
+// running sum).  out points at (row0, col0) of a row-major matrix with row
+// stride ld (float2); rows_valid / cols_valid clip the chunk at the matrix
+// edge; vec: out and ld allow 16-byte stores (out 16-byte aligned, ld even).
+template <bool CORR>
+__device__ __forceinline__ void store_chunk(uint32_t t, uint32_t im_off, uint32_t corr_off, float2* out, long long ld,
+                                            int rows_valid, int cols_valid, int lane, bool vec) {
+  const int rq = lane >> 2, cq = 2 * (lane & 3);
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
+  for (int hh = 0; hh < 2; ++hh) {
+    const uint32_t th = t + ((uint32_t)(16 * hh) << 16);
+    uint32_t re[16], im[16];
+    if constexpr (CORR) {
+      uint32_t cre[16], cim[16];
+      tmem_ld16x256x4(th, th + im_off, th + corr_off, th + corr_off + im_off, re, im, cre, cim);
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      stg[lane * kStgPitch + j] = make_float2(__uint_as_float(re[16 * half + j]), __uint_as_float(im[16 * half + j]));
-    __syncwarp();
-    if (16 * half + c < cols_valid) {
-#pragma unroll 4
-      for (int r = rr; r < nr; r += 2) out[(long long)r * ld + 16 * half + c] = stg[r * kStgPitch + c];
+      for (int i = 0; i < 16; ++i) {
+        re[i] = __float_as_uint(__uint_as_float(re[i]) + __uint_as_float(cre[i]));
+        im[i] = __float_as_uint(__uint_as_float(im[i]) + __uint_as_float(cim[i]));
+      }
+    } else {
+      tmem_ld16x256x2(th, th + im_off, re, im);
     }
-    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const int r = 16 * hh + 8 * g + rq, c = 8 * j + cq, k = 4 * j + 2 * g;
+        if (r < rows_valid) {
+          float2* o = out + (long long)r * ld + c;
+          const float r0 = __uint_as_float(re[k]), i0 = __uint_as_float(im[k]);
+          const float r1 = __uint_as_float(re[k + 1]), i1 = __uint_as_float(im[k + 1]);
+          if (vec && c + 1 < cols_valid) {
+            *reinterpret_cast<float4*>(o) = make_float4(r0, i0, r1, i1);
+          } else {
+            if (c < cols_valid) o[0] = make_float2(r0, i0);
+            if (c + 1 < cols_valid) o[1] = make_float2(r1, i1);
+          }
+        }
+      }
+    }
   }
 }
 
