@@ -43,6 +43,16 @@ constexpr int kTsvdThreads = 512;
 constexpr int kTsvdWarps = kTsvdThreads / 32;
 constexpr int kTsvdMaxCols = 128;   // 2 min(m, n)
 constexpr int kTsvdMaxSweeps = 40;
+// A phase ends after a sweep in which every pair was orthogonal to within this
+// relative off-diagonal |x^H y| / (|x| |y|) when it was visited: cyclic
+// Jacobi converges quadratically there, so the next sweep would meet
+// off-diagonals of order 1e-8, far under the rotation threshold, and is
+// skipped (a sweep without rotations also meets the bound).
+constexpr float kTsvdStopRatio = 1e-4f;
+// Phase 0 (before the Newton-Schulz step) may stop earlier: the sweep after
+// the step rotates every pair still above the rotation threshold (measured:
+// a sweep at 2.6e-4 is followed by one at 2.0e-6).
+constexpr float kTsvdStopRatio0 = 1e-3f;
 constexpr size_t kTsvdSmemMax = 200 * 1024;  // dynamic shared memory of the in-smem variant
 constexpr int kTsvdClusterMax = 4;            // CTAs per pair of the global-scratch variant
 
@@ -66,6 +76,67 @@ template <bool G>
 __device__ __forceinline__ void pair_sync() {
   if constexpr (G) cg::this_cluster().sync();
   else __syncthreads();
+}
+
+// One 32 x 32 complex output tile out(i, j) = sum_l a(i, l) b(l, j) (CONJA:
+// conj(a(i, l))) by one CTA (512 threads, two outputs each), the operands
+// staged through shared memory kTileK entries of l at a time (sm: kTileSmem
+// bytes) and read once per tile.  fa(i, l), fb(l, j) return the entries
+// (0 <= i < ni, 0 <= j < nj, 0 <= l < K); IFAST stages a with i fastest (a
+// column-major over rows i), else l fastest (columns over l), so that the
+// loads are coalesced either way; b is staged l fastest.  put(i, j, value)
+// receives the result.
+constexpr int kTileP = 33;   // padded pitch of a's staging
+constexpr int kTileK = 128;  // inner entries staged at a time
+constexpr size_t kTileSmem = (size_t)(kTileP + 32) * kTileK * sizeof(float2);
+
+template <bool IFAST, bool CONJA, class FA, class FB, class Put>
+__device__ void tile_mm(FA fa, FB fb, int K, int ni, int nj, float2* sm, Put put) {
+  float2* As = sm;                   // [l][i], pitch kTileP
+  float2* Bs = sm + kTileP * kTileK;  // [j][l], pitch kTileK
+  const int i = threadIdx.x & 31, j0 = threadIdx.x >> 5;
+  float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kTileK) {
+    const int kc = min(kTileK, K - k0);
+    // every load of the chunk in flight at once (a thread's share is at most
+    // 32 kTileK / 512 = 8 entries of each operand), then the shared stores
+    constexpr int U = 32 * kTileK / kTsvdThreads;
+    float2 va[U], vb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = threadIdx.x + u * kTsvdThreads;
+      va[u] = vb[u] = make_float2(0.f, 0.f);
+      if (idx < 32 * kc) {
+        const int ii = IFAST ? (idx & 31) : idx / kc, ll = IFAST ? (idx >> 5) : idx - (idx / kc) * kc;
+        if (ii < ni) va[u] = fa(ii, k0 + ll);
+        const int jj = idx / kc, lb = idx - jj * kc;
+        if (jj < nj) vb[u] = fb(k0 + lb, jj);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = threadIdx.x + u * kTsvdThreads;
+      if (idx < 32 * kc) {
+        const int ii = IFAST ? (idx & 31) : idx / kc, ll = IFAST ? (idx >> 5) : idx - (idx / kc) * kc;
+        As[ll * kTileP + ii] = va[u];
+        const int jj = idx / kc, lb = idx - jj * kc;
+        Bs[jj * kTileK + lb] = vb[u];
+      }
+    }
+    __syncthreads();
+    for (int l = 0; l < kc; ++l) {
+      float2 a = As[l * kTileP + i];
+      if (CONJA) a.y = -a.y;
+      const float2 b0 = Bs[j0 * kTileK + l], b1 = Bs[(j0 + 16) * kTileK + l];
+      re0 = fmaf(a.x, b0.x, fmaf(-a.y, b0.y, re0));
+      im0 = fmaf(a.x, b0.y, fmaf(a.y, b0.x, im0));
+      re1 = fmaf(a.x, b1.x, fmaf(-a.y, b1.y, re1));
+      im1 = fmaf(a.x, b1.y, fmaf(a.y, b1.x, im1));
+    }
+    __syncthreads();
+  }
+  if (i < ni && j0 < nj) put(i, j0, make_float2(re0, im0));
+  if (i < ni && j0 + 16 < nj) put(i, j0 + 16, make_float2(re1, im1));
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -220,7 +291,7 @@ __device__ __forceinline__ void stw4(float4* p, float4 v) {
 // column are zero and stay zero).  Rotates in place; returns whether it did.
 template <int NX, int NV>
 __device__ __forceinline__ bool rotate_regs(float4 (&xr)[NX], float4 (&yr)[NX], float4 (&vxr)[NV],
-                                            float4 (&vyr)[NV], float tol) {
+                                            float4 (&vyr)[NV], float tol, float& ratio) {
   float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
 #pragma unroll
   for (int i = 0; i < NX; ++i) {
@@ -235,7 +306,9 @@ __device__ __forceinline__ bool rotate_regs(float4 (&xr)[NX], float4 (&yr)[NX], 
   gr = warp_sum(gr);
   gi = warp_sum(gi);
   const float gabs = hypotf(gr, gi);
-  if (!(gabs > tol * sqrtf(al * be) && gabs > 1e-30f)) return false;
+  const float nrm = sqrtf(al * be);
+  ratio = nrm > 0.f ? gabs / nrm : 0.f;
+  if (!(gabs > tol * nrm && gabs > 1e-30f)) return false;
   const float zeta = (be - al) / (2.f * gabs);
   const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
   const float cs = 1.f / sqrtf(1.f + tt * tt), sn = cs * tt;
@@ -280,14 +353,14 @@ __device__ __forceinline__ void store_col(const float4 (&r)[N], float4* dst, int
 template <bool G, int NX, int NV>
 __device__ __forceinline__ bool jacobi_pair_reg(float2* __restrict__ x, float2* __restrict__ y,
                                                 float2* __restrict__ vx, float2* __restrict__ vy, int R, int C,
-                                                float tol, int lane) {
+                                                float tol, int lane, float& ratio) {
   const int R2 = R >> 1, C2 = C >> 1;
   float4 xr[NX], yr[NX], vxr[NV], vyr[NV];
   load_col<G>(xr, reinterpret_cast<const float4*>(x), R2, lane);
   load_col<G>(yr, reinterpret_cast<const float4*>(y), R2, lane);
   load_col<G>(vxr, reinterpret_cast<const float4*>(vx), C2, lane);
   load_col<G>(vyr, reinterpret_cast<const float4*>(vy), C2, lane);
-  if (!rotate_regs(xr, yr, vxr, vyr, tol)) return false;
+  if (!rotate_regs(xr, yr, vxr, vyr, tol, ratio)) return false;
   store_col<G>(xr, reinterpret_cast<float4*>(x), R2, lane);
   store_col<G>(yr, reinterpret_cast<float4*>(y), R2, lane);
   store_col<G>(vxr, reinterpret_cast<float4*>(vx), C2, lane);
@@ -329,9 +402,10 @@ __device__ __forceinline__ void rr_pair(int C, int rr, int t, int& a, int& b) {
 // buffers alternate between two sets, so the one cluster barrier per round
 // orders both the hand-over and the reuse of a set two rounds later.  The
 // rotations and their order are those of the sweeps from memory.
-// Returns whether a sweep without rotations ended the loop (cluster-uniform).
-__device__ __forceinline__ bool ring_sweeps(float2* X, float2* V, int R, int C, float tol, int nc, int rank,
-                                            int warp, int lane, int tid, int* rotations, float4* slots) {
+// Returns whether the stop test (largest relative off-diagonal of a sweep
+// under stop) ended the loop (cluster-uniform).
+__device__ __forceinline__ bool ring_sweeps(float2* X, float2* V, int R, int C, float tol, float stop, int nc,
+                                            int rank, int warp, int lane, int tid, int* maxoff, float4* slots) {
   cg::cluster_group cl = cg::this_cluster();
   const int R2 = R >> 1, C2 = C >> 1, L = R2 + C2;
   const int T = C / 2 - 1;
@@ -354,10 +428,14 @@ __device__ __forceinline__ bool ring_sweeps(float2* X, float2* V, int R, int C, 
   int set = 0;
   bool converged = false;
   for (int sweep = 0; sweep < kTsvdMaxSweeps; ++sweep) {
-    if (tid == 0) *rotations = 0;
+    if (tid == 0) *maxoff = 0;
     cl.sync();
     for (int rr = 0; rr < C - 1; ++rr) {
-      if (active && rotate_regs(xa, xb, va, vb, tol) && lane == 0) atomicAdd(rotations, 1);
+      if (active) {
+        float ratio;
+        rotate_regs(xa, xb, va, vb, tol, ratio);
+        if (lane == 0) atomicMax(maxoff, __float_as_int(ratio));  // ratio >= 0: ordered as an int
+      }
       if (T == 0) continue;  // one pair: nothing moves
       if (active && t >= 1) {
         float4* s = local_slot(set, 0, warp);
@@ -393,12 +471,12 @@ __device__ __forceinline__ bool ring_sweeps(float2* X, float2* V, int R, int C, 
       }
       set ^= 1;
     }
-    // every CTA sums the same counters, after the last round's increments and
+    // every CTA takes the same maximum, after the last round's updates and
     // before the next sweep clears them
     cl.sync();
-    int total = 0;
-    for (int j = 0; j < nc; ++j) total += *cl.map_shared_rank(rotations, j);
-    const bool done = total == 0;
+    int worst = 0;
+    for (int j = 0; j < nc; ++j) worst = max(worst, *cl.map_shared_rank(maxoff, j));
+    const bool done = __int_as_float(worst) < stop;
     cl.sync();
     if (done) {
       converged = true;
@@ -427,7 +505,7 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   extern __shared__ float4 tsvd_smem[];
   __shared__ float sig[kTsvdMaxCols];
   __shared__ int perm[kTsvdMaxCols];
-  __shared__ int rotations;
+  __shared__ int maxoff;  // largest relative off-diagonal of the sweep (float bits)
   int nc = 1, rank = 0;
   if constexpr (G) {
     nc = (int)cg::this_cluster().num_blocks();
@@ -473,16 +551,55 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   // 2. cyclic one-sided Jacobi sweeps; X = M V throughout.
   // A rotation is skipped once |x^H y| <= tol |x| |y|; FP32 dot products over
   // R entries carry about sqrt(R / 32) eps of rounding, so the bound grows
-  // past 256 rows.  Phase 0 sweeps until no pair rotates.  V then has
+  // past 256 rows.  Phase 0 sweeps until a sweep's pairs were all orthogonal
+  // to kTsvdStopRatio0 when visited (1e-3; the sweep after the step below
+  // finishes the job), phase 1 until kTsvdStopRatio (1e-4: quadratic
+  // convergence leaves the next sweep nothing to rotate).  V then has
   // drifted from unitary by the rounding of its rotations (about
   // sqrt(rotations per column) eps: 1e-5 for 128 columns, which would show in
   // A = U S V^H), so one Newton-Schulz step T = (3 I - V^H V) / 2 is applied
-  // to V and to X (keeping X = M V), and phase 1 sweeps again (two or three
-  // sweeps restore the columns' orthogonality).
+  // to V and to X (keeping X = M V), and phase 1 sweeps again (one sweep
+  // restores the columns' orthogonality, the step having moved them by ~1e-5).
   const float tol = 2e-6f * fmaxf(1.f, sqrtf((float)R / 256.f));
   const bool reg_path = R <= 512 && C <= 128;  // jacobi_pair_reg's register capacity
   for (int phase = 0; phase < 2; ++phase) {
-  if (phase == 1) {
+  if (phase == 1 && G) {
+    // Newton-Schulz step with 32 x 32 tiles staged in shared memory, the
+    // tiles dealt over the cluster's CTAs: Tm = (3 I - V^H V) / 2, then
+    // V <- V Tm and X <- X Tm in blocks of C rows, through Tmp.
+    float2* sm = reinterpret_cast<float2*>(tsvd_smem);
+    const int nt = (C + 31) / 32;
+    for (int t = rank; t < nt * nt; t += nc) {
+      const int i0 = (t / nt) * 32, c0 = (t % nt) * 32;
+      tile_mm<false, true>([&](int i, int l) { return ldw<G>(V + (long long)(i0 + i) * C + l); },
+                           [&](int l, int j) { return ldw<G>(V + (long long)(c0 + j) * C + l); }, C,
+                           min(32, C - i0), min(32, C - c0), sm, [&](int i, int j, float2 g) {
+                             stw<G>(Tm + (long long)(c0 + j) * C + i0 + i,
+                                    make_float2(0.5f * ((i0 + i == c0 + j ? 3.f : 0.f) - g.x), -0.5f * g.y));
+                           });
+    }
+    pair_sync<G>();
+    for (int blk = -1; blk < (R + C - 1) / C; ++blk) {
+      float2* src = blk < 0 ? V : X;
+      const long long lds = blk < 0 ? C : R;
+      const int r0 = blk < 0 ? 0 : blk * C;
+      const int rows = blk < 0 ? C : min(C, R - r0);
+      const int ntr = (rows + 31) / 32;
+      for (int t = rank; t < ntr * nt; t += nc) {
+        const int rb = (t / nt) * 32, c0 = (t % nt) * 32;
+        tile_mm<true, false>([&](int i, int l) { return ldw<G>(src + (long long)l * lds + r0 + rb + i); },
+                             [&](int l, int j) { return ldw<G>(Tm + (long long)(c0 + j) * C + l); }, C,
+                             min(32, rows - rb), min(32, C - c0), sm,
+                             [&](int i, int j, float2 v) { stw<G>(Tmp + (long long)(c0 + j) * rows + rb + i, v); });
+      }
+      pair_sync<G>();
+      for (int idx = gtid; idx < rows * C; idx += gthreads) {
+        const int j = idx / rows, r = idx - j * rows;
+        stw<G>(src + (long long)j * lds + r0 + r, ldw<G>(Tmp + idx));
+      }
+      pair_sync<G>();
+    }
+  } else if (phase == 1) {
     // Tm = (3 I - V^H V) / 2, column-major
     for (int idx = gtid; idx < C * C; idx += gthreads) {
       const int j = idx / C, i = idx - j * C;
@@ -522,14 +639,15 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
     }
   }
   if constexpr (RING) {
-    if (!ring_sweeps(X, V, R, C, tol, nc, rank, warp, lane, tid, &rotations, reinterpret_cast<float4*>(tsvd_smem)) &&
+    if (!ring_sweeps(X, V, R, C, tol, phase == 0 ? kTsvdStopRatio0 : kTsvdStopRatio, nc, rank, warp, lane, tid,
+                     &maxoff, reinterpret_cast<float4*>(tsvd_smem)) &&
         rank == 0 && tid == 0)
       atomicExch(a.status, 1);
     continue;
   }
   bool converged = false;
   for (int sweep = 0; sweep < kTsvdMaxSweeps; ++sweep) {
-    if (tid == 0) rotations = 0;
+    if (tid == 0) maxoff = 0;
     pair_sync<G>();
     for (int rr = 0; rr < C - 1; ++rr) {
       for (int t = gwarp; t < C / 2; t += gwarps) {
@@ -540,9 +658,10 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
         if (reg_path) {
           float2* vx = V + (long long)ca * C;
           float2* vy = V + (long long)cb * C;
-          const bool rotated = R <= 256 ? jacobi_pair_reg<G, 4, 2>(x, y, vx, vy, R, C, tol, lane)
-                                        : jacobi_pair_reg<G, 8, 2>(x, y, vx, vy, R, C, tol, lane);
-          if (rotated && lane == 0) atomicAdd(&rotations, 1);
+          float ratio;
+          if (R <= 256) jacobi_pair_reg<G, 4, 2>(x, y, vx, vy, R, C, tol, lane, ratio);
+          else jacobi_pair_reg<G, 8, 2>(x, y, vx, vy, R, C, tol, lane, ratio);
+          if (lane == 0) atomicMax(&maxoff, __float_as_int(ratio));
           continue;
         }
         float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
@@ -558,7 +677,9 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
         gr = warp_sum(gr);
         gi = warp_sum(gi);
         const float gabs = hypotf(gr, gi);
-        if (gabs > tol * sqrtf(al * be) && gabs > 1e-30f) {
+        const float nrm = sqrtf(al * be);
+        if (lane == 0) atomicMax(&maxoff, __float_as_int(nrm > 0.f ? gabs / nrm : 0.f));
+        if (gabs > tol * nrm && gabs > 1e-30f) {
           // [x, y] <- [x, conj(e) y] [[c, s], [-s, c]], e = gamma / |gamma|
           const float zeta = (be - al) / (2.f * gabs);
           const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
@@ -576,19 +697,18 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
             stw<G>(vx + r, make_float2(cs * u.x - sn * v.x, cs * u.y - sn * v.y));
             stw<G>(vy + r, make_float2(sn * u.x + cs * v.x, sn * u.y + cs * v.y));
           }
-          if (lane == 0) atomicAdd(&rotations, 1);
         }
       }
       pair_sync<G>();
     }
-    // every CTA of the pair sums the same counters, after the round's barrier
-    // and before the next sweep clears them (the barrier below)
-    int total = rotations;
+    // every CTA of the pair takes the same maximum, after the round's barrier
+    // and before the next sweep clears it (the barrier below)
+    int worst = maxoff;
     if constexpr (G) {
-      total = 0;
-      for (int j = 0; j < nc; ++j) total += *cg::this_cluster().map_shared_rank(&rotations, j);
+      worst = 0;
+      for (int j = 0; j < nc; ++j) worst = max(worst, *cg::this_cluster().map_shared_rank(&maxoff, j));
     }
-    const bool done = total == 0;
+    const bool done = __int_as_float(worst) < (phase == 0 ? kTsvdStopRatio0 : kTsvdStopRatio);
     pair_sync<G>();
     if (done) {
       converged = true;
@@ -597,30 +717,42 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   }
   if (!converged && rank == 0 && tid == 0) atomicExch(a.status, 1);
   }
-  // the rest (sorting, completion, scatter) is the first CTA's alone; the
-  // others leave after the last barrier, with no access to their shared
-  // memory pending
-  if (rank != 0) return;
+  // the rest (sorting, completion, scatter) is the first CTA's alone, but for
+  // the structured completion at a self-paired frequency, which every CTA of
+  // the cluster shares; the others leave after their last barrier, with no
+  // access to their shared memory pending
+  const bool share = G && f == g;  // uniform in the cluster
+  if (rank != 0 && !share) return;
 
   // 3. singular values (column norms), sorted decreasing (ties by index)
-  for (int c = warp; c < C; c += kTsvdWarps) {
+  for (int c = warp; c < C && rank == 0; c += kTsvdWarps) {
     const float2 d = warp_dot(X + (long long)c * R, X + (long long)c * R, R, lane);
     if (lane == 0) sig[c] = sqrtf(fmaxf(d.x, 0.f));
   }
   __syncthreads();
-  if (tid < C) {
+  if (tid < C && rank == 0) {
     const float s = sig[tid];
-    int rank = 0;
-    for (int j = 0; j < C; ++j) rank += (sig[j] > s) || (sig[j] == s && j < tid);
-    perm[rank] = tid;
+    int rk = 0;
+    for (int j = 0; j < C; ++j) rk += (sig[j] > s) || (sig[j] == s && j < tid);
+    perm[rk] = tid;
   }
   __syncthreads();
+  if (share) {
+    // the other CTAs take the norms and the order from the first
+    pair_sync<G>();
+    if (rank != 0)
+      for (int c = tid; c < C; c += kTsvdThreads) {
+        sig[c] = *cg::this_cluster().map_shared_rank(&sig[c], 0);
+        perm[c] = *cg::this_cluster().map_shared_rank(&perm[c], 0);
+      }
+    pair_sync<G>();  // the copies are done before the first CTA may leave
+  }
   const float smax = sig[perm[0]];
   const float null_tol = 1e-6f * smax;
 
   // 4. normalise the X columns (the left vectors when tall, else the right
   //    ones); the other side is V, unitary already
-  for (long long idx = tid; idx < (long long)R * C; idx += kTsvdThreads) {
+  for (long long idx = tid; idx < (long long)R * C && rank == 0; idx += kTsvdThreads) {
     const int c = (int)(idx / R);
     const float s = sig[c];
     X[idx] = s > null_tol && s > 0.f ? cscale(X[idx], 1.f / s) : make_float2(0.f, 0.f);
@@ -696,7 +828,98 @@ __global__ void __launch_bounds__(kTsvdThreads) tsvd_pair_kernel(TsvdArgs a) {
   // completed from basis vectors by warp 0.
   __shared__ float2 coef[2 * kTsvdMaxCols];
   __shared__ float nrm;
-  for (int i = 0; i < k; ++i) {
+  bool structured = false;
+  if constexpr (G) {
+    // When every candidate is live, one Newton-Schulz step on each side's
+    // structured set S = [w_0 .. w_{k-1} | partner(w_0) .. partner(w_{k-1})]
+    // does the orthogonalisation at once: the candidates are orthonormal, and
+    // orthogonal to the other candidates' partners, to the sweeps' accuracy
+    // (a doubled singular value's subspace holds its vectors' partners), so
+    // S^H S = I + E with small E and S (3 I - S^H S) / 2 is orthonormal to
+    // O(|E|^2).  The new w_i are the first k columns.  The tiles are dealt over
+    // the cluster's CTAs.  Otherwise (a null or nearly dependent candidate:
+    // |E| > 0.1) the first CTA runs the sequential completion below.
+    bool all_live = true;
+    for (int i = 0; i < k; ++i) {
+      const float sv = sig[perm[2 * i]];
+      if (!(sv > null_tol && sv > 0.f)) all_live = false;
+    }
+    if (all_live) {  // the same in every CTA
+      float2* sm = reinterpret_cast<float2*>(tsvd_smem);
+      pair_sync<G>();  // the first CTA's normalisation of X is complete
+      for (int idx = gtid; idx < 2 * m * k; idx += gthreads) {
+        const int i = idx / (2 * m), r = idx - i * 2 * m;
+        __stcg(Wa + idx, __ldcg(W + (long long)perm[2 * i] * ldw + r));
+      }
+      for (int idx = gtid; idx < 2 * n * k; idx += gthreads) {
+        const int i = idx / (2 * n), r = idx - i * 2 * n;
+        __stcg(Za + idx, __ldcg(Z + (long long)perm[2 * i] * ldz + r));
+      }
+      if (tid == 0) maxoff = 0;
+      pair_sync<G>();
+      const int nt = (C + 31) / 32;
+      float mydev = 0.f;  // this thread's largest |S^H S - I| entry
+      for (int t = rank; t < 2 * nt * nt; t += nc) {
+        const int side = t / (nt * nt), tt = t - side * nt * nt;
+        const float2* B = side == 0 ? Wa : Za;
+        const int h = side == 0 ? m : n;
+        float2* T = side == 0 ? Tm : Tmp;
+        auto col = [&](int c, int l) -> float2 {
+          if (c < k) return __ldcg(B + (long long)c * 2 * h + l);
+          const float2* w = B + (long long)(c - k) * 2 * h;  // partner_at, read through L2
+          return l < h ? make_float2(-__ldcg(w + h + l).x, __ldcg(w + h + l).y)
+                       : make_float2(__ldcg(w + l - h).x, -__ldcg(w + l - h).y);
+        };
+        const int i0 = (tt / nt) * 32, c0 = (tt % nt) * 32;
+        tile_mm<false, true>([&](int i, int l) { return col(i0 + i, l); }, [&](int l, int j) { return col(c0 + j, l); },
+                             2 * h, min(32, C - i0), min(32, C - c0), sm, [&](int i, int j, float2 g) {
+                               const bool d = i0 + i == c0 + j;
+                               mydev = fmaxf(mydev, fabsf(g.x - (d ? 1.f : 0.f)) + fabsf(g.y));
+                               __stcg(T + (long long)(c0 + j) * C + i0 + i,
+                                      make_float2(0.5f * ((d ? 3.f : 0.f) - g.x), -0.5f * g.y));
+                             });
+      }
+      {
+        const int wdev = __reduce_max_sync(0xffffffffu, __float_as_int(mydev));  // deviations >= 0
+        if (lane == 0) atomicMax(&maxoff, wdev);
+      }
+      pair_sync<G>();
+      int worst = 0;
+      for (int j = 0; j < nc; ++j) worst = max(worst, *cg::this_cluster().map_shared_rank(&maxoff, j));
+      if (__int_as_float(worst) <= 0.1f) {  // the same in every CTA
+        // X is free (its columns were copied into Wa or Za): the new W at
+        // X (2m x k), the new Z after it (2n x k)
+        const int ntw = ((2 * m + 31) / 32) * ((k + 31) / 32), ntz = ((2 * n + 31) / 32) * ((k + 31) / 32);
+        for (int t = rank; t < ntw + ntz; t += nc) {
+          const int side = t < ntw ? 0 : 1, tt = side == 0 ? t : t - ntw;
+          const float2* B = side == 0 ? Wa : Za;
+          const int h = side == 0 ? m : n;
+          const float2* T = side == 0 ? Tm : Tmp;
+          float2* out = side == 0 ? X : X + (long long)2 * m * k;
+          const int ntc = (k + 31) / 32;
+          const int r0 = (tt / ntc) * 32, c0 = (tt % ntc) * 32;
+          tile_mm<true, false>(
+              [&](int i, int l) {
+                if (l < k) return __ldcg(B + (long long)l * 2 * h + r0 + i);
+                const float2* w = B + (long long)(l - k) * 2 * h;
+                const int r = r0 + i;
+                return r < h ? make_float2(-__ldcg(w + h + r).x, __ldcg(w + h + r).y)
+                             : make_float2(__ldcg(w + r - h).x, -__ldcg(w + r - h).y);
+              },
+              [&](int l, int j) { return __ldcg(T + (long long)(c0 + j) * C + l); }, C, min(32, 2 * h - r0),
+              min(32, k - c0), sm, [&](int i, int j, float2 v) { __stcg(out + (long long)(c0 + j) * 2 * h + r0 + i, v); });
+        }
+        pair_sync<G>();
+        for (int idx = gtid; idx < 2 * m * k; idx += gthreads) __stcg(Wa + idx, __ldcg(X + idx));
+        for (int idx = gtid; idx < 2 * n * k; idx += gthreads) __stcg(Za + idx, __ldcg(X + (long long)2 * m * k + idx));
+        pair_sync<G>();
+        structured = true;
+      }
+    }
+  }
+  // the sequential completion and the scatter are the first CTA's
+  if (rank != 0) return;
+  for (int i = 0; i < k && !structured; ++i) {
     const int c = perm[2 * i];
     const bool live = sig[c] > null_tol && sig[c] > 0.f;
     float2* wa = Wa + (long long)i * 2 * m;
@@ -793,12 +1016,14 @@ cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, 
   // columns in registers when a lane's share fits rotate_regs<4, 2> (R <= 256,
   // C <= 128); the hand-over buffers: 2 sets x 2 columns x 16 slots per CTA
   const bool ring = a.R <= 256;
-  const size_t ring_smem = ring ? (size_t)4 * kTsvdWarps * (a.R / 2 + a.C / 2) * sizeof(float4) : 0;
+  size_t ring_smem = ring ? (size_t)4 * kTsvdWarps * (a.R / 2 + a.C / 2) * sizeof(float4) : 0;
   if (ring_smem > kTsvdSmemMax) return cudaErrorInvalidValue;
+  if (ring_smem < kTileSmem) ring_smem = kTileSmem;  // the Newton-Schulz tiles
   auto kfn = ring ? tsvd_pair_kernel<true, true> : tsvd_pair_kernel<true, false>;
-  static std::atomic<unsigned long long> attr_set{0};
-  if (ring) {
-    cudaError_t e = ensure_smem_attr(attr_set, tsvd_pair_kernel<true, true>, kTsvdSmemMax);
+  static std::atomic<unsigned long long> attr_set_ring{0}, attr_set_l2{0};
+  {
+    cudaError_t e = ring ? ensure_smem_attr(attr_set_ring, tsvd_pair_kernel<true, true>, kTsvdSmemMax)
+                         : ensure_smem_attr(attr_set_l2, tsvd_pair_kernel<true, false>, kTsvdSmemMax);
     if (e != cudaSuccess) return e;
   }
   // enough CTAs that every column pair of a round has its own warp (C / 2
