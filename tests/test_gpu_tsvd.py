@@ -83,15 +83,18 @@ def test_tsvd_truncation_error(m, n, p):
         assert abs(err - T.truncation_error_sq(sigma, r)) <= 2e-5 * total, (r, err, T.truncation_error_sq(sigma, r))
 
 
+@pytest.mark.parametrize("m,n", [(8, 6), (128, 32)])
 @pytest.mark.parametrize("p", [1, 4, 5])
-def test_tsvd_rank_deficient(p):
+def test_tsvd_rank_deficient(m, n, p):
     """The zero tensor and a tubal-rank-1 tensor: unitary factors (null
-    columns completed), spectra zero beyond the rank, the tensor rebuilt."""
+    columns completed), spectra zero beyond the rank, the tensor rebuilt.
+    8 x 6 runs in one CTA's shared memory; 128 x 32 in a cluster with the
+    global scratch, where the self-paired frequencies fall back from the
+    one-step structured completion (null candidates) to the sequential one."""
     import torch
     from paper_2212_14318_gb300 import qtp
     from tests._qlayout import comp_to_planes
     rng = np.random.default_rng(90 + p)
-    m, n = 8, 6
     x, y = rng.standard_normal((4, m, 1, p)), rng.standard_normal((4, n, 1, p))
     for Aq in (np.zeros((4, m, n, p)), Q.tprod_def(x, Q.conj_transpose(y))):
         A = comp_to_planes(Aq).astype(np.float32)
