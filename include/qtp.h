@@ -125,7 +125,12 @@ QTP_API qtp_status qtp_plan_get_tiles(const qtp_plan* plan, int* tiles3);
  * (p > 128 without a one-kernel compile-time transform that factor as
  * p = N1 N2 with N2 in {128, 256, 100, 64} and N1 <= 32, or from p = 2048 with
  * any factor between 4 and sqrt(p)) transform in two launches per transform
- * step (through an intermediate in the workspace): up to 5 and 8.  The training pair issues *forward
+ * step (through an intermediate in the workspace): up to 5 and 8.  Tensor-core
+ * plans with small m and s (max(m, s) <= 128, min(m, s) <= 64, n <= 384 in
+ * split-BF16) and p >= 256 form their forward products in the grouped kernel,
+ * one tile per frequency, after a one-block copy of the problem record: one
+ * forward launch more (QTP_SMALL_TILES = 0 in the environment at plan creation
+ * keeps the single-product kernel).  The training pair issues *forward
  * (qtp_forward_saving, never the one-CTA route) and *backward minus the
  * transform launches of A and B (qtp_backward_saved).  Library extension
  * with no counterpart in the paper; for launch accounting.

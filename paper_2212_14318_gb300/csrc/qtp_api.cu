@@ -285,10 +285,91 @@ TcProblem tc_bwd_b(const qtp_plan* pl, const void* sa, const void* sg, float2* s
   return pr;
 }
 
+}  // namespace
+
+// Forward products of small m and s at many frequencies (long tubes) through
+// the persistent grouped kernel: one 128 x 64 tile per frequency holds both
+// output halves, TMEM is double-buffered and the epilogue of one tile runs
+// under the MMAs of the next, where the single-product kernel would start a
+// CTA per tiny tile and pay its prologue and epilogue each time (64 x 64 x
+// 4096: 402 us).  The problem record and the two tensor maps go to d_blob
+// before every products launch by a one-block copy kernel (they travel as its
+// parameter); the tensor maps are encoded again only when the spectra move.
+struct SmallTiles {
+  void* d_blob = nullptr;                        // device: tensor maps (A, B), then the problem record
+  alignas(64) unsigned char h_blob[kPutBlobBytes];
+  const void* sa = nullptr;                      // spectra the encoded maps describe
+  const void* sb = nullptr;
+  const void* sc = nullptr;
+  int num_sms = 0;
+};
+
+namespace {
+
+// The route: tensor-core precisions, a reduction short enough for single
+// accumulators in split-BF16 (as in the batch), one grouped tile per
+// frequency (max(m, s) <= 128, min(m, s) <= 64: the larger side on the 128
+// rows) and enough frequencies for several tiles per SM.  QTP_SMALL_TILES = 0
+// keeps the single-product kernel, 1 takes the route whenever the shape fits.
+bool small_tiles_route(const qtp_plan* pl) {
+  if (pl->precision == QTP_PREC_FP32) return false;
+  if (pl->precision == QTP_PREC_BF16X3 && pl->n > kTcSingleMaxK) return false;
+  if (fused_small_eligible(pl->m, pl->n, pl->s, pl->p)) return false;
+  if (std::max(pl->m, pl->s) > kGroupTcBM || std::min(pl->m, pl->s) > kGroupTcBN) return false;
+  int min_p = 256;
+  if (const char* env = getenv("QTP_SMALL_TILES")) {
+    if (!strcmp(env, "0")) return false;
+    if (!strcmp(env, "1")) min_p = 1;
+  }
+  return pl->p >= min_p;
+}
+
+qtp_status run_products_small(const qtp_plan* pl, const void* sa, const void* sb, float2* sc, cudaStream_t st) {
+  SmallTiles& S = *pl->small;
+  const int fmt = pl->precision == QTP_PREC_BF16X3 ? FMT_BF16X3 : FMT_BF16;
+  const int np = fmt == FMT_BF16X3 ? 4 : 2;
+  const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
+  GroupProblem P;
+  static_assert(256 + sizeof(GroupProblem) <= (size_t)kPutBlobBytes, "blob size");
+  if (S.sa != sa || S.sb != sb || S.sc != sc) {
+    memset(&P, 0, sizeof(P));
+    P.tile_begin = 0;
+    P.sa_off = 0;  // offsets from the A spectra
+    P.sb_off = (long long)((const char*)sb - (const char*)sa);
+    P.out_off = (long long)((const char*)sc - (const char*)sa);
+    P.M = m; P.N = s; P.K = n; P.p = p;
+    P.bn = kGroupTcBN;
+    auto padded = [](long long rows, long long cols) { return (rows + 127) / 128 * 128 * ((cols + 15) / 16 * 16); };
+    P.trans = padded(s, m) < padded(m, s) ? 1 : 0;
+    const int trows = P.trans ? s : m, tcols = P.trans ? m : s;
+    P.tiles_m = (trows + kGroupTcBM - 1) / kGroupTcBM;
+    P.tiles_n = (tcols + kGroupTcBN - 1) / kGroupTcBN;
+    P.lda = (int)spec_ld(fmt, n);
+    P.ldb = (int)spec_ld(fmt, s);
+    P.tmA = S.d_blob;
+    P.tmB = (const char*)S.d_blob + 128;
+    char msg[256];
+    if (!encode_group_map(S.h_blob, sa, m, n, P.lda, p, np, false, !P.trans, msg, sizeof(msg)) ||
+        !encode_group_map(S.h_blob + 128, sb, n, s, P.ldb, p, np, true, false, msg, sizeof(msg)))
+      return fail(QTP_ERR_CUDA, "products (grouped tiles): %s", msg);
+    memcpy(S.h_blob + 256, &P, sizeof(P));
+    S.sa = sa; S.sb = sb; S.sc = sc;
+  } else {
+    memcpy(&P, S.h_blob + 256, sizeof(P));
+  }
+  QTP_CUDA(launch_put_blob(S.h_blob, 256 + (int)sizeof(GroupProblem), S.d_blob, st), "products (grouped tiles)");
+  const long long tiles = (long long)P.tiles_m * P.tiles_n * p;
+  QTP_CUDA(launch_gemm_tc_grouped(reinterpret_cast<const GroupProblem*>((const char*)S.d_blob + 256), 1, tiles, np,
+                                  (char*)const_cast<void*>(sa), pl->d_err, S.num_sms, st),
+           "products (grouped tiles)");
+  return QTP_OK;
+}
+
 // Step 2 of Alg. 5.1 for the forward product: out half 0 = C1, half 1 = C2.
 //   C1_f = A1_f B1_f - A2_f conj(B2_{-f}),   C2_f = A1_f B2_f + A2_f conj(B1_{-f})
 qtp_status run_products_fwd(const qtp_plan* pl, const void* sa, const void* sb, float2* sc, cudaStream_t st) {
   const int m = pl->m, n = pl->n, s = pl->s, p = pl->p;
+  if (pl->small) return run_products_small(pl, sa, sb, sc, st);
   if (pl->precision == QTP_PREC_FP32) {
     GemmProblem pr;
     memset(&pr, 0, sizeof(pr));
@@ -742,10 +823,27 @@ qtp_status qtp_plan_create(qtp_plan** out, int m, int n, int s, int p, int preci
     delete pl;
     return cuda_fail(e, "plan creation");
   }
+  if (small_tiles_route(pl)) {
+    pl->small = new SmallTiles();
+    e = cudaMalloc(&pl->small->d_blob, kPutBlobBytes);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pl->small->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
+    if (e != cudaSuccess) {
+      cudaFree(pl->small->d_blob);
+      delete pl->small;
+      cudaFree(pl->d_tw);
+      cudaFree(pl->d_err);
+      delete pl;
+      return cuda_fail(e, "plan creation");
+    }
+  }
   pl->flags = flags;
   if (flags & QTP_PLAN_AUTOTUNE) {
     qtp_status r = autotune(pl);
     if (r != QTP_OK) {
+      if (pl->small) {
+        cudaFree(pl->small->d_blob);
+        delete pl->small;
+      }
       cudaFree(pl->d_tw);
       cudaFree(pl->d_err);
       delete pl;
@@ -770,7 +868,7 @@ qtp_status qtp_plan_launch_count(const qtp_plan* pl, int* forward, int* backward
   if (!forward || !backward) return fail(QTP_ERR_INVALID_ARG, "output pointer is NULL");
   // each transform step takes two launches in its two-pass form
   const int sf = pl->fft_split_fwd != FFT_ONE, si = pl->fft_split_inv != FFT_ONE;
-  *forward = fused_small_eligible(pl->m, pl->n, pl->s, pl->p) ? 1 : 3 + sf + si;
+  *forward = fused_small_eligible(pl->m, pl->n, pl->s, pl->p) ? 1 : 3 + sf + si + (pl->small ? 1 : 0);
   *backward = 5 + 2 * sf + si;
   return QTP_OK;
 }
@@ -800,6 +898,10 @@ qtp_status qtp_plan_destroy(qtp_plan* pl) {
   qtp_plan_set_tracing(pl, 0);
   destroy_pipe(pl->pipe);
   pl->pipe = nullptr;
+  if (pl->small) {
+    cudaFree(pl->small->d_blob);
+    delete pl->small;
+  }
   cudaFree(pl->d_tw);
   cudaFree(pl->d_err);
   delete pl;

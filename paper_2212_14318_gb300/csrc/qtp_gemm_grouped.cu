@@ -416,6 +416,24 @@ bool encode_group_map(void* tm, const void* base, int rows, int cols, int ld, in
   return true;
 }
 
+namespace {
+// Bytes handed to a kernel by value and copied to device memory by one block.
+struct Blob {
+  alignas(64) unsigned char b[kPutBlobBytes];
+};
+__global__ void put_blob_kernel(const __grid_constant__ Blob src, int nbytes, unsigned char* dst) {
+  for (int i = threadIdx.x; i < nbytes; i += blockDim.x) dst[i] = src.b[i];
+}
+}  // namespace
+
+cudaError_t launch_put_blob(const void* host, int nbytes, void* dst, cudaStream_t st) {
+  if (nbytes <= 0 || nbytes > kPutBlobBytes) return cudaErrorInvalidValue;
+  Blob b;
+  memcpy(b.b, host, (size_t)nbytes);
+  put_blob_kernel<<<1, 128, 0, st>>>(b, nbytes, reinterpret_cast<unsigned char*>(dst));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long long total_tiles, int nparts,
                                    char* ws, int* d_err, int num_ctas, cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;

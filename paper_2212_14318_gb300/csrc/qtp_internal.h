@@ -283,6 +283,11 @@ cudaError_t launch_gemm_tc_grouped(const GroupProblem* d_probs, int nprobs, long
                                    char* ws, int* d_err, int num_ctas, cudaStream_t st);
 cudaError_t launch_gemm_simt_grouped(const GroupProblem* d_probs, const int* d_prob_of_tile, long long total_tiles,
                                      char* ws, cudaStream_t st);
+// Copy nbytes (<= kPutBlobBytes) of host data to device memory at dst with
+// one stream-ordered one-block kernel (the bytes travel as its parameter, so
+// the host buffer may change as soon as the call returns).
+constexpr int kPutBlobBytes = 512;
+cudaError_t launch_put_blob(const void* host, int nbytes, void* dst, cudaStream_t st);
 // Tile shapes of the grouped kernels (rows x complex columns).
 constexpr int kGroupTcBM = 128, kGroupTcBN = 64;
 constexpr int kGroupSimtBM = 64, kGroupSimtBN = 128;
@@ -326,4 +331,7 @@ struct qtp_plan {
   cudaEvent_t ev[4];  // stage boundaries of the last traced call
   // streams and events of qtp_forward_host_many, created on its first call
   struct HostPipe* pipe;
+  // forward products of small m and s at many frequencies through the grouped
+  // kernel (null: the single-product kernel)
+  struct SmallTiles* small;
 };

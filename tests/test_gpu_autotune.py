@@ -57,7 +57,10 @@ def test_autotuned_transform_forms(m, n, s, p, tmp_path, monkeypatch):
     for precision in ("bf16x3", "fp32"):
         plan = qtp.Plan(m, n, s, p, precision, autotune=True)
         fwd, bwd = plan.launch_count()
-        assert fwd in (3, 4, 5) and bwd in (5, 6, 7, 8), (fwd, bwd)
+        # transforms in one or two launches each; the split-BF16 forward of these
+        # small products adds the grouped-tile products' record copy
+        extra = 1 if precision == "bf16x3" else 0
+        assert fwd - extra in (3, 4, 5) and bwd in (5, 6, 7, 8), (fwd, bwd)
         C = to_host(plan.forward(to_dev(A), to_dev(B)))
         plan.sync()
         Aq, Bq, Gq = planes_to_comp(A), planes_to_comp(B), planes_to_comp(G)

@@ -326,7 +326,10 @@ def test_forward_large_p_both_transforms(split, precision, m, n, s, p):
         plan = qtp.Plan(m, n, s, p, precision)
     finally:
         del os.environ["QTP_FFT_SPLIT"]
-    assert plan.launch_count()[0] == (3 if split == "0" else 5)
+    # tensor-core precisions: these small products take the grouped-tile
+    # products from p = 256 (one extra launch: the problem record's copy)
+    small = 1 if precision != "fp32" and p >= 256 else 0
+    assert plan.launch_count()[0] == (3 if split == "0" else 5) + small
     C = to_host(plan.forward(to_dev(A), to_dev(B)))
     plan.sync()
     Aq, Bq = planes_to_comp(A), planes_to_comp(B)
@@ -358,12 +361,54 @@ def test_backward_large_p(split, precision, m, n, s, p):
         plan = qtp.Plan(m, n, s, p, precision)
     finally:
         os.environ.pop("QTP_FFT_SPLIT", None)
+    small = 0 if precision == "fp32" else 1  # the forward's grouped-tile products (backward unchanged)
     if split == "1" or p in (1000, 4096):
-        assert plan.launch_count() == (5, 8)
+        assert plan.launch_count() == (5 + small, 8)
     else:
-        assert plan.launch_count() == (4, 7)
+        assert plan.launch_count() == (4 + small, 7)
     dA, dB = plan.backward(to_dev(G), to_dev(A), to_dev(B))
     plan.sync()
     Aq, Bq, Gq = planes_to_comp(A), planes_to_comp(B), planes_to_comp(G)
     assert_close(to_host(dA), Q.alg51(Gq, Q.conj_transpose(Bq)), REL_TOL, ELEM_TOL, f"dA p={p}")
     assert_close(to_host(dB), Q.alg51(Q.conj_transpose(Aq), Gq), REL_TOL, ELEM_TOL, f"dB p={p}")
+
+
+# The forward products of small m and s through the grouped kernel (one tile
+# per frequency holding both output halves): taken by itself from p = 256,
+# forced here (QTP_SMALL_TILES=1) at short tube lengths too.  Plain and
+# transposed tiles (the larger of m and s on the 128 rows), ragged K up to the
+# single-accumulator limit, both tensor-core precisions, and a second call with
+# other buffers (the tensor maps encoded again) against the oracle.
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("m,n,s,p,env", [(64, 64, 64, 16, "1"), (128, 40, 64, 8, "1"), (40, 30, 128, 12, "1"),
+                                         (100, 384, 50, 5, "1"), (33, 20, 17, 300, None)])
+def test_forward_small_tiles_route(precision, m, n, s, p, env):
+    import os
+    import torch
+    qtp = _qtp()
+    if env is not None:
+        os.environ["QTP_SMALL_TILES"] = env
+    try:
+        plan = qtp.Plan(m, n, s, p, precision)
+        os.environ["QTP_SMALL_TILES"] = "0"  # the single-product kernel, for comparison
+        plan_tc = qtp.Plan(m, n, s, p, precision)
+    finally:
+        os.environ.pop("QTP_SMALL_TILES", None)
+    assert plan.launch_count()[0] == plan_tc.launch_count()[0] + 1
+    for call in range(2):
+        A, B = _inputs(m, n, s, p, seed=7 * call + p + m)
+        dA, dB = to_dev(A), to_dev(B)
+        C = to_host(plan.forward(dA, dB))
+        plan.sync()
+        C_tc = to_host(plan_tc.forward(dA, dB))
+        plan_tc.sync()
+        Aq, Bq = planes_to_comp(A), planes_to_comp(B)
+        ref = Q.alg51(Aq, Bq)
+        if precision == "bf16x3":
+            assert_close(C, ref, REL_TOL, ELEM_TOL, f"grouped tiles, call {call}")
+        else:  # one bf16 product: the single-product kernel's error level, not more
+            err = np.linalg.norm(planes_to_comp(C) - ref) / np.linalg.norm(ref)
+            err_tc = np.linalg.norm(planes_to_comp(C_tc) - ref) / np.linalg.norm(ref)
+            assert err <= 1.5 * err_tc + 1e-6, (err, err_tc)
+        del dA, dB
+        torch.cuda.synchronize()
