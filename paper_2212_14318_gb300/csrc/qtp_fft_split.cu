@@ -457,14 +457,14 @@ __global__ void __launch_bounds__(kThreads, min_blocks<N2, true>()) fft_long_inv
 
 template <int N2, bool INV>
 constexpr size_t long_smem() {
-  return (size_t)N2 * fs_pitch(N2, INV) * sizeof(float2);
+  return (size_t)N2 * fs_pitch(N2, INV, true) * sizeof(float2);
 }
 
 // Runs of the two-pass N2 transform over one k1's rows: the padded run space
 // of the bf16 forward (odd rows get a phantom tube) or the plain one.
 long long long_runs(int rows, int cols, int n2, bool inv, int fmt) {
   const int cp = (!inv && fmt != FMT_C32 && (cols & 1)) ? cols + 1 : cols;
-  return div_up(2LL * rows * cp, tubes_for(n2, inv));
+  return div_up(2LL * rows * cp, tubes_for(n2, inv, true));
 }
 
 template <int N1>

@@ -46,7 +46,10 @@ __host__ __device__ constexpr Split split_of(int p, bool inv) {
 //   Two-pass: about QTP_FS_ELEMS = 4096 complex per CTA (32 KB of exchange
 //   buffer), at least 32 tubes (the frequency-major stores write runs of T
 //   tubes) as long as the buffer stays within 64 KB (p = 256, 512, 1024:
-//   32, 16, 8 tubes).
+//   32, 16, 8 tubes).  The forward one-kernel form takes about
+//   QTP_FS_ELEMS_FWD = 6400, which changes p = 100 alone (64 tubes, 50 KB:
+//   the batch's p = 100 forward transforms 1026 -> 927 us on 512 products;
+//   the inverse and the long form's inner p = 100 measured slower with 64).
 //   Stockham: about QTP_FFT_ELEMS complex per buffer (2304: ~34 KB per CTA,
 //   up to six resident CTAs per SM; measured faster than 4608); the forward
 //   transform keeps at least 32 tubes, the inverse, whose stores are
@@ -56,6 +59,9 @@ __host__ __device__ constexpr Split split_of(int p, bool inv) {
 #endif
 #ifndef QTP_FS_ELEMS
 #define QTP_FS_ELEMS 4096
+#endif
+#ifndef QTP_FS_ELEMS_FWD
+#define QTP_FS_ELEMS_FWD 6400
 #endif
 // Resident CTAs per SM the transform kernels are compiled for (caps their
 // registers at 65536 / (kThreads * resident CTAs)): the two-pass transforms
@@ -75,11 +81,12 @@ __host__ __device__ constexpr int min_blocks() {
   return P >= 256 ? 2 : (INV ? QTP_FFT_MINB_INV : QTP_FFT_MINB);
 }
 
-__host__ __device__ constexpr int tubes_for(int p, bool inv) {
+// lng: the inner pass of a long transform (qtp_fft_split.cu).
+__host__ __device__ constexpr int tubes_for(int p, bool inv, bool lng = false) {
   int lim = 0;
   if (split_of(p, inv).r1 != 0) {
     // at least 32 tubes while the buffer stays within 64 KB (8 192 complex)
-    lim = QTP_FS_ELEMS / p;
+    lim = (inv || lng ? QTP_FS_ELEMS : QTP_FS_ELEMS_FWD) / p;
     const int cap = 8192 / p < 32 ? 8192 / p : 32;
     if (lim < cap) lim = cap;
   } else {
@@ -113,9 +120,9 @@ __host__ __device__ constexpr int fs_conflicts(int A, int S, int tp) {
     }
   return total;
 }
-__host__ __device__ constexpr int fs_pitch(int p, bool inv) {
+__host__ __device__ constexpr int fs_pitch(int p, bool inv, bool lng = false) {
   const Split sp = split_of(p, inv);
-  const int T = tubes_for(p, inv);
+  const int T = tubes_for(p, inv, lng);
   const int A = sp.r2, S = 1;
   int best = T, cost = fs_conflicts(A, S, T);
   for (int pad = 2; pad < 32; pad += 2) {
@@ -162,8 +169,8 @@ template <int P, int FMT, bool LONG = false>
 __device__ __forceinline__ void fs_fwd_body(const FftFwdJob& job, long long b, const float2* __restrict__ tw,
                                             float2* smem, const LongMap& L = LongMap{1, 0, P, nullptr}) {
   constexpr int R1 = split_of(P, false).r1, R2 = split_of(P, false).r2;
-  constexpr int T = tubes_for(P, false);
-  constexpr int TP = fs_pitch(P, false);
+  constexpr int T = tubes_for(P, false, LONG);
+  constexpr int TP = fs_pitch(P, false, LONG);
   constexpr int NPARTS = FMT == FMT_BF16X3 ? 4 : (FMT == FMT_BF16 ? 2 : 1);
   static_assert(R1 * R2 == P && kThreads % T == 0, "two-pass split");
 
@@ -332,8 +339,8 @@ template <int P, bool LONG = false>
 __device__ __forceinline__ void fs_inv_body(const FftInvJob& job, long long b, const float2* __restrict__ tw,
                                             float2* smem, const LongMap& L = LongMap{1, 0, P, nullptr}) {
   constexpr int F1 = split_of(P, true).r1, F2 = split_of(P, true).r2;
-  constexpr int T = tubes_for(P, true);
-  constexpr int TP = fs_pitch(P, true);
+  constexpr int T = tubes_for(P, true, LONG);
+  constexpr int TP = fs_pitch(P, true, LONG);
   static_assert(F1 * F2 == P && kThreads % T == 0, "two-pass split");
 
   const long long per_plane = (long long)job.rows * job.cols;
