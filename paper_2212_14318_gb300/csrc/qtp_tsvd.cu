@@ -29,9 +29,14 @@
 // warps with a cluster barrier between rounds, and the cluster's first CTA
 // finishes alone.  When 2 max(m, n) <= 256 the columns stay in registers for
 // a whole phase and pass between neighbouring warps (ring_sweeps) instead of
-// going through L2 every round.  The rotations and their order are the same
+// going through L2 every round; those clusters take up to eight CTAs, as
+// many as keep all pairs in one wave.  The rotations and their order are the same
 // in every variant.
 #include <cooperative_groups.h>
+
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "qtp_internal.h"
 
@@ -54,7 +59,7 @@ constexpr float kTsvdStopRatio = 1e-4f;
 // a sweep at 2.6e-4 is followed by one at 2.0e-6).
 constexpr float kTsvdStopRatio0 = 1e-3f;
 constexpr size_t kTsvdSmemMax = 200 * 1024;  // dynamic shared memory of the in-smem variant
-constexpr int kTsvdClusterMax = 4;            // CTAs per pair of the global-scratch variant
+constexpr int kTsvdClusterMax = 8;            // CTAs per pair of the global-scratch variant (portable)
 
 namespace cg = cooperative_groups;
 
@@ -390,8 +395,9 @@ __device__ __forceinline__ void rr_pair(int C, int rr, int t, int& a, int& b) {
 }
 
 // Jacobi sweeps with the columns in registers (the cluster variant when
-// R <= 256).  Pair slot t (one per warp of the cluster) keeps its two columns
-// of X and V in registers for a whole phase; between rounds every slot hands
+// R <= 256).  Pair slot t (one per warp of the first wpc warps of each of the
+// cluster's CTAs) keeps its two columns of X and V in registers for a whole
+// phase; between rounds every slot hands
 // one column to each neighbour through shared memory (distributed shared
 // memory between the cluster's CTAs), which is the round-robin order of
 // rr_pair run as a ring (T = C/2 - 1):
@@ -409,8 +415,9 @@ __device__ __forceinline__ bool ring_sweeps(float2* X, float2* V, int R, int C, 
   cg::cluster_group cl = cg::this_cluster();
   const int R2 = R >> 1, C2 = C >> 1, L = R2 + C2;
   const int T = C / 2 - 1;
-  const int t = rank * kTsvdWarps + warp;
-  const bool active = t <= T;
+  const int wpc = (T + nc) / nc;  // slots per CTA, ceil((T + 1) / nc) <= kTsvdWarps
+  const int t = rank * wpc + warp;
+  const bool active = warp < wpc && t <= T;
   float4 xa[4], xb[4], va[2], vb[2];
   int ca = 0, cb = 0;
   if (active) {
@@ -423,7 +430,7 @@ __device__ __forceinline__ bool ring_sweeps(float2* X, float2* V, int R, int C, 
   // hand-over buffer of slot u: set s, kind 0 (its first column) or 1 (its second)
   auto local_slot = [&](int s, int kind, int w) { return slots + ((s * 2 + kind) * kTsvdWarps + w) * L; };
   auto slot_of = [&](int s, int kind, int u) -> const float4* {
-    return cl.map_shared_rank(local_slot(s, kind, u % kTsvdWarps), u / kTsvdWarps);
+    return cl.map_shared_rank(local_slot(s, kind, u % wpc), u / wpc);
   };
   int set = 0;
   bool converged = false;
@@ -1027,21 +1034,70 @@ cudaError_t launch_tsvd_pairs(const float2* H, int m, int n, int p, float2* Uh, 
     if (e != cudaSuccess) return e;
   }
   // enough CTAs that every column pair of a round has its own warp (C / 2
-  // pairs), at most kTsvdClusterMax
-  int nc = (a.C / 2 + kTsvdWarps - 1) / kTsvdWarps;
-  nc = nc < 1 ? 1 : (nc > kTsvdClusterMax ? kTsvdClusterMax : nc);
+  // pairs); the sweeps from L2 deal the pairs over the warps in order, so
+  // they take no more
+  const int npairs = p / 2 + 1;
+  const int nc_min = (a.C / 2 + kTsvdWarps - 1) / kTsvdWarps < 1 ? 1 : (a.C / 2 + kTsvdWarps - 1) / kTsvdWarps;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((p / 2 + 1) * nc));
   cfg.blockDim = dim3(kTsvdThreads);
   cfg.dynamicSmemBytes = ring_smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)nc;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  auto set_nc = [&](int c) {
+    cfg.gridDim = dim3((unsigned)(npairs * c));
+    attr[0].val.clusterDim.x = (unsigned)c;
+  };
+  int nc = nc_min;
+  if (ring) {
+    // The ring's rounds are bound by each SM's issue of its slots' steps, so
+    // the slots are spread over more CTAs while the clusters still run in
+    // one wave (128x64x32, 17 pairs: 4, 5, 6 CTAs 2.95, 2.68, 2.37 ms; 8 CTAs
+    // 1.96 ms a wave, but only 16 clusters of 8 fit at once).  The count
+    // with the fewest waves x (slots per CTA + 8), the waves from the
+    // occupancy query, cached per (device, C, pairs).
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const long long key = ((long long)dev << 40) | ((long long)a.C << 20) | npairs;
+    static std::mutex mu;
+    static std::vector<std::pair<long long, int>> chosen;
+    int found = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (const auto& kv : chosen)
+        if (kv.first == key) found = kv.second;
+    }
+    if (found == 0) {
+      found = nc_min;
+      double best = 1e30;
+      for (int c = nc_min; c <= kTsvdClusterMax; ++c) {
+        set_nc(c);
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) != cudaSuccess || active < 1) {
+          (void)cudaGetLastError();
+          continue;
+        }
+        const int wpc = (a.C / 2 + c - 1) / c;
+        const double cost = (double)((npairs + active - 1) / active) * (wpc + 8);
+        if (cost < best) {
+          best = cost;
+          found = c;
+        }
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      chosen.emplace_back(key, found);
+    }
+    nc = found;
+    if (const char* ev = getenv("QTP_TSVD_CLUSTER")) {  // a fixed count, for measurement
+      const int want = atoi(ev);
+      if (want >= nc_min && want <= kTsvdClusterMax) nc = want;
+    }
+  }
+  set_nc(nc);
   cudaError_t e = cudaLaunchKernelEx(&cfg, kfn, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
