@@ -242,7 +242,11 @@ QTP_API qtp_status qtp_backward_saved(const qtp_plan* plan, const float* dC, con
  * caller-owned, 16-byte aligned; workspace_bytes >= qtp_tsvd_workspace_size.
  * FP32 one-sided Jacobi per frequency pair.  Limits: min(m, n) <=
  * QTP_TSVD_MAX_K, max(m, n) <= QTP_TSVD_MAX_MN, p <= 4096 (QTP_ERR_UNSUPPORTED
- * beyond).  Asynchronous on stream. */
+ * beyond).  Asynchronous on stream.  When a pair's columns are kept in
+ * registers (2 max(m, n) <= 256, buffers past 200 KB) a cluster of up to 8 CTAs
+ * shares it, the count taken from the cluster occupancy at the first call of
+ * a shape; QTP_TSVD_CLUSTER = n in the environment fixes it (for
+ * measurement; the results do not depend on it). */
 #define QTP_TSVD_MAX_K 64
 #define QTP_TSVD_MAX_MN 1024
 QTP_API qtp_status qtp_tsvd_workspace_size(int m, int n, int p, size_t* bytes);
@@ -251,12 +255,15 @@ QTP_API qtp_status qtp_tsvd(int m, int n, int p, const float* A, float* U, float
 
 /* Synchronise stream after a qtp_tsvd call of this shape on this workspace
  * and report whether every frequency pair's Jacobi sweeps converged: each of
- * the two sweep phases stops after a sweep without rotations or after 40
- * sweeps; a pair that still rotated in its 40th sweep gets factors that are
- * written as usual but may miss the orthogonality bound, and this call then
- * returns QTP_ERR_NOT_CONVERGED (else QTP_OK; QTP_ERR_CUDA if the stream
- * reports an error).  The status lives in the workspace and is cleared by the
- * next qtp_tsvd on it. */
+ * the two sweep phases (before and after the Newton-Schulz step that keeps V
+ * unitary) stops after a sweep whose column pairs were all orthogonal to
+ * within a relative off-diagonal |x^H y| / (|x| |y|) of 1e-3 (the first
+ * phase) or 1e-4 (the second) when visited, or after 40 sweeps; a pair that
+ * missed the bound in its 40th sweep gets factors that are written as usual
+ * but may miss the orthogonality bound, and this call then returns
+ * QTP_ERR_NOT_CONVERGED (else QTP_OK; QTP_ERR_CUDA if the stream reports an
+ * error).  The status lives in the workspace and is cleared by the next
+ * qtp_tsvd on it. */
 QTP_API qtp_status qtp_tsvd_sync(int m, int n, int p, const void* workspace, void* stream);
 
 /* Gradients of a real loss L(C), C = A * B, with each quaternion entry taken

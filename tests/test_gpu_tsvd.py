@@ -25,8 +25,8 @@ pytestmark = pytest.mark.gpu
 SHAPES = [(1, 1, 1), (5, 3, 1), (3, 5, 2), (8, 8, 8), (16, 12, 16), (12, 16, 12), (40, 24, 31), (24, 40, 7),
           (64, 64, 32), (200, 16, 8), (16, 300, 5), (130, 20, 100),
           # columns in registers handed over between warps (2 max(m, n) <= 256 with the buffers in the
-          # global scratch): a 2-CTA cluster; a 3-CTA cluster whose last CTA has idle warps (C/2 not a
-          # multiple of 16); the wide input (sweeps on M_f^H)
+          # global scratch): 32, 40 and 40 pair slots, so CTAs with idle warps at most cluster sizes; the
+          # wide input (sweeps on M_f^H); test_tsvd_ring_cluster_counts runs them at fixed cluster sizes
           (128, 32, 4), (120, 40, 6), (40, 120, 9),
           # sweeps from L2 with the register pair step (256 < 2 max(m, n) <= 512, buffers above 200 KB)
           (200, 64, 8)]
@@ -110,6 +110,33 @@ def test_tsvd_rank_deficient(m, n, p):
         assert np.max(sigma[:, 1:]) <= 1e-5 * scale
         rec = tp(tp(U, S), Q.conj_transpose(V))
         assert np.sqrt(np.sum((rec - Aq) ** 2)) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("m,n,p,counts", [(128, 32, 4, (2, 3, 5, 8)), (120, 40, 6, (3, 4, 7)),
+                                           (40, 120, 9, (3, 6)), (64, 64, 32, (4, 5, 8))])
+def test_tsvd_ring_cluster_counts(m, n, p, counts, monkeypatch):
+    """The register ring's pair slots spread over any count of CTAs from the
+    smallest that holds them (QTP_TSVD_CLUSTER fixes it; by default the
+    launch takes the count from the cluster occupancy): the rotations, their
+    order and every other step's arithmetic are the same, so the factors are
+    bit-identical to the default count's, which are valid against the
+    oracle.  8 CTAs for 17 pairs runs two waves of clusters."""
+    from paper_2212_14318_gb300 import qtp
+    A = synth.quat_normal(m, n, p, 11)
+    Ad = to_dev(A)
+    monkeypatch.delenv("QTP_TSVD_CLUSTER", raising=False)
+    ref = [to_host(t) for t in qtp.tsvd(Ad, check=True)]
+    for c in counts:
+        monkeypatch.setenv("QTP_TSVD_CLUSTER", str(c))
+        out = [to_host(t) for t in qtp.tsvd(Ad, check=True)]
+        for a, b in zip(ref, out):
+            np.testing.assert_array_equal(a, b, err_msg=f"{c} CTAs")
+    U, S, V = (planes_to_comp(t) for t in ref[:3])
+    sigma = ref[3].astype(np.float64)
+    Aq = planes_to_comp(A)
+    _, _, _, sref = T.tsvd(Aq)
+    assert np.max(np.abs(sigma - sref)) <= SIGMA_TOL * sref.max()
+    check_valid(Aq, U, S, V, sigma, (m, n, p))
 
 
 def test_tsvd_repeatable():
