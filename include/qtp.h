@@ -322,7 +322,8 @@ QTP_API qtp_status qtp_forward_batched(qtp_batch_plan* plan, const float* const*
  * no counterpart).  Step 2 runs every product either in the grouped kernel
  * (128 x 64 tiles that compute both output halves) or in the single-product
  * kernel (128 x 256 / 128 x 128 tiles per output half, one launch each,
- * spread over four streams of the plan inside the graph): products whose
+ * spread over eight streams of the plan inside the graph, concurrent with
+ * the grouped kernel): products whose
  * split-BF16 reduction exceeds 384 per half always take the latter, and so do
  * products with min(m, s) >= *route_min.  Without QTP_BATCH_AUTOTUNE
  * *route_min is INT_MAX (every other product grouped; the environment
